@@ -1,0 +1,292 @@
+"""Benchmark of the fused hybrid thermal LB boiling step (one JSON line).
+
+Workload: the 4096 x 4096 bubble-array boiling domain (walls in y, heated
+bottom at superheat 0.1 T_c, 256 vapour bubbles of radius 20-60 in saturated
+liquid at 0.86 T_c, paper EOS a = 3/49). A "step" is one time step of the
+whole path: stream + collide + forces, RK4 temperature, wall heat flux.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+value      MLUPS (lattice-cell updates per microsecond) over all ranks, device
+           time of the timed steps with the state resident in HBM (the state,
+           1.34 GB, is larger than L2, so no flush is needed).
+e2e        the same metric through the public API with host buffers: every
+           step uploads the wall temperature profile from host memory, steps,
+           and reads the heat-flux accumulators back (synchronising).
+roofline   the fused kernel's algorithmic 80 B per cell update (9 populations
+           and theta, each read and written once) over its average CUDA-event
+           duration, against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference
+           the FP64 oracle on the host cores, on a bounded band of rows of the
+           same workload.
+Multi-GPU (torchrun): independent replicas, one domain per rank (weak scaling).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline (fwd, adjoint); boiling-curve sims/hour batched vs plain"
+L = 4096
+BYTES_PER_LU = 80  # 9 populations + theta, FP32, read + write
+WORKLOAD = {"workload": "boiling domain 4096x4096, 256 vapour bubbles r=20-60, walls in y, "
+                        "heated bottom superheat 0.1Tc, Ts=0.86Tc, PR a=3/49 b=2/21 omega=0.344",
+            "Lx": L, "Ly": L, "state_bytes": None, "l2": "inputs larger than L2 (no flush)"}
+
+
+def workload_config():
+    from paper_1501_03857_gb300 import lb
+    return lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS)
+
+
+def workload_rho0(cfg, rv, rl):
+    from paper_1501_03857_gb300 import inputs
+    return inputs.bubble_density(cfg.Lx, cfg.Ly, rl, rv, n_bubbles=256, r_min=20.0, r_max=60.0, seed=4)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i", str(index),
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds: float = 12.0, rows: int = 48):
+    """The FP64 oracle on a band of `rows` rows (full 4096 width, the bottom
+    wall band) of the workload, for about `seconds` of CPU time."""
+    import torch
+    import oracle as O
+    from paper_1501_03857_gb300 import inputs
+    cores = os.cpu_count() or 1
+    torch.set_num_threads(cores)
+    a, b, R, om = 3 / 49, 2 / 21, 1.0, 0.344
+    Tc = O.critical_temperature(a, b, R)
+    rv, rl = O.maxwell_coexistence(a, b, R, om, 0.86 * Tc)
+    rho_full = inputs.bubble_density(L, L, rl, rv, n_bubbles=256, r_min=20.0, r_max=60.0, seed=4)
+    rho0 = torch.tensor(rho_full[:rows], dtype=torch.float64)
+    P = O.Params(Lx=L, Ly=rows, a=a, b=b, R=R, omega=om)
+    P.finalize(rho0=rho0, superheat=0.1 * Tc, rho_v=rv, rho_l=rl)
+    P.rho_ave = float(np.asarray(rho_full, np.float64).mean())
+    f, th = O.initial_state(rho0, P)
+    f, th, _ = O.step(f, th, P)  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        f, th, _ = O.step(f, th, P)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds and n >= 2:
+            break
+    mlups = n * L * rows / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle (PyTorch CPU), {n} steps of a {L}x{rows} bottom band of the workload, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    import oracle as O
+    from paper_1501_03857_gb300 import inputs
+    cores = os.cpu_count() or 1
+    torch.set_num_threads(cores)
+    rows = 32
+    a, b, R, om = 3 / 49, 2 / 21, 1.0, 0.344
+    Tc = O.critical_temperature(a, b, R)
+    rv, rl = O.maxwell_coexistence(a, b, R, om, 0.86 * Tc)
+    rho_full = inputs.bubble_density(L, L, rl, rv, n_bubbles=256, r_min=20.0, r_max=60.0, seed=4)
+    rho0 = torch.tensor(rho_full[:rows], dtype=torch.float64)
+    P = O.Params(Lx=L, Ly=rows, a=a, b=b, R=R, omega=om)
+    P.finalize(rho0=rho0, superheat=0.1 * Tc, rho_v=rv, rho_l=rl)
+    P.rho_ave = float(np.asarray(rho_full, np.float64).mean())
+    f, th = O.initial_state(rho0, P)
+    for _ in range(args.warmup):
+        f, th, _ = O.step(f, th, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, th, _ = O.step(f, th, P)
+    el = time.perf_counter() - t0
+    value = args.steps * L * rows / el / 1e6
+    sample = f"FP64 oracle (PyTorch CPU), each step a {L}x{rows} bottom band of the workload"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, sample_rows=rows),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1501_03857_gb300 import lb
+
+    cfg = workload_config()
+    rv, rl = lb.coexistence(cfg)
+    Tc = lb.critical_temperature(cfg)
+    rho0 = workload_rho0(cfg, rv, rl)
+    stream = torch.cuda.current_stream()
+    sim = lb.Simulation(cfg, superheat=0.1 * Tc, Gw=0.0, rho0=rho0, stream=stream)
+    cells = cfg.Lx * cfg.Ly
+    WORKLOAD["state_bytes"] = 2 * 10 * cells * 4
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-timed region: K steps, one fused kernel launch each
+    sim.step(args.warmup)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = ClockSampler(local) if rank == 0 else None
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clocks = clk.stop() if clk else None
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    sim.sync()
+    ms_all = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_all = float(t.item())
+    value = world * cells * args.steps / (ms_all * 1e-3) / 1e6
+
+    # ---- end-to-end through the public API with host buffers
+    prof = np.zeros(cfg.Lx, dtype=np.float64)
+    try:
+        prof_t = torch.from_numpy(prof).pin_memory()
+        prof = prof_t.numpy()
+    except RuntimeError:
+        pass
+    e2e_steps = max(3, min(args.steps, 50))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_wall_temperature(0.1 * Tc, prof)
+        sim.step(1)
+        sim.heat_flux()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": cfg.Lx * 4, "d2h_bytes_per_step": 76, "steps": e2e_steps,
+           "api": "lb_set_wall_temperature + lb_step(1) + lb_heat_flux per step"}
+
+    if rank == 0:
+        peak, src = measured_peaks()
+        avg_ms = float(np.mean(kern_ms))
+        achieved = BYTES_PER_LU * cells / (avg_ms * 1e-3) / 1e9
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            traffic = json.load(open(tp)).get("lb_fused_step")
+        info = sim.info()
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, parallelism=f"replicas{world}", launch=info),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "peak_source": src,
+                             "kernel": "lb_fused_step", "bytes_per_lu": BYTES_PER_LU,
+                             "avg_kernel_ms": avg_ms},
+                "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

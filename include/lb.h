@@ -1,0 +1,186 @@
+/*
+ * lb.h - C ABI of the GB300 (sm_103a) hybrid thermal pseudopotential lattice
+ * Boltzmann boiling step (Li, Kang, Francois, He, Luo; arXiv 1501.03857).
+ *
+ * One time step advances the D2Q9 MRT populations with the improved forcing
+ * scheme (Eqs. 2-9), the Peng-Robinson pseudopotential (Eq. 21) and the
+ * wettability force (Eq. 22), integrates the temperature equation (Eq. 18)
+ * with classical RK4 (Eqs. 19-20) and isotropic central differences, and
+ * accumulates the bottom-wall heat flux q(t) (Sec. 3.2).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns LB_OK (0) or a negative LB_E_* code; the message of
+ *    the last failure on the calling thread is returned by lb_last_error().
+ *    Nothing aborts, traps or prints.
+ *  - Fields are row-major [y][x] with x fastest, rows y = 0 (heated bottom
+ *    wall) .. Ly-1 (top). Populations are [alpha][y][x] with the velocity
+ *    order e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1) e5=(1,1) e6=(-1,1)
+ *    e7=(-1,-1) e8=(1,-1).
+ *  - Units are lattice units (delta_x = delta_t = 1, Sec. 3.1).
+ *  - The caller owns every device buffer (the workspace) and the CUDA stream
+ *    (passed as void*, a cudaStream_t). The handle owns host metadata only.
+ *    All device work is issued asynchronously on that stream; entry points
+ *    that return host data synchronise the stream first.
+ *  - Device-detected faults (EOS domain, non-finite values) latch a flag
+ *    that the next synchronising call (lb_sync, lb_heat_flux, lb_fields,
+ *    lb_get_state, lb_mass) reports as LB_E_EOS_DOMAIN / LB_E_NONFINITE and
+ *    then clears.
+ */
+#ifndef LB_H
+#define LB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_OK 0
+#define LB_E_INVAL (-1)       /* bad argument, size or state                */
+#define LB_E_CUDA (-2)        /* a CUDA runtime call failed                 */
+#define LB_E_EOS_DOMAIN (-3)  /* psi argument 2(p - rho/3)/G < 0 somewhere  */
+#define LB_E_NONFINITE (-4)   /* NaN or Inf in rho or T                     */
+#define LB_E_TIMEOUT (-5)     /* a bounded device wait gave up              */
+
+/* Boundary condition in y (Sec. 3.1: periodic in x, solid walls at y = 0
+ * and y = Ly). */
+#define LB_BC_WALLS 0         /* Zou-He no-slip walls, T_b below, T_s above */
+#define LB_BC_TOP_OUTFLOW 1   /* bottom wall; top row zero-gradient, T_s    */
+#define LB_BC_PERIODIC 2      /* periodic in y too (invariant tests)        */
+
+/* Grid and switches. Lx >= 1, Ly >= 3. */
+typedef struct lb_grid {
+    int32_t Lx, Ly;
+    int32_t bc_y;         /* LB_BC_*                                         */
+    int32_t ghost_layer;  /* 1: apply F_m on wall rows with a ghost row that
+                             copies the wall row's psi (the ~90 degree
+                             variant of Sec. 3.2); 0: no F on wall rows      */
+    int32_t isothermal;   /* 1: skip the temperature equation (T frozen)     */
+    int32_t reserved;
+} lb_grid;
+
+/* Peng-Robinson EOS (Eq. 21) and pseudopotential parameters. The paper
+ * uses a = 3/49, b = 2/21, R = 1, omega = 0.344, sigma = 1.2 (after Eq. 21);
+ * G must be negative (psi = sqrt(2 (p - rho c_s^2)/(G c^2)), after Eq. 7). */
+typedef struct lb_eos {
+    double a, b, R, omega, G, sigma;
+} lb_eos;
+
+/* Thermal and transport parameters (Sec. 3.1) and the initial pool.
+ * Paper values: T_s = 0.86 T_c, c_v = 6, c_v chi = 0.028, g = 3e-5,
+ * nu_L = 0.1, nu_V = 0.5/3. s_e, s_zeta, s_q are the relaxation rates of
+ * Eq. 4 that the paper leaves unstated (defaults 0.8, 0.8, 1.1). The
+ * initial state is liquid below y = pool_height and vapour above with a
+ * tanh interface of width 5 and relative density noise +-noise_amp drawn
+ * from splitmix64(seed, y*Lx + x). */
+typedef struct lb_thermal {
+    double Ts_over_Tc, cv, cv_chi, g, nu_l, nu_v, s_e, s_zeta, s_q;
+    double pool_height, noise_amp;
+    uint64_t seed;
+} lb_thermal;
+
+typedef struct lb_handle lb_handle;
+
+/* ---- host-only helpers (no GPU needed) -------------------------------- */
+
+/* T_c = 0.0778 a / (0.45724 b R), from the two relations after Eq. 21. */
+int lb_critical_temperature(const lb_eos* eos, double* Tc);
+
+/* Maxwell equal-area coexistence densities of the PR EOS at temperature T
+ * (0 < T < T_c), solved in FP64 on the host (Sec. 3.1: rho_L ~ 6.5 and
+ * rho_V ~ 0.38 at 0.86 T_c). */
+int lb_coexistence(const lb_eos* eos, double T, double* rho_v, double* rho_l);
+
+/* The initial density lb_init builds when rho0 == NULL (Sec. 3.1 set-up),
+ * written to the caller's host array rho0[Ly*Lx]. */
+int lb_initial_density(const lb_grid* grid, const lb_eos* eos,
+                       const lb_thermal* th, float* rho0);
+
+/* Device workspace bytes lb_init needs for this grid (populations and
+ * temperature, double-buffered, plus accumulators). */
+int lb_workspace_bytes(const lb_grid* grid, size_t* bytes);
+
+/* ---- simulation --------------------------------------------------------- */
+
+/* Create a simulation in the caller's device workspace (>= the size from
+ * lb_workspace_bytes, 256-byte aligned) on stream `stream` (a cudaStream_t).
+ * Tb_profile: NULL or Lx values added to `superheat` to give the bottom-wall
+ * superheat T_b(x) - T_s (Sec. 3.2 defines Delta T = T_b - T_s). Gw: the
+ * fluid-solid interaction strength of Eq. 22 on the heating wall. rho0: NULL
+ * (build the pool from `th`) or a host array [Ly*Lx] of initial densities.
+ * The populations start at the rest equilibrium w_a rho0 and T = T_s, with
+ * the wall rows at their Dirichlet temperatures. rho_ave of Eq. 9 is the
+ * mean of rho0. Synchronises the stream before returning. */
+int lb_init(lb_handle** h, const lb_grid* grid, const lb_eos* eos,
+            const lb_thermal* th, const double* Tb_profile, double superheat,
+            double Gw, const float* rho0, void* dev_workspace,
+            size_t workspace_bytes, void* stream);
+
+/* Advance nsteps (>= 0) time steps asynchronously on the stream; each step
+ * adds one sample q(t) (level t, before the step's update) to the device
+ * FP64 heat-flux accumulators. */
+int lb_step(lb_handle* h, int nsteps);
+
+/* Change the bottom-wall temperature (the superheat step of Sec. 3.2):
+ * T_b(x) - T_s = superheat + (Tb_profile ? Tb_profile[x] : 0). Takes effect
+ * at the next step (the current wall row is overwritten too). Asynchronous;
+ * Tb_profile may be reused as soon as the call returns. */
+int lb_set_wall_temperature(lb_handle* h, const double* Tb_profile, double superheat);
+
+/* Change G_w of Eq. 22. */
+int lb_set_wettability(lb_handle* h, double Gw);
+
+/* Read the wall heat-flux statistics (Sec. 3.2): q_inst = the last q(t),
+ * q_mean and q_std over the samples since the last reset, nsamples. Any
+ * output pointer may be NULL. reset != 0 clears the sums after reading.
+ * Synchronises the stream. */
+int lb_heat_flux(lb_handle* h, double* q_inst, double* q_mean, double* q_std,
+                 int64_t* nsamples, int reset);
+
+/* Macroscopic fields at the current time level: rho = sum f, u = (sum e f
+ * + F/2)/rho with the forces of this level (Eq. 6), T = T_s + theta. Each
+ * output is [Ly*Lx] FP32 or NULL; on_device != 0 means device pointers.
+ * Synchronises the stream. */
+int lb_fields(lb_handle* h, float* rho, float* ux, float* uy, float* T, int on_device);
+
+/* Copy the raw state out / in: post-collision populations fpost[9*Ly*Lx]
+ * and theta = T - T_s [Ly*Lx] (either may be NULL). lb_get_state
+ * synchronises; lb_set_state is asynchronous (the source must stay valid
+ * until the stream reaches it when on_device != 0). */
+int lb_get_state(lb_handle* h, float* fpost, float* theta, int on_device);
+int lb_set_state(lb_handle* h, const float* fpost, const float* theta, int on_device);
+
+/* Total mass sum_x rho = sum_x sum_a f*_a, accumulated in FP64 on the
+ * device (Eq. 9's rho_ave is mass / (Lx Ly) at t = 0). Synchronises. */
+int lb_mass(lb_handle* h, double* mass);
+
+/* Wait for the stream and report latched device faults. */
+int lb_sync(lb_handle* h);
+
+/* Number of steps taken, and the launch shape in use: threads per block
+ * (a multiple of 32; 10 of them are x-halo columns) and rows per segment. */
+int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblocks);
+
+/* Override the launch shape (block_x in [64, 1024] multiple of 32 and
+ * seg_rows >= 1; 0 keeps the automatic choice). Used by the autotuner. */
+int lb_set_launch(lb_handle* h, int block_x, int seg_rows);
+
+/* Checkpoint: lb_save_bytes gives the blob size; lb_save writes the state,
+ * step count, accumulators and wall profile into host memory; lb_load
+ * restores a blob saved from a handle with the same grid. Both
+ * synchronise. */
+int lb_save_bytes(lb_handle* h, size_t* bytes);
+int lb_save(lb_handle* h, void* host_buf, size_t bytes);
+int lb_load(lb_handle* h, const void* host_buf, size_t bytes);
+
+/* Release the handle (the workspace stays the caller's). */
+int lb_destroy(lb_handle* h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_H */

@@ -1,0 +1,135 @@
+// Device-side definitions shared by the kernels of the GB300 boiling step.
+//
+// Lattice: D2Q9 with e0=(0,0) e1=(1,0) e2=(0,1) e3=(-1,0) e4=(0,-1)
+// e5=(1,1) e6=(-1,1) e7=(-1,-1) e8=(1,-1) (Sec. 2). Fields are pitched
+// row-major [y][pitch] FP32, populations are 9 such planes (SoA).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbgpu {
+
+constexpr int HALO = 5;    // x-halo columns per side recomputed by a block
+constexpr int RING = 4;    // rows kept per stencil field in shared memory
+constexpr int TRING = 8;   // rows kept of theta^t
+constexpr int SM_ROWS = 7 * RING + TRING;  // psi rho vx vy u2 u3 u4 + theta
+
+enum { BC_WALLS = 0, BC_TOP_OUTFLOW = 1, BC_PERIODIC = 2 };
+enum : unsigned { ERR_EOS = 1u, ERR_NONFINITE = 2u };
+
+// FP64 device accumulators (wall heat flux of Sec. 3.2, mass, fault flags).
+struct Acc {
+    double q_partial;   // sum over x of q_w for the step in flight
+    double q_last;      // q(t) of the last completed step
+    double q_sum, q_sum2, q_n;
+    double mass;
+    unsigned int count; // bottom blocks that added their partial this step
+    unsigned int err;   // ERR_* bits
+    double pad[2];
+};
+
+// Everything one launch of the step needs, passed by value.
+struct StepParams {
+    const float* f_in;
+    float* f_out;
+    const float* th_in;
+    float* th_out;
+    const float* thb;   // theta_b(x) = T_b(x) - T_s on the bottom wall
+    Acc* acc;
+    int Lx, Ly, pitch, plane;
+    int bc, ghost, isothermal;
+    int nout, nstrips, seg_h;
+    // Peng-Robinson EOS (Eq. 21): phi(T) = (k0 - k1 sqrt(T))^2 with
+    // k0 = 1 + kappa, k1 = kappa / sqrt(Tc); psi^2 = two_over_G (p - rho/3).
+    float Ts, a, b, R, two_over_G, k0, k1, G;
+    // MRT collision (Eqs. 2, 4, 8)
+    float s_e, s_z, s_q, sig_e, sig_z;
+    float rho_v, inv_drho, tau_v, dtau;
+    // forces (Eqs. 9, 22); gw6 = G_w/6 is -G_w sum_a omega_a s e_a,y on row 1
+    float g, rho_ave, gw6;
+    // temperature (Eq. 18): chi = c_v chi / c_v, cvchi = c_v chi
+    float chi, cvchi, inv_cv;
+};
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    int r = v % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ bool finite_f(float v) { return fabsf(v) <= 3.402823466e38f; }
+
+// psi(rho, T) = sqrt(2 (p_EOS - rho c_s^2) / G), c = 1 (Sec. 2 and Eq. 21).
+__device__ __forceinline__ float eos_psi(float rho, float T, const StepParams& P, bool& bad) {
+    const float sT = sqrtf(T);
+    float ph = P.k0 - P.k1 * sT;
+    ph *= ph;
+    const float br = P.b * rho;
+    const float p = rho * P.R * T / (1.f - br) - P.a * ph * rho * rho / (1.f + 2.f * br - br * br);
+    float arg = P.two_over_G * (p - rho * (1.f / 3.f));
+    if (arg < 0.f) {
+        bad = true;
+        arg = 0.f;
+    }
+    return sqrtf(arg);
+}
+
+// Pulled populations of row y at column x (Eq. 3: f_a(x) = f*_a(x - e_a)).
+// Populations whose source lies outside a wall are left 0 and filled by
+// Zou-He; with the outflow top the source row is clamped to the top row.
+__device__ __forceinline__ void load_row(const StepParams& P, int y, int x, int xm, int xp,
+                                         float (&f)[9], float& th) {
+    const float* __restrict__ F = P.f_in;
+    const int pl = P.plane, pitch = P.pitch;
+    int ym = y - 1, yp = y + 1;
+    bool okm = true, okp = true;
+    if (P.bc == BC_PERIODIC) {
+        if (ym < 0) ym += P.Ly;
+        if (yp >= P.Ly) yp -= P.Ly;
+    } else {
+        okm = ym >= 0;
+        if (yp >= P.Ly) {
+            if (P.bc == BC_TOP_OUTFLOW) yp = P.Ly - 1;
+            else okp = false;
+        }
+    }
+    const int rc = y * pitch, rm = ym * pitch, rp = yp * pitch;
+    f[0] = __ldg(F + 0 * pl + rc + x);
+    f[1] = __ldg(F + 1 * pl + rc + xm);
+    f[3] = __ldg(F + 3 * pl + rc + xp);
+    f[2] = okm ? __ldg(F + 2 * pl + rm + x) : 0.f;
+    f[5] = okm ? __ldg(F + 5 * pl + rm + xm) : 0.f;
+    f[6] = okm ? __ldg(F + 6 * pl + rm + xp) : 0.f;
+    f[4] = okp ? __ldg(F + 4 * pl + rp + x) : 0.f;
+    f[7] = okp ? __ldg(F + 7 * pl + rp + xp) : 0.f;
+    f[8] = okp ? __ldg(F + 8 * pl + rp + xm) : 0.f;
+    th = __ldg(P.th_in + rc + x);
+}
+
+// Zou-He no-slip (u = 0) fill of the unknown populations on the wall rows
+// (Sec. 3.1): zero momentum and bounce-back of the normal non-equilibrium
+// part. Bottom unknowns 2, 5, 6; top unknowns 4, 7, 8 (walls only).
+__device__ __forceinline__ void wall_fill(const StepParams& P, int y, float (&f)[9]) {
+    if (P.bc != BC_PERIODIC && y == 0) {
+        const float d = 0.5f * (f[1] - f[3]);
+        f[2] = f[4];
+        f[5] = f[7] - d;
+        f[6] = f[8] + d;
+    }
+    if (P.bc == BC_WALLS && y == P.Ly - 1) {
+        const float d = 0.5f * (f[1] - f[3]);
+        f[4] = f[2];
+        f[7] = f[5] + d;
+        f[8] = f[6] - d;
+    }
+}
+
+// sum_a w_a psi(x + e_a) e_a with w = 1/3 (axis), 1/12 (diagonal), Eq. 7;
+// pm, pc, pn point at column x of rows y-1, y, y+1.
+__device__ __forceinline__ void psi_sum(const float* pm, const float* pc, const float* pn,
+                                        float& sx, float& sy) {
+    sx = (pc[1] - pc[-1]) * (1.f / 3.f) + ((pn[1] - pm[-1]) + (pm[1] - pn[-1])) * (1.f / 12.f);
+    sy = (pn[0] - pm[0]) * (1.f / 3.f) + ((pn[1] - pm[-1]) + (pn[-1] - pm[1])) * (1.f / 12.f);
+}
+
+}  // namespace lbgpu

@@ -1,0 +1,663 @@
+// C-ABI implementation (include/lb.h): parameter validation, FP64 host
+// thermodynamics (critical point, Maxwell coexistence), the initial pool,
+// workspace layout, launches and read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb.h"
+#include "lb_internal.h"
+
+using namespace lbgpu;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(LB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LB_CUDA(call, what)                              \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Peng-Robinson thermodynamics in FP64 (Eq. 21)
+// ---------------------------------------------------------------------------
+
+struct Pr {
+    double a, b, R, omega, Tc, kappa;
+    explicit Pr(const lb_eos& e)
+        : a(e.a), b(e.b), R(e.R), omega(e.omega),
+          Tc(0.0778 * e.a / (0.45724 * e.b * e.R)),
+          kappa(0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega) {}
+    double phi(double T) const {
+        const double t = 1.0 + kappa * (1.0 - std::sqrt(T / Tc));
+        return t * t;
+    }
+    double p(double rho, double T) const {
+        return rho * R * T / (1.0 - b * rho) - a * phi(T) * rho * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
+    }
+    // integral of p dv in v = 1/rho (antiderivative)
+    double prim(double v, double T) const {
+        const double s2 = std::sqrt(2.0);
+        return R * T * std::log(v - b) -
+               a * phi(T) / (2.0 * s2 * b) * std::log((v + b - s2 * b) / (v + b + s2 * b));
+    }
+};
+
+// root of p(rho) = P on [lo, hi] where p - P changes sign, by bisection
+double pr_root(const Pr& e, double T, double P, double lo, double hi) {
+    double flo = e.p(lo, T) - P;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const double fm = e.p(mid, T) - P;
+        if ((fm < 0) == (flo < 0)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+        if (hi - lo <= 1e-16 * hi) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Maxwell equal-area construction: find P_sat with p(rho_V) = p(rho_L) =
+// P_sat and int_{v_L}^{v_V} (p - P_sat) dv = 0.
+int maxwell(const Pr& e, double T, double* rv, double* rl) {
+    if (!(T > 0.0 && T < e.Tc)) return fail(LB_E_INVAL, "coexistence needs 0 < T < Tc (T=%g, Tc=%g)", T, e.Tc);
+    const int N = 40000;
+    const double rmax = (1.0 / e.b) * (1.0 - 1e-9);
+    const double r0 = 1e-6, dr = (rmax * 0.999 - r0) / N;
+    double r_hi = -1, r_lo = -1, p_hi = 0, p_lo = 0;
+    double pprev = e.p(r0, T), dprev = 0;
+    for (int i = 1; i <= N; ++i) {
+        const double r = r0 + i * dr, pc = e.p(r, T), d = pc - pprev;
+        if (i > 1) {
+            if (r_hi < 0 && dprev > 0 && d <= 0) { r_hi = r - dr; p_hi = pprev; }
+            else if (r_hi > 0 && r_lo < 0 && dprev < 0 && d >= 0) { r_lo = r - dr; p_lo = pprev; break; }
+        }
+        dprev = d;
+        pprev = pc;
+    }
+    if (r_hi < 0 || r_lo < 0) return fail(LB_E_INVAL, "isotherm T=%g has no van der Waals loop", T);
+    p_lo = std::max(p_lo, 1e-8 * p_hi);
+    double Plo = p_lo, Phi = p_hi, vV = 0, vL = 0;
+    for (int it = 0; it < 300; ++it) {
+        const double P = 0.5 * (Plo + Phi);
+        const double rV = pr_root(e, T, P, 1e-18, r_hi);
+        const double rL = pr_root(e, T, P, r_lo, rmax);
+        vV = 1.0 / rV;
+        vL = 1.0 / rL;
+        const double A = e.prim(vV, T) - e.prim(vL, T) - P * (vV - vL);
+        if (A > 0) Plo = P; else Phi = P;
+        if (Phi - Plo <= 1e-17 * Phi) break;
+    }
+    const double P = 0.5 * (Plo + Phi);
+    *rv = pr_root(e, T, P, 1e-18, r_hi);
+    *rl = pr_root(e, T, P, r_lo, rmax);
+    return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Initial pool (Sec. 3.1) with splitmix64 noise
+// ---------------------------------------------------------------------------
+
+inline uint64_t splitmix64(uint64_t seed, uint64_t n) {
+    uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void pool(int Lx, int Ly, double rl, double rv, double h, double amp, uint64_t seed, float* out) {
+    for (int y = 0; y < Ly; ++y) {
+        const double prof = 0.5 * (rl + rv) - 0.5 * (rl - rv) * std::tanh(2.0 * (y - h) / 5.0);
+        for (int x = 0; x < Lx; ++x) {
+            double r = prof;
+            if (amp != 0.0) {
+                const uint64_t n = (uint64_t)y * (uint64_t)Lx + (uint64_t)x;
+                const double u = (double)(splitmix64(seed, n) >> 11) * 0x1.0p-53;
+                r = r * (1.0 + amp * (2.0 * u - 1.0));
+            }
+            out[(size_t)y * Lx + x] = (float)r;
+        }
+    }
+}
+
+int validate(const lb_grid* g, const lb_eos* e, const lb_thermal* t) {
+    if (!g || !e || !t) return fail(LB_E_INVAL, "null parameter struct");
+    if (g->Lx < 1 || g->Ly < 3) return fail(LB_E_INVAL, "grid %dx%d: need Lx >= 1, Ly >= 3", g->Lx, g->Ly);
+    if (g->bc_y < LB_BC_WALLS || g->bc_y > LB_BC_PERIODIC) return fail(LB_E_INVAL, "bad bc_y %d", g->bc_y);
+    const long long pitch = (g->Lx + 31) / 32 * 32;
+    if (9LL * pitch * g->Ly >= (1LL << 31)) return fail(LB_E_INVAL, "grid too large for 32-bit plane offsets");
+    if (!(e->a > 0 && e->b > 0 && e->R > 0)) return fail(LB_E_INVAL, "EOS needs a, b, R > 0");
+    if (!(e->G < 0)) return fail(LB_E_INVAL, "G must be negative");
+    if (!(e->sigma >= 0)) return fail(LB_E_INVAL, "sigma must be >= 0");
+    if (!(t->Ts_over_Tc > 0 && t->Ts_over_Tc < 1)) return fail(LB_E_INVAL, "Ts/Tc must be in (0, 1)");
+    if (!(t->cv > 0 && t->cv_chi >= 0)) return fail(LB_E_INVAL, "need cv > 0, cv_chi >= 0");
+    if (!(t->nu_l > 0 && t->nu_v > 0)) return fail(LB_E_INVAL, "viscosities must be > 0");
+    const double rates[3] = {t->s_e, t->s_zeta, t->s_q};
+    for (double r : rates)
+        if (!(r > 0 && r < 2)) return fail(LB_E_INVAL, "relaxation rates must be in (0, 2)");
+    return LB_OK;
+}
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    int pitch;
+    size_t plane, f0, f1, t0, t1, thb, acc, total;
+};
+
+Layout layout(const lb_grid* g) {
+    Layout L;
+    L.pitch = (g->Lx + 31) / 32 * 32;
+    L.plane = (size_t)L.pitch * g->Ly;
+    const size_t fb = 9 * L.plane * sizeof(float), tb = L.plane * sizeof(float);
+    L.f0 = 0;
+    L.f1 = align256(L.f0 + fb);
+    L.t0 = align256(L.f1 + fb);
+    L.t1 = align256(L.t0 + tb);
+    L.thb = align256(L.t1 + tb);
+    L.acc = align256(L.thb + (size_t)L.pitch * sizeof(float));
+    L.total = align256(L.acc + sizeof(Acc));
+    return L;
+}
+
+}  // namespace
+
+struct lb_handle {
+    lb_grid grid;
+    lb_eos eos;
+    lb_thermal th;
+    double Tc, Ts, rho_v, rho_l, rho_ave, Gw, superheat;
+    std::vector<double> profile;
+    Layout lay;
+    char* ws;
+    float* f[2];
+    float* t[2];
+    float* thb;
+    Acc* acc;
+    int cur;
+    cudaStream_t st;
+    int64_t steps;
+    Launch launch;
+    StepParams base;
+    float* wall_pinned;      // pinned staging of theta_b(x) for the upload
+    cudaEvent_t wall_done;   // the last upload from wall_pinned has run
+    bool wall_pending;
+};
+
+namespace {
+
+void fill_params(lb_handle* h) {
+    StepParams& P = h->base;
+    memset(&P, 0, sizeof(P));
+    const lb_grid& g = h->grid;
+    const lb_eos& e = h->eos;
+    const lb_thermal& t = h->th;
+    P.thb = h->thb;
+    P.acc = h->acc;
+    P.Lx = g.Lx;
+    P.Ly = g.Ly;
+    P.pitch = h->lay.pitch;
+    P.plane = (int)h->lay.plane;
+    P.bc = g.bc_y;
+    P.ghost = g.ghost_layer ? 1 : 0;
+    P.isothermal = g.isothermal ? 1 : 0;
+    const double kappa = 0.37464 + 1.54226 * e.omega - 0.26992 * e.omega * e.omega;
+    P.Ts = (float)h->Ts;
+    P.a = (float)e.a;
+    P.b = (float)e.b;
+    P.R = (float)e.R;
+    P.G = (float)e.G;
+    P.two_over_G = (float)(2.0 / e.G);
+    P.k0 = (float)(1.0 + kappa);
+    P.k1 = (float)(kappa / std::sqrt(h->Tc));
+    P.s_e = (float)t.s_e;
+    P.s_z = (float)t.s_zeta;
+    P.s_q = (float)t.s_q;
+    P.sig_e = (float)(e.sigma / (1.0 / t.s_e - 0.5));
+    P.sig_z = (float)(e.sigma / (1.0 / t.s_zeta - 0.5));
+    P.rho_v = (float)h->rho_v;
+    P.inv_drho = (float)(1.0 / (h->rho_l - h->rho_v));
+    const double tau_v = t.nu_v * 3.0 + 0.5, tau_l = t.nu_l * 3.0 + 0.5;
+    P.tau_v = (float)tau_v;
+    P.dtau = (float)(tau_l - tau_v);
+    P.g = (float)t.g;
+    P.rho_ave = (float)h->rho_ave;
+    P.gw6 = (float)(h->Gw / 6.0);
+    P.chi = (float)(t.cv_chi / t.cv);
+    P.cvchi = (float)t.cv_chi;
+    P.inv_cv = (float)(1.0 / t.cv);
+}
+
+int choose_launch(lb_handle* h, int block_x, int seg_rows) {
+    int dev = 0, nsm = 0;
+    LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    const int Lx = h->grid.Lx, Ly = h->grid.Ly;
+    int bx = block_x;
+    if (bx <= 0) bx = (Lx + 2 * HALO <= 256) ? std::max(64, (Lx + 2 * HALO + 31) / 32 * 32) : 256;
+    if (bx < 64 || bx > 1024 || bx % 32) return fail(LB_E_INVAL, "block_x %d must be a multiple of 32 in [64, 1024]", bx);
+    int occ = 0;
+    LB_CUDA((cudaError_t)step_occupancy(bx, &occ), "occupancy");
+    if (occ < 1) return fail(LB_E_INVAL, "block_x %d does not fit on an SM", bx);
+    const int nout = bx - 2 * HALO;
+    const int nstrips = (Lx + nout - 1) / nout;
+    int seg = seg_rows;
+    if (seg <= 0) {
+        const int slots = nsm * occ;
+        const int nseg = std::max(1, slots / nstrips);
+        seg = std::max(8, (Ly + nseg - 1) / nseg);
+    }
+    h->launch.block_x = bx;
+    h->launch.seg_rows = seg;
+    h->launch.nstrips = nstrips;
+    h->launch.nseg = (Ly + seg - 1) / seg;
+    h->base.nout = nout;
+    h->base.nstrips = nstrips;
+    h->base.seg_h = seg;
+    return LB_OK;
+}
+
+int check_device_errors(lb_handle* h) {
+    unsigned err = 0;
+    LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    LB_CUDA(cudaMemcpy(&err, &h->acc->err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error flags");
+    if (err) {
+        const unsigned z = 0;
+        LB_CUDA(cudaMemcpy(&h->acc->err, &z, sizeof(unsigned), cudaMemcpyHostToDevice), "clear error flags");
+        if (err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature on the device");
+        if (err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument 2(p - rho/3)/G < 0 (EOS domain)");
+    }
+    return LB_OK;
+}
+
+int upload_wall(lb_handle* h) {
+    const int Lx = h->grid.Lx;
+    if (h->wall_pending) LB_CUDA(cudaEventSynchronize(h->wall_done), "wait for the previous wall upload");
+    for (int x = 0; x < Lx; ++x)
+        h->wall_pinned[x] = (float)(h->superheat + (h->profile.empty() ? 0.0 : h->profile[x]));
+    LB_CUDA(cudaMemcpyAsync(h->thb, h->wall_pinned, Lx * sizeof(float), cudaMemcpyHostToDevice, h->st),
+            "upload wall temperature");
+    LB_CUDA(cudaEventRecord(h->wall_done, h->st), "cudaEventRecord");
+    h->wall_pending = true;
+    return LB_OK;
+}
+
+void release(lb_handle* h) {
+    if (!h) return;
+    if (h->wall_pending) cudaEventSynchronize(h->wall_done);
+    if (h->wall_done) cudaEventDestroy(h->wall_done);
+    if (h->wall_pinned) cudaFreeHost(h->wall_pinned);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_last_error(void) { return g_err.c_str(); }
+
+int lb_critical_temperature(const lb_eos* eos, double* Tc) {
+    if (!eos || !Tc) return fail(LB_E_INVAL, "null argument");
+    if (!(eos->a > 0 && eos->b > 0 && eos->R > 0)) return fail(LB_E_INVAL, "EOS needs a, b, R > 0");
+    *Tc = Pr(*eos).Tc;
+    return LB_OK;
+}
+
+int lb_coexistence(const lb_eos* eos, double T, double* rho_v, double* rho_l) {
+    if (!eos || !rho_v || !rho_l) return fail(LB_E_INVAL, "null argument");
+    if (!(eos->a > 0 && eos->b > 0 && eos->R > 0)) return fail(LB_E_INVAL, "EOS needs a, b, R > 0");
+    return maxwell(Pr(*eos), T, rho_v, rho_l);
+}
+
+int lb_initial_density(const lb_grid* grid, const lb_eos* eos, const lb_thermal* th, float* rho0) {
+    int rc = validate(grid, eos, th);
+    if (rc) return rc;
+    if (!rho0) return fail(LB_E_INVAL, "null output");
+    Pr pr(*eos);
+    double rv, rl;
+    rc = maxwell(pr, th->Ts_over_Tc * pr.Tc, &rv, &rl);
+    if (rc) return rc;
+    pool(grid->Lx, grid->Ly, rl, rv, th->pool_height, th->noise_amp, th->seed, rho0);
+    return LB_OK;
+}
+
+int lb_workspace_bytes(const lb_grid* grid, size_t* bytes) {
+    if (!grid || !bytes) return fail(LB_E_INVAL, "null argument");
+    if (grid->Lx < 1 || grid->Ly < 3) return fail(LB_E_INVAL, "grid %dx%d: need Lx >= 1, Ly >= 3", grid->Lx, grid->Ly);
+    *bytes = layout(grid).total;
+    return LB_OK;
+}
+
+int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_thermal* th,
+            const double* Tb_profile, double superheat, double Gw, const float* rho0, void* dev_workspace,
+            size_t workspace_bytes, void* stream) {
+    if (!out) return fail(LB_E_INVAL, "null handle pointer");
+    *out = nullptr;
+    int rc = validate(grid, eos, th);
+    if (rc) return rc;
+    const Layout lay = layout(grid);
+    if (!dev_workspace || workspace_bytes < lay.total)
+        return fail(LB_E_INVAL, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, lay.total);
+    if (((uintptr_t)dev_workspace) & 255) return fail(LB_E_INVAL, "workspace must be 256-byte aligned");
+    if (!std::isfinite(superheat) || !std::isfinite(Gw)) return fail(LB_E_INVAL, "non-finite superheat or Gw");
+
+    lb_handle* h = new lb_handle();
+    h->grid = *grid;
+    h->eos = *eos;
+    h->th = *th;
+    Pr pr(*eos);
+    h->Tc = pr.Tc;
+    h->Ts = th->Ts_over_Tc * pr.Tc;
+    rc = maxwell(pr, h->Ts, &h->rho_v, &h->rho_l);
+    if (rc) { release(h); return rc; }
+    h->Gw = Gw;
+    h->superheat = superheat;
+    if (Tb_profile) h->profile.assign(Tb_profile, Tb_profile + grid->Lx);
+    h->lay = lay;
+    h->ws = (char*)dev_workspace;
+    h->f[0] = (float*)(h->ws + lay.f0);
+    h->f[1] = (float*)(h->ws + lay.f1);
+    h->t[0] = (float*)(h->ws + lay.t0);
+    h->t[1] = (float*)(h->ws + lay.t1);
+    h->thb = (float*)(h->ws + lay.thb);
+    h->acc = (Acc*)(h->ws + lay.acc);
+    h->cur = 0;
+    h->st = (cudaStream_t)stream;
+    h->steps = 0;
+    h->wall_pinned = nullptr;
+    h->wall_done = nullptr;
+    h->wall_pending = false;
+    {
+        cudaError_t e0 = cudaMallocHost((void**)&h->wall_pinned, grid->Lx * sizeof(float));
+        if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&h->wall_done, cudaEventDisableTiming);
+        if (e0 != cudaSuccess) {
+            release(h);
+            return cuda_fail(e0, "wall staging");
+        }
+    }
+
+    const int Lx = grid->Lx, Ly = grid->Ly;
+    std::vector<float> r0;
+    const float* src = rho0;
+    if (!src) {
+        r0.resize((size_t)Lx * Ly);
+        pool(Lx, Ly, h->rho_l, h->rho_v, th->pool_height, th->noise_amp, th->seed, r0.data());
+        src = r0.data();
+    }
+    double sum = 0.0;
+    for (size_t i = 0; i < (size_t)Lx * Ly; ++i) {
+        if (!std::isfinite(src[i]) || src[i] <= 0.f) {
+            release(h);
+            return fail(LB_E_INVAL, "initial density must be finite and > 0 (cell %zu)", i);
+        }
+        sum += src[i];
+    }
+    h->rho_ave = sum / ((double)Lx * Ly);
+    fill_params(h);
+    rc = choose_launch(h, 0, 0);
+    if (rc) { release(h); return rc; }
+    cudaError_t e = step_prepare(1024);
+    if (e != cudaSuccess) { release(h); return cuda_fail(e, "cudaFuncSetAttribute"); }
+
+    auto bail = [&](cudaError_t err, const char* what) { release(h); return cuda_fail(err, what); };
+    if ((e = cudaMemsetAsync(h->acc, 0, sizeof(Acc), h->st)) != cudaSuccess) return bail(e, "clear accumulators");
+    if ((rc = upload_wall(h))) { release(h); return rc; }
+    // rho0 goes through the second population buffer as a pitched scratch
+    if ((e = cudaMemcpy2DAsync(h->f[1], lay.pitch * sizeof(float), src, Lx * sizeof(float), Lx * sizeof(float), Ly,
+                               cudaMemcpyHostToDevice, h->st)) != cudaSuccess)
+        return bail(e, "upload rho0");
+    StepParams P = h->base;
+    if ((e = launch_init(P, h->f[1], h->f[0], h->t[0], h->st)) != cudaSuccess) return bail(e, "init kernel");
+    if ((e = cudaStreamSynchronize(h->st)) != cudaSuccess) return bail(e, "lb_init synchronize");
+    *out = h;
+    return LB_OK;
+}
+
+int lb_step(lb_handle* h, int nsteps) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (nsteps < 0) return fail(LB_E_INVAL, "nsteps must be >= 0");
+    for (int n = 0; n < nsteps; ++n) {
+        StepParams P = h->base;
+        P.f_in = h->f[h->cur];
+        P.f_out = h->f[1 - h->cur];
+        P.th_in = h->t[h->cur];
+        P.th_out = h->t[1 - h->cur];
+        LB_CUDA(launch_step(P, h->launch, h->st), "step launch");
+        h->cur ^= 1;
+        h->steps++;
+    }
+    return LB_OK;
+}
+
+int lb_set_wall_temperature(lb_handle* h, const double* Tb_profile, double superheat) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (!std::isfinite(superheat)) return fail(LB_E_INVAL, "non-finite superheat");
+    h->superheat = superheat;
+    if (Tb_profile) h->profile.assign(Tb_profile, Tb_profile + h->grid.Lx);
+    else h->profile.clear();
+    int rc = upload_wall(h);
+    if (rc) return rc;
+    if (h->grid.bc_y != LB_BC_PERIODIC)
+        LB_CUDA(cudaMemcpyAsync(h->t[h->cur], h->thb, h->grid.Lx * sizeof(float), cudaMemcpyDeviceToDevice, h->st),
+                "wall row update");
+    return LB_OK;
+}
+
+int lb_set_wettability(lb_handle* h, double Gw) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (!std::isfinite(Gw)) return fail(LB_E_INVAL, "non-finite Gw");
+    h->Gw = Gw;
+    h->base.gw6 = (float)(Gw / 6.0);
+    return LB_OK;
+}
+
+int lb_heat_flux(lb_handle* h, double* q_inst, double* q_mean, double* q_std, int64_t* nsamples, int reset) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    Acc a;
+    LB_CUDA(cudaMemcpyAsync(&a, h->acc, sizeof(Acc), cudaMemcpyDeviceToHost, h->st), "read accumulators");
+    int rc = check_device_errors(h);
+    const double n = a.q_n;
+    const double mean = n > 0 ? a.q_sum / n : 0.0;
+    const double var = n > 1 ? std::max(0.0, (a.q_sum2 - n * mean * mean) / (n - 1)) : 0.0;
+    if (q_inst) *q_inst = a.q_last;
+    if (q_mean) *q_mean = mean;
+    if (q_std) *q_std = std::sqrt(var);
+    if (nsamples) *nsamples = (int64_t)n;
+    if (reset) {
+        LB_CUDA(cudaMemsetAsync(&h->acc->q_sum, 0, 3 * sizeof(double), h->st), "reset accumulators");
+        LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    }
+    return rc;
+}
+
+int lb_fields(lb_handle* h, float* rho, float* ux, float* uy, float* T, int on_device) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    StepParams P = h->base;
+    P.f_in = h->f[h->cur];
+    P.th_in = h->t[h->cur];
+    float* scr = h->f[1 - h->cur];
+    const int Lx = h->grid.Lx, Ly = h->grid.Ly, pitch = h->lay.pitch;
+    const size_t pl = h->lay.plane;
+    if (on_device) {
+        LB_CUDA(launch_macro(P, scr, rho, ux, uy, T, Lx, h->st), "fields kernel");
+        return check_device_errors(h);
+    }
+    float* o[4] = {rho ? scr + 4 * pl : nullptr, ux ? scr + 5 * pl : nullptr, uy ? scr + 6 * pl : nullptr,
+                   T ? scr + 7 * pl : nullptr};
+    LB_CUDA(launch_macro(P, scr, o[0], o[1], o[2], o[3], pitch, h->st), "fields kernel");
+    float* dst[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k])
+            LB_CUDA(cudaMemcpy2DAsync(dst[k], Lx * sizeof(float), o[k], pitch * sizeof(float), Lx * sizeof(float), Ly,
+                                      cudaMemcpyDeviceToHost, h->st),
+                    "fields read-back");
+    return check_device_errors(h);
+}
+
+int lb_get_state(lb_handle* h, float* fpost, float* theta, int on_device) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    const int Lx = h->grid.Lx, Ly = h->grid.Ly, pitch = h->lay.pitch;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (fpost)
+        LB_CUDA(cudaMemcpy2DAsync(fpost, Lx * sizeof(float), h->f[h->cur], pitch * sizeof(float), Lx * sizeof(float),
+                                  9 * Ly, k, h->st),
+                "populations read-back");
+    if (theta)
+        LB_CUDA(cudaMemcpy2DAsync(theta, Lx * sizeof(float), h->t[h->cur], pitch * sizeof(float), Lx * sizeof(float),
+                                  Ly, k, h->st),
+                "temperature read-back");
+    return check_device_errors(h);
+}
+
+int lb_set_state(lb_handle* h, const float* fpost, const float* theta, int on_device) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    const int Lx = h->grid.Lx, Ly = h->grid.Ly, pitch = h->lay.pitch;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (fpost)
+        LB_CUDA(cudaMemcpy2DAsync(h->f[h->cur], pitch * sizeof(float), fpost, Lx * sizeof(float), Lx * sizeof(float),
+                                  9 * Ly, k, h->st),
+                "populations upload");
+    if (theta)
+        LB_CUDA(cudaMemcpy2DAsync(h->t[h->cur], pitch * sizeof(float), theta, Lx * sizeof(float), Lx * sizeof(float),
+                                  Ly, k, h->st),
+                "temperature upload");
+    if (!on_device) LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_mass(lb_handle* h, double* mass) {
+    if (!h || !mass) return fail(LB_E_INVAL, "null argument");
+    StepParams P = h->base;
+    LB_CUDA(launch_mass(P, h->f[h->cur], h->st), "mass kernel");
+    LB_CUDA(cudaMemcpyAsync(mass, &h->acc->mass, sizeof(double), cudaMemcpyDeviceToHost, h->st), "mass read-back");
+    return check_device_errors(h);
+}
+
+int lb_sync(lb_handle* h) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    return check_device_errors(h);
+}
+
+int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblocks) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (steps) *steps = h->steps;
+    if (block_x) *block_x = h->launch.block_x;
+    if (seg_rows) *seg_rows = h->launch.seg_rows;
+    if (nblocks) *nblocks = h->launch.nstrips * h->launch.nseg;
+    return LB_OK;
+}
+
+int lb_set_launch(lb_handle* h, int block_x, int seg_rows) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (seg_rows < 0) return fail(LB_E_INVAL, "seg_rows must be >= 0");
+    return choose_launch(h, block_x, seg_rows);
+}
+
+namespace {
+struct SaveHeader {
+    char magic[8];
+    int32_t Lx, Ly;
+    int64_t steps;
+    double superheat, Gw;
+    int32_t has_profile, pad;
+};
+}  // namespace
+
+int lb_save_bytes(lb_handle* h, size_t* bytes) {
+    if (!h || !bytes) return fail(LB_E_INVAL, "null argument");
+    const size_t cells = (size_t)h->grid.Lx * h->grid.Ly;
+    *bytes = sizeof(SaveHeader) + sizeof(Acc) + 10 * cells * sizeof(float) + h->grid.Lx * sizeof(double);
+    return LB_OK;
+}
+
+int lb_save(lb_handle* h, void* host_buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lb_save_bytes(h, &need);
+    if (rc) return rc;
+    if (!host_buf || bytes < need) return fail(LB_E_INVAL, "save buffer of %zu bytes < %zu", bytes, need);
+    char* p = (char*)host_buf;
+    SaveHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LBBOIL1", 8);
+    hd.Lx = h->grid.Lx;
+    hd.Ly = h->grid.Ly;
+    hd.steps = h->steps;
+    hd.superheat = h->superheat;
+    hd.Gw = h->Gw;
+    hd.has_profile = h->profile.empty() ? 0 : 1;
+    memcpy(p, &hd, sizeof(hd));
+    p += sizeof(hd);
+    LB_CUDA(cudaMemcpyAsync(p, h->acc, sizeof(Acc), cudaMemcpyDeviceToHost, h->st), "save accumulators");
+    p += sizeof(Acc);
+    const size_t cells = (size_t)h->grid.Lx * h->grid.Ly;
+    rc = lb_get_state(h, (float*)p, (float*)p + 9 * cells, 0);
+    if (rc) return rc;
+    p += 10 * cells * sizeof(float);
+    for (int x = 0; x < h->grid.Lx; ++x) ((double*)p)[x] = h->profile.empty() ? 0.0 : h->profile[x];
+    return LB_OK;
+}
+
+int lb_load(lb_handle* h, const void* host_buf, size_t bytes) {
+    size_t need = 0;
+    int rc = lb_save_bytes(h, &need);
+    if (rc) return rc;
+    if (!host_buf || bytes < need) return fail(LB_E_INVAL, "load buffer of %zu bytes < %zu", bytes, need);
+    const char* p = (const char*)host_buf;
+    SaveHeader hd;
+    memcpy(&hd, p, sizeof(hd));
+    if (memcmp(hd.magic, "LBBOIL1", 8) != 0 || hd.Lx != h->grid.Lx || hd.Ly != h->grid.Ly)
+        return fail(LB_E_INVAL, "checkpoint does not match this grid");
+    p += sizeof(hd);
+    Acc a;
+    memcpy(&a, p, sizeof(Acc));
+    a.err = 0;
+    a.count = 0;
+    a.q_partial = 0.0;
+    LB_CUDA(cudaMemcpyAsync(h->acc, &a, sizeof(Acc), cudaMemcpyHostToDevice, h->st), "load accumulators");
+    p += sizeof(Acc);
+    const size_t cells = (size_t)h->grid.Lx * h->grid.Ly;
+    rc = lb_set_state(h, (const float*)p, (const float*)p + 9 * cells, 0);
+    if (rc) return rc;
+    p += 10 * cells * sizeof(float);
+    h->steps = hd.steps;
+    h->Gw = hd.Gw;
+    h->base.gw6 = (float)(hd.Gw / 6.0);
+    h->superheat = hd.superheat;
+    if (hd.has_profile) h->profile.assign((const double*)p, (const double*)p + h->grid.Lx);
+    else h->profile.clear();
+    rc = upload_wall(h);
+    if (rc) return rc;
+    LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_destroy(lb_handle* h) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    release(h);
+    return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,34 @@
+// Host-side declarations shared by the translation units of liblbboil.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lb_device.cuh"
+
+namespace lbgpu {
+
+// Launch shape of the fused step: block_x threads per block (block_x - 2*HALO
+// output columns), seg_rows rows per block, nstrips x nseg blocks.
+struct Launch {
+    int block_x, seg_rows, nstrips, nseg;
+};
+
+size_t step_smem_bytes(int block_x);
+cudaError_t step_prepare(int block_x);  // opt in to the dynamic shared memory
+cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
+int step_occupancy(int block_x, int* blocks_per_sm);
+
+// Initial state: f* = w_a rho0 (rest equilibrium), theta = 0 with the wall
+// rows at their Dirichlet values. rho0 is pitched [Ly][pitch].
+cudaError_t launch_init(const StepParams& P, const float* rho0, float* f, float* th, cudaStream_t st);
+
+// Macroscopic fields (rho, u with the level's forces, T) into outputs with
+// row stride ostride; scratch holds 4 pitched planes.
+cudaError_t launch_macro(const StepParams& P, float* scratch, float* rho, float* ux, float* uy,
+                         float* T, int ostride, cudaStream_t st);
+
+// acc->mass = sum over cells and directions of f (FP64).
+cudaError_t launch_mass(const StepParams& P, const float* f, cudaStream_t st);
+
+}  // namespace lbgpu

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of the C ABI in include/lb.h (argument marshalling only).
+
+Every step of the boiling model runs in the CUDA kernels of liblbboil.so;
+PyTorch supplies the device workspace and the stream. If the library is
+missing the import of this module fails loudly: there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblbboil.so")
+
+LB_OK = 0
+ERRORS = {-1: "LB_E_INVAL", -2: "LB_E_CUDA", -3: "LB_E_EOS_DOMAIN", -4: "LB_E_NONFINITE", -5: "LB_E_TIMEOUT"}
+BC_WALLS, BC_TOP_OUTFLOW, BC_PERIODIC = 0, 1, 2
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lb_grid(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32), ("bc_y", C.c_int32), ("ghost_layer", C.c_int32),
+                ("isothermal", C.c_int32), ("reserved", C.c_int32)]
+
+
+class lb_eos(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("a", "b", "R", "omega", "G", "sigma")]
+
+
+class lb_thermal(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("Ts_over_Tc", "cv", "cv_chi", "g", "nu_l", "nu_v", "s_e", "s_zeta",
+                                          "s_q", "pool_height", "noise_amp")] + [("seed", C.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_1501_03857_gb300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, SZ = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    DP, FP, I64P = C.POINTER(C.c_double), C.c_void_p, C.POINTER(C.c_int64)
+    sig = {
+        "lb_critical_temperature": [C.POINTER(lb_eos), DP],
+        "lb_coexistence": [C.POINTER(lb_eos), D, DP, DP],
+        "lb_initial_density": [C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), FP],
+        "lb_workspace_bytes": [C.POINTER(lb_grid), C.POINTER(C.c_size_t)],
+        "lb_init": [C.POINTER(P), C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), P, D, D, P, P, SZ, P],
+        "lb_step": [P, I],
+        "lb_set_wall_temperature": [P, P, D],
+        "lb_set_wettability": [P, D],
+        "lb_heat_flux": [P, DP, DP, DP, I64P, I],
+        "lb_fields": [P, FP, FP, FP, FP, I],
+        "lb_get_state": [P, FP, FP, I],
+        "lb_set_state": [P, FP, FP, I],
+        "lb_mass": [P, DP],
+        "lb_sync": [P],
+        "lb_info": [P, I64P, C.POINTER(I), C.POINTER(I), C.POINTER(I)],
+        "lb_set_launch": [P, I, I],
+        "lb_save_bytes": [P, C.POINTER(C.c_size_t)],
+        "lb_save": [P, P, SZ],
+        "lb_load": [P, P, SZ],
+        "lb_destroy": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.lb_last_error.argtypes = []
+    lib.lb_last_error.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def check(rc: int):
+    if rc != LB_OK:
+        raise LBError(rc, lib.lb_last_error().decode())
+    return rc
+
+
+@dataclasses.dataclass
+class Config:
+    """Grid, EOS and thermal parameters; defaults are the paper's (Sec. 3.1,
+    after Eq. 21) on a 600 x 150 domain with the pool up to y = 90."""
+    Lx: int = 600
+    Ly: int = 150
+    bc_y: int = BC_WALLS
+    ghost_layer: bool = False
+    isothermal: bool = False
+    a: float = 3.0 / 49.0
+    b: float = 2.0 / 21.0
+    R: float = 1.0
+    omega: float = 0.344
+    G: float = -1.0
+    sigma: float = 1.2
+    Ts_over_Tc: float = 0.86
+    cv: float = 6.0
+    cv_chi: float = 0.028
+    g: float = 3e-5
+    nu_l: float = 0.1
+    nu_v: float = 0.5 / 3.0
+    s_e: float = 0.8
+    s_zeta: float = 0.8
+    s_q: float = 1.1
+    pool_height: float = 90.0
+    noise_amp: float = 1e-4
+    seed: int = 1
+
+    def structs(self):
+        g = lb_grid(self.Lx, self.Ly, self.bc_y, int(self.ghost_layer), int(self.isothermal), 0)
+        e = lb_eos(self.a, self.b, self.R, self.omega, self.G, self.sigma)
+        t = lb_thermal(self.Ts_over_Tc, self.cv, self.cv_chi, self.g, self.nu_l, self.nu_v, self.s_e, self.s_zeta,
+                       self.s_q, self.pool_height, self.noise_amp, self.seed)
+        return g, e, t
+
+
+def critical_temperature(cfg: Config) -> float:
+    _, e, _ = cfg.structs()
+    out = C.c_double()
+    check(lib.lb_critical_temperature(C.byref(e), C.byref(out)))
+    return out.value
+
+
+def coexistence(cfg: Config, T: Optional[float] = None):
+    _, e, _ = cfg.structs()
+    if T is None:
+        T = cfg.Ts_over_Tc * critical_temperature(cfg)
+    rv, rl = C.c_double(), C.c_double()
+    check(lib.lb_coexistence(C.byref(e), T, C.byref(rv), C.byref(rl)))
+    return rv.value, rl.value
+
+
+def initial_density(cfg: Config) -> np.ndarray:
+    g, e, t = cfg.structs()
+    out = np.empty((cfg.Ly, cfg.Lx), dtype=np.float32)
+    check(lib.lb_initial_density(C.byref(g), C.byref(e), C.byref(t), out.ctypes.data))
+    return out
+
+
+def workspace_bytes(cfg: Config) -> int:
+    g, _, _ = cfg.structs()
+    n = C.c_size_t()
+    check(lib.lb_workspace_bytes(C.byref(g), C.byref(n)))
+    return n.value
+
+
+def _host_ptr(a: Optional[np.ndarray], dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data
+
+
+class Simulation:
+    """One boiling domain on the current CUDA device.
+
+    cfg: Config; superheat: T_b - T_s on the bottom wall (plus an optional
+    per-x profile); Gw: Eq. 22's wettability strength; rho0: optional initial
+    density [Ly, Lx] (host array). Device memory is a torch uint8 tensor owned
+    by this object; work runs on `stream` (default: torch's current stream)."""
+
+    def __init__(self, cfg: Config, superheat: float = 0.0, Gw: float = 0.0, profile=None, rho0=None,
+                 stream=None):
+        import torch
+        self.cfg = cfg
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nbytes = workspace_bytes(cfg)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        self._ws = base + ((-base) % 256)
+        g, e, t = cfg.structs()
+        prof, pp = _host_ptr(profile, np.float64)
+        r0, rp = _host_ptr(rho0, np.float32)
+        h = C.c_void_p()
+        check(lib.lb_init(C.byref(h), C.byref(g), C.byref(e), C.byref(t), pp, float(superheat), float(Gw), rp,
+                          self._ws, nbytes, self.stream.cuda_stream))
+        self.h = h
+        self.Lx, self.Ly = cfg.Lx, cfg.Ly
+
+    # -- stepping -----------------------------------------------------------
+    def step(self, n: int = 1):
+        check(lib.lb_step(self.h, int(n)))
+
+    def set_wall_temperature(self, superheat: float, profile=None):
+        prof, pp = _host_ptr(profile, np.float64)
+        check(lib.lb_set_wall_temperature(self.h, pp, float(superheat)))
+
+    def set_wettability(self, Gw: float):
+        check(lib.lb_set_wettability(self.h, float(Gw)))
+
+    def set_launch(self, block_x: int = 0, seg_rows: int = 0):
+        check(lib.lb_set_launch(self.h, int(block_x), int(seg_rows)))
+
+    def info(self):
+        st, bx, sr, nb = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        check(lib.lb_info(self.h, C.byref(st), C.byref(bx), C.byref(sr), C.byref(nb)))
+        return {"steps": st.value, "block_x": bx.value, "seg_rows": sr.value, "blocks": nb.value}
+
+    # -- read-back ----------------------------------------------------------
+    def heat_flux(self, reset: bool = False):
+        qi, qm, qs, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+        check(lib.lb_heat_flux(self.h, C.byref(qi), C.byref(qm), C.byref(qs), C.byref(n), int(reset)))
+        return {"q_inst": qi.value, "q_mean": qm.value, "q_std": qs.value, "n": n.value}
+
+    def fields(self):
+        out = [np.empty((self.Ly, self.Lx), dtype=np.float32) for _ in range(4)]
+        check(lib.lb_fields(self.h, *[o.ctypes.data for o in out], 0))
+        return dict(zip(("rho", "ux", "uy", "T"), out))
+
+    def fields_device(self, rho, ux, uy, T):
+        ptr = lambda t: None if t is None else t.data_ptr()
+        check(lib.lb_fields(self.h, ptr(rho), ptr(ux), ptr(uy), ptr(T), 1))
+
+    def get_state(self):
+        f = np.empty((9, self.Ly, self.Lx), dtype=np.float32)
+        th = np.empty((self.Ly, self.Lx), dtype=np.float32)
+        check(lib.lb_get_state(self.h, f.ctypes.data, th.ctypes.data, 0))
+        return f, th
+
+    def set_state(self, fpost=None, theta=None):
+        f, fp = _host_ptr(fpost, np.float32)
+        t, tp = _host_ptr(theta, np.float32)
+        check(lib.lb_set_state(self.h, fp, tp, 0))
+
+    def mass(self) -> float:
+        m = C.c_double()
+        check(lib.lb_mass(self.h, C.byref(m)))
+        return m.value
+
+    def sync(self):
+        check(lib.lb_sync(self.h))
+
+    def save(self) -> bytes:
+        n = C.c_size_t()
+        check(lib.lb_save_bytes(self.h, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        check(lib.lb_save(self.h, buf, n.value))
+        return buf.raw
+
+    def load(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        check(lib.lb_load(self.h, buf, len(blob)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,99 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol that
+include/lb.h declares, and its host-only entry points (FP64 thermodynamics,
+initial pool, validation, workspace layout) agree with the oracle and the
+input generator."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1501_03857_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lb():
+    from paper_1501_03857_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    from paper_1501_03857_gb300 import lb as lbmod
+    return lbmod
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lb):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lb.lib, n), n
+
+
+def test_critical_temperature_matches_oracle(lb):
+    for a in (3 / 49, 2 / 49):
+        cfg = lb.Config(a=a)
+        assert abs(lb.critical_temperature(cfg) - O.critical_temperature(a, cfg.b, cfg.R)) < 1e-15
+
+
+@pytest.mark.parametrize("a,tr", [(3 / 49, 0.86), (2 / 49, 0.86), (3 / 49, 0.7), (3 / 49, 0.95)])
+def test_coexistence_matches_oracle(lb, a, tr):
+    cfg = lb.Config(a=a, Ts_over_Tc=tr)
+    T = tr * lb.critical_temperature(cfg)
+    rv, rl = lb.coexistence(cfg)
+    orv, orl = O.maxwell_coexistence(a, cfg.b, cfg.R, cfg.omega, T)
+    assert abs(rv / orv - 1) < 1e-10 and abs(rl / orl - 1) < 1e-10
+
+
+def test_initial_density_matches_input_generator(lb):
+    cfg = lb.Config(Lx=37, Ly=23, pool_height=9.5, noise_amp=1e-4, seed=7)
+    got = lb.initial_density(cfg)
+    rv, rl = lb.coexistence(cfg)
+    want = inputs.pool_density(37, 23, rl, rv, 9.5, noise_amp=1e-4, seed=7)
+    assert got.shape == want.shape
+    ulp = np.abs(got.view(np.int32).astype(np.int64) - want.view(np.int32).astype(np.int64))
+    assert ulp.max() <= 1
+
+
+def test_workspace_layout_grows_with_grid(lb):
+    small = lb.workspace_bytes(lb.Config(Lx=10, Ly=10))
+    big = lb.workspace_bytes(lb.Config(Lx=4096, Ly=4096))
+    assert big >= 2 * 10 * 4096 * 4096 * 4  # two copies of 9 populations + theta
+    assert small % 256 == 0 and big % 256 == 0
+
+
+@pytest.mark.parametrize("kw", [dict(Lx=0), dict(Ly=2), dict(bc_y=7), dict(G=1.0), dict(s_e=2.0),
+                                dict(Ts_over_Tc=1.2), dict(nu_l=0.0)])
+def test_invalid_parameters_rejected_before_any_device_call(lb, kw):
+    cfg = lb.Config(Lx=16, Ly=16)
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    g, e, t = cfg.structs()
+    import ctypes as C
+    h = C.c_void_p()
+    rc = lb.lib.lb_init(C.byref(h), C.byref(g), C.byref(e), C.byref(t), None, 0.0, 0.0, None, None, 0, None)
+    assert rc == -1
+    assert lb.lib.lb_last_error().decode()
+
+
+def test_workspace_too_small_rejected(lb):
+    import ctypes as C
+    cfg = lb.Config(Lx=16, Ly=16)
+    g, e, t = cfg.structs()
+    h = C.c_void_p()
+    rc = lb.lib.lb_init(C.byref(h), C.byref(g), C.byref(e), C.byref(t), None, 0.0, 0.0, None,
+                        C.c_void_p(256), 10, None)
+    assert rc == -1 and "workspace" in lb.lib.lb_last_error().decode()
+
+
+def test_null_handle_calls_fail_cleanly(lb):
+    assert lb.lib.lb_step(None, 1) == -1
+    assert lb.lib.lb_sync(None) == -1
+    assert lb.lib.lb_destroy(None) == -1

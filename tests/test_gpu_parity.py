@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA step, called through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (normalised max-norm error, max|gpu - oracle| / max|oracle| per
+field) follow from FP32 storage and arithmetic: one step from an FP32 state
+carries a few ulp (2^-24 ~ 6e-8) of rounding per operation through about a
+hundred dependent operations, so 2e-6; after 200 steps the benchmark spec's bound
+1e-5 applies.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1501_03857_gb300 import inputs
+from parity_util import norm_err, oracle_fields, oracle_initial_fp32, oracle_params, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL_ONE_STEP = 2e-6
+TOL_200 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lb():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1501_03857_gb300 import lb as lbmod
+    return lbmod
+
+
+def coex(lb, cfg):
+    return lb.coexistence(cfg)
+
+
+CASES = [
+    # (Lx, Ly, bc, ghost, Gw, isothermal)
+    (8, 6, 0, False, 0.0, False),
+    (33, 17, 0, False, 0.08, False),
+    (33, 17, 1, False, 0.0, False),
+    (33, 17, 2, False, 0.0, False),
+    (40, 12, 0, True, 0.0, False),
+    (21, 9, 0, False, 0.0, True),
+    (300, 70, 0, False, 0.105, False),
+    (517, 41, 1, False, 0.065, False),
+]
+
+
+@pytest.mark.parametrize("Lx,Ly,bc,ghost,Gw,iso", CASES)
+def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso):
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, ghost_layer=ghost, isothermal=iso)
+    rv, rl = coex(lb, cfg)
+    rho0, f0, th0 = inputs.random_state(Lx, Ly, rl, rv, Ly * 0.45, seed=Lx * 1000 + Ly)
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=Gw, rho0=rho0)
+    sim.set_launch(0, 5)  # several segments even on small grids
+    sim.set_state(f0, th0)
+    sim.step(1)
+    fg, tg = sim.get_state()
+    P = oracle_params(cfg, rho0, superheat=0.012, Gw=Gw)
+    fr, tr, qs = run_oracle(f0, th0, P, 1)
+    assert norm_err(fg, fr.numpy()) < TOL_ONE_STEP
+    assert norm_err(tg, tr.numpy()) < TOL_ONE_STEP
+    if bc != 2:
+        h = sim.heat_flux()
+        assert h["n"] == 1
+        assert abs(h["q_inst"] - qs[0]) <= 1e-5 * abs(qs[0]) + 1e-12
+
+
+def config1(lb, outflow=True):
+    """100 x 100 pool, a = 2/49, superheat 0.1 Tc, pool to y = 40, noise 1e-4,
+    seed 1, g = 3e-5 (the small FP64 configuration)."""
+    cfg = lb.Config(Lx=100, Ly=100, a=2 / 49, bc_y=1 if outflow else 0, pool_height=40.0, noise_amp=1e-4, seed=1)
+    Tc = lb.critical_temperature(cfg)
+    return cfg, 0.1 * Tc
+
+
+@pytest.mark.parametrize("outflow", [True, False])
+def test_200_steps_config1(lb, outflow):
+    cfg, sh = config1(lb, outflow)
+    rv, rl = coex(lb, cfg)
+    rho0 = inputs.pool_density(cfg.Lx, cfg.Ly, rl, rv, cfg.pool_height, noise_amp=cfg.noise_amp, seed=cfg.seed)
+    P = oracle_params(cfg, rho0, superheat=sh)
+    f0, th0 = oracle_initial_fp32(rho0, P)
+    sim = lb.Simulation(cfg, superheat=sh, rho0=rho0)
+    sim.set_state(f0, th0)
+    sim.step(200)
+    fg, tg = sim.get_state()
+    fr, tr, qs = run_oracle(f0, th0, P, 200)
+    errs = {"f": norm_err(fg, fr.numpy()), "theta": norm_err(tg, tr.numpy())}
+    fl = sim.fields()
+    rr, vxr, vyr, Tr = oracle_fields(fr, tr, P)
+    errs.update(rho=norm_err(fl["rho"], rr), ux=norm_err(fl["ux"], vxr), uy=norm_err(fl["uy"], vyr))
+    for k, v in errs.items():
+        assert v < TOL_200, (k, v, errs)
+    h = sim.heat_flux()
+    assert h["n"] == 200
+    assert abs(h["q_mean"] / np.mean(qs) - 1) < 1e-5
+
+
+def test_launch_shape_does_not_change_results(lb):
+    cfg = lb.Config(Lx=263, Ly=57, bc_y=0)
+    rv, rl = coex(lb, cfg)
+    rho0, f0, th0 = inputs.random_state(cfg.Lx, cfg.Ly, rl, rv, 25, seed=5)
+    ref = None
+    for bx, seg in ((0, 0), (64, 1), (96, 7), (256, 57), (512, 3), (128, 1000)):
+        sim = lb.Simulation(cfg, superheat=0.01, Gw=0.05, rho0=rho0)
+        sim.set_launch(bx, seg)
+        sim.set_state(f0, th0)
+        sim.step(3)
+        fg, tg = sim.get_state()
+        if ref is None:
+            ref = (fg, tg)
+        else:
+            assert np.array_equal(fg, ref[0]) and np.array_equal(tg, ref[1]), (bx, seg)
+
+
+def test_fields_and_mass_match_oracle(lb):
+    cfg = lb.Config(Lx=64, Ly=48, bc_y=0, pool_height=20)
+    rv, rl = coex(lb, cfg)
+    rho0, f0, th0 = inputs.random_state(cfg.Lx, cfg.Ly, rl, rv, 20, seed=9)
+    sim = lb.Simulation(cfg, superheat=0.01, Gw=0.1, rho0=rho0)
+    sim.set_state(f0, th0)
+    fl = sim.fields()
+    P = oracle_params(cfg, rho0, superheat=0.01, Gw=0.1)
+    rr, vxr, vyr, Tr = oracle_fields(torch.tensor(f0, dtype=torch.float64), torch.tensor(th0, dtype=torch.float64), P)
+    assert norm_err(fl["rho"], rr) < TOL_ONE_STEP
+    assert norm_err(fl["ux"], vxr) < 1e-5
+    assert norm_err(fl["uy"], vyr) < 1e-5
+    assert norm_err(fl["T"], Tr) < 1e-6
+    assert abs(sim.mass() / float(np.asarray(f0, np.float64).sum()) - 1) < 1e-12
+
+
+def test_mass_conserved_periodic(lb):
+    """Fully periodic: mass is conserved to FP32 rounding (FP64 sum)."""
+    cfg = lb.Config(Lx=128, Ly=96, bc_y=2, g=0.0)
+    rv, rl = coex(lb, cfg)
+    rho0 = inputs.droplet_density(128, 96, rl, rv, 20, noise_amp=1e-3, seed=2)
+    sim = lb.Simulation(cfg, rho0=rho0)
+    m0 = sim.mass()
+    sim.step(2000)
+    sim.sync()
+    assert abs(sim.mass() / m0 - 1) < 1e-5
+
+
+def test_eos_domain_and_nonfinite_flags(lb):
+    cfg = lb.Config(Lx=16, Ly=8, bc_y=2)
+    rv, rl = coex(lb, cfg)
+    rho0 = np.full((8, 16), rl, dtype=np.float32)
+    sim = lb.Simulation(cfg, rho0=rho0)
+    f, th = sim.get_state()
+    f2 = f.copy()
+    f2[:, 3, 4] *= 9.9 / rl  # density beyond the EOS limit -> psi argument < 0
+    sim.set_state(f2, th)
+    sim.step(1)
+    with pytest.raises(lb.LBError) as ei:
+        sim.sync()
+    assert ei.value.code == -3
+    sim.sync()  # the flag was cleared by the report
+    f3 = f.copy()
+    f3[0, 2, 2] = np.nan
+    sim.set_state(f3, th)
+    sim.step(1)
+    with pytest.raises(lb.LBError) as ei:
+        sim.sync()
+    assert ei.value.code == -4
+
+
+def test_save_load_roundtrip(lb):
+    cfg = lb.Config(Lx=50, Ly=30, bc_y=0, pool_height=12)
+    sim = lb.Simulation(cfg, superheat=0.01)
+    sim.step(10)
+    blob = sim.save()
+    sim.step(5)
+    f1, t1 = sim.get_state()
+    q1 = sim.heat_flux()
+    sim.load(blob)
+    assert sim.info()["steps"] == 10
+    sim.step(5)
+    f2, t2 = sim.get_state()
+    assert np.array_equal(f1, f2) and np.array_equal(t1, t2)
+    q2 = sim.heat_flux()
+    assert q2["n"] == q1["n"] and abs(q2["q_mean"] - q1["q_mean"]) <= 1e-12 * abs(q1["q_mean"])
+
+
+def test_wall_temperature_profile_and_superheat_step(lb):
+    """Per-x wall profile and the superheat step of Sec. 3.2 match the oracle."""
+    cfg = lb.Config(Lx=40, Ly=20, bc_y=0, pool_height=10)
+    rv, rl = coex(lb, cfg)
+    rho0 = inputs.pool_density(40, 20, rl, rv, 10, noise_amp=1e-3, seed=4)
+    prof = 0.004 * np.sin(2 * math.pi * np.arange(40) / 40)
+    P = oracle_params(cfg, rho0, superheat=0.01, profile=prof)
+    f0, th0 = oracle_initial_fp32(rho0, P)
+    sim = lb.Simulation(cfg, superheat=0.01, profile=prof, rho0=rho0)
+    sim.set_state(f0, th0)
+    sim.step(20)
+    sim.set_wall_temperature(0.02, prof)
+    sim.step(20)
+    f, th, _ = run_oracle(f0, th0, P, 20)
+    P.theta_b = torch.tensor(0.02 + prof, dtype=torch.float64)
+    th = th.clone()
+    th[0] = P.theta_b
+    fr, tr, _ = run_oracle(f.numpy(), th.numpy(), P, 20)
+    fg, tg = sim.get_state()
+    assert norm_err(fg, fr.numpy()) < 1e-5
+    assert norm_err(tg, tr.numpy()) < 1e-5
+
+
+def test_full_size_sampled_rows(lb):
+    """4096 x 4096 bubble domain, one step in the benchmark's launch shape:
+    bands of rows (bottom wall, middle, top wall) against the oracle run on
+    the band alone; rows at least 7 away from a band's artificial edge depend
+    only on data inside the band."""
+    L = 4096
+    cfg = lb.Config(Lx=L, Ly=L, bc_y=0)
+    rv, rl = coex(lb, cfg)
+    rho0 = inputs.bubble_density(L, L, rl, rv, n_bubbles=256, r_min=20, r_max=60, seed=4)
+    sim = lb.Simulation(cfg, superheat=0.1 * lb.critical_temperature(cfg), Gw=0.0, rho0=rho0)
+    rho_ave = float(np.asarray(rho0, np.float64).mean())
+    P = oracle_params(cfg, None, superheat=0.1 * lb.critical_temperature(cfg), rho_ave=rho_ave)
+    # the initial state of both sides: the oracle's equilibrium of rho0, in FP32
+    f0, th0 = oracle_initial_fp32(rho0, P)
+    sim.set_state(f0, th0)
+    sim.step(1)
+    fg, tg = sim.get_state()
+    band = 16
+    for y0, bc in ((0, 0), (2000, 2), (L - band, 0)):
+        Pb = oracle_params(lb.Config(Lx=L, Ly=band, bc_y=bc), None, superheat=P.theta_b[0].item(), rho_ave=rho_ave)
+        fr, tr, qs = run_oracle(f0[:, y0:y0 + band], th0[y0:y0 + band], Pb, 1)
+        if y0 == 0:
+            rows = list(range(0, band - 7))
+            q = sim.heat_flux()["q_inst"]
+            assert abs(q - qs[0]) <= 1e-5 * abs(qs[0])
+        elif y0 == L - band:
+            rows = list(range(7, band))
+        else:
+            rows = list(range(7, band - 7))
+        assert norm_err(fg[:, y0 + rows[0]:y0 + rows[-1] + 1], fr.numpy()[:, rows[0]:rows[-1] + 1]) < TOL_ONE_STEP
+        assert norm_err(tg[y0 + rows[0]:y0 + rows[-1] + 1], tr.numpy()[rows[0]:rows[-1] + 1]) < TOL_ONE_STEP
