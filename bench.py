@@ -279,7 +279,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=4096, help="domain edge (profiling of smaller cases)")
     args = ap.parse_args()
+    global L
+    L = args.size
+    WORKLOAD["Lx"] = WORKLOAD["Ly"] = L
+    if L != 4096:
+        WORKLOAD["workload"] = WORKLOAD["workload"].replace("4096x4096", f"{L}x{L}")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

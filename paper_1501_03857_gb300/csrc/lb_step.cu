@@ -60,28 +60,28 @@ __device__ __forceinline__ float rhs_K(const Stencil& u, const Coef& k, const St
     return k.ax * u.dx + k.ay * u.dy + P.chi * u.lap - T * (k.cA - k.cB * dphi);
 }
 
-// MRT collision, Eq. 2, with the forcing moments of Eq. 8; f* = M^-1 m*
-// written to the nine output planes at offset idx.
+// MRT collision, Eq. 2, with the forcing moments of Eq. 8, written in the
+// exactly equivalent additive form f* = f + M^-1 dm with
+// dm = -Lambda (m - m^eq) + (I - Lambda/2) S. dm is small (non-equilibrium
+// moments and forces), so FP32 rounding stays at ~1 ulp of f per step and
+// mass is conserved to rounding (dm_rho = 0 exactly). The non-equilibrium
+// moments use rho v = j + F/2 (Eq. 6) in place of the rounded product.
 __device__ __forceinline__ void collide_store(const float (&f)[9], float rho, float vx, float vy,
                                               float Fx, float Fy, float Fmx, float Fmy, float psi,
                                               const StepParams& P, float* __restrict__ out, int idx) {
-    // m = M f (rows e, zeta, qx, qy, pxx, pxy; rho and j are known)
-    const float sa = f[1] + f[2] + f[3] + f[4];
-    const float sd = f[5] + f[6] + f[7] + f[8];
-    const float m1 = -4.f * f[0] - sa + 2.f * sd;
-    const float m2 = 4.f * f[0] - 2.f * sa + sd;
-    const float m4 = -2.f * (f[1] - f[3]) + (f[5] - f[6] - f[7] + f[8]);
-    const float m6 = -2.f * (f[2] - f[4]) + (f[5] + f[6] - f[7] - f[8]);
-    const float m7 = f[1] - f[2] + f[3] - f[4];
-    const float m8 = f[5] - f[6] + f[7] - f[8];
-    // m^eq, Eq. 5
+    const float sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const float sd = (f[5] + f[7]) + (f[6] + f[8]);
+    const float dxd = (f[5] - f[7]) + (f[8] - f[6]);  // sum of e_x f over diagonals
+    const float dyd = (f[5] - f[7]) + (f[6] - f[8]);  // sum of e_y f over diagonals
     const float v2 = vx * vx + vy * vy;
-    const float eq1 = rho * (-2.f + 3.f * v2);
-    const float eq2 = rho * (1.f - 3.f * v2);
-    const float eq4 = -rho * vx;
-    const float eq6 = -rho * vy;
-    const float eq7 = rho * (vx * vx - vy * vy);
-    const float eq8 = rho * vx * vy;
+    const float rv2 = rho * v2;
+    // m - m^eq (Eq. 5) for e, zeta, qx, qy, pxx, pxy
+    const float ne1 = (sa + 4.f * sd - 2.f * f[0]) - 3.f * rv2;
+    const float ne2 = 3.f * (f[0] - sa) + 3.f * rv2;
+    const float ne4 = 2.f * dxd - (f[1] - f[3]) + 0.5f * Fx;
+    const float ne6 = 2.f * dyd - (f[2] - f[4]) + 0.5f * Fy;
+    const float ne7 = ((f[1] + f[3]) - (f[2] + f[4])) - rho * (vx * vx - vy * vy);
+    const float ne8 = ((f[5] + f[7]) - (f[6] + f[8])) - rho * vx * vy;
     // S, Eq. 8
     const float vF = vx * Fx + vy * Fy;
     const float psi2 = psi * psi;
@@ -93,34 +93,33 @@ __device__ __forceinline__ void collide_store(const float (&f)[9], float rho, fl
     // tau_nu(rho): linear between the coexistence densities, clamped
     const float sfr = fminf(fmaxf((rho - P.rho_v) * P.inv_drho, 0.f), 1.f);
     const float snu = 1.f / (P.tau_v + P.dtau * sfr);
-    // m* = m - Lambda (m - m^eq) + (I - Lambda/2) S
-    const float ms1 = m1 - P.s_e * (m1 - eq1) + (1.f - 0.5f * P.s_e) * S1;
-    const float ms2 = m2 - P.s_z * (m2 - eq2) + (1.f - 0.5f * P.s_z) * S2;
-    const float ms4 = m4 - P.s_q * (m4 - eq4) - (1.f - 0.5f * P.s_q) * Fx;
-    const float ms6 = m6 - P.s_q * (m6 - eq6) - (1.f - 0.5f * P.s_q) * Fy;
-    const float ms7 = m7 - snu * (m7 - eq7) + (1.f - 0.5f * snu) * S7;
-    const float ms8 = m8 - snu * (m8 - eq8) + (1.f - 0.5f * snu) * S8;
-    const float ms3 = rho * vx + 0.5f * Fx;  // s_j = 1: j* = rho v + F/2
-    const float ms5 = rho * vy + 0.5f * Fy;
-    // f* = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
-    const float n0 = rho * (1.f / 9.f), n1 = ms1 * (1.f / 36.f), n2 = ms2 * (1.f / 36.f);
-    const float n3 = ms3 * (1.f / 6.f), n4 = ms4 * (1.f / 12.f);
-    const float n5 = ms5 * (1.f / 6.f), n6 = ms6 * (1.f / 12.f);
-    const float n7 = ms7 * 0.25f, n8 = ms8 * 0.25f;
-    const float ax_ = n0 - n1 - 2.f * n2;
-    const float dg = n0 + 2.f * n1 + n2;
+    // dm = -Lambda (m - m^eq) + (I - Lambda/2) S; with s_j = 1 and
+    // rho v = j + F/2 the momentum rows give dm_j = F.
+    const float dm1 = -P.s_e * ne1 + (1.f - 0.5f * P.s_e) * S1;
+    const float dm2 = -P.s_z * ne2 + (1.f - 0.5f * P.s_z) * S2;
+    const float dm4 = -P.s_q * ne4 - (1.f - 0.5f * P.s_q) * Fx;
+    const float dm6 = -P.s_q * ne6 - (1.f - 0.5f * P.s_q) * Fy;
+    const float dm7 = -snu * ne7 + (1.f - 0.5f * snu) * S7;
+    const float dm8 = -snu * ne8 + (1.f - 0.5f * snu) * S8;
+    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4)
+    const float n1 = dm1 * (1.f / 36.f), n2 = dm2 * (1.f / 36.f);
+    const float n3 = Fx * (1.f / 6.f), n4 = dm4 * (1.f / 12.f);
+    const float n5 = Fy * (1.f / 6.f), n6 = dm6 * (1.f / 12.f);
+    const float n7 = dm7 * 0.25f, n8 = dm8 * 0.25f;
+    const float ax_ = -n1 - 2.f * n2;
+    const float dg = 2.f * n1 + n2;
     const float cx = n3 - 2.f * n4, cy = n5 - 2.f * n6;
     const float dxx = n3 + n4, dyy = n5 + n6;
     const int pl = P.plane;
-    out[idx] = n0 - 4.f * n1 + 4.f * n2;
-    out[1 * pl + idx] = ax_ + cx + n7;
-    out[2 * pl + idx] = ax_ + cy - n7;
-    out[3 * pl + idx] = ax_ - cx + n7;
-    out[4 * pl + idx] = ax_ - cy - n7;
-    out[5 * pl + idx] = dg + dxx + dyy + n8;
-    out[6 * pl + idx] = dg - dxx + dyy - n8;
-    out[7 * pl + idx] = dg - dxx - dyy + n8;
-    out[8 * pl + idx] = dg + dxx - dyy - n8;
+    out[idx] = f[0] + (4.f * (n2 - n1));
+    out[1 * pl + idx] = f[1] + (ax_ + cx + n7);
+    out[2 * pl + idx] = f[2] + (ax_ + cy - n7);
+    out[3 * pl + idx] = f[3] + (ax_ - cx + n7);
+    out[4 * pl + idx] = f[4] + (ax_ - cy - n7);
+    out[5 * pl + idx] = f[5] + (dg + dxx + dyy + n8);
+    out[6 * pl + idx] = f[6] + (dg - dxx + dyy - n8);
+    out[7 * pl + idx] = f[7] + (dg - dxx - dyy + n8);
+    out[8 * pl + idx] = f[8] + (dg + dxx - dyy - n8);
 }
 
 }  // namespace

@@ -21,12 +21,21 @@ def oracle_params(cfg, rho0, superheat=0.0, Gw=0.0, profile=None, rho_ave=None):
     return P
 
 
-def norm_err(got, ref):
-    """max |got - ref| / max |ref| (normalised max-norm error)."""
+def norm_err(got, ref, scale=None):
+    """max |got - ref| / max |ref| (normalised max-norm error); `scale`
+    replaces max |ref| where the field's natural scale is known."""
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
-    scale = np.abs(ref).max()
+    if scale is None:
+        scale = np.abs(ref).max()
     return float(np.abs(got - ref).max() / (scale if scale > 0 else 1.0))
+
+
+def theta_err(got, ref, superheat):
+    """Temperature error relative to the temperature scale of the problem,
+    max(max |theta_ref|, wall superheat): where theta is still ~0 (only the
+    div v source has acted) its own maximum is not a meaningful scale."""
+    return norm_err(got, ref, max(float(np.abs(np.asarray(ref)).max()), abs(superheat)))
 
 
 def oracle_initial_fp32(rho0, P):

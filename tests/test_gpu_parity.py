@@ -16,7 +16,7 @@ import torch
 
 import oracle as O
 from paper_1501_03857_gb300 import inputs
-from parity_util import norm_err, oracle_fields, oracle_initial_fp32, oracle_params, run_oracle
+from parity_util import norm_err, oracle_fields, oracle_initial_fp32, oracle_params, run_oracle, theta_err
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso):
     P = oracle_params(cfg, rho0, superheat=0.012, Gw=Gw)
     fr, tr, qs = run_oracle(f0, th0, P, 1)
     assert norm_err(fg, fr.numpy()) < TOL_ONE_STEP
-    assert norm_err(tg, tr.numpy()) < TOL_ONE_STEP
+    assert theta_err(tg, tr.numpy(), 0.012) < TOL_ONE_STEP
     if bc != 2:
         h = sim.heat_flux()
         assert h["n"] == 1
@@ -88,10 +88,13 @@ def test_200_steps_config1(lb, outflow):
     sim.step(200)
     fg, tg = sim.get_state()
     fr, tr, qs = run_oracle(f0, th0, P, 200)
-    errs = {"f": norm_err(fg, fr.numpy()), "theta": norm_err(tg, tr.numpy())}
+    errs = {"f": norm_err(fg, fr.numpy()), "theta": theta_err(tg, tr.numpy(), sh)}
     fl = sim.fields()
     rr, vxr, vyr, Tr = oracle_fields(fr, tr, P)
-    errs.update(rho=norm_err(fl["rho"], rr), ux=norm_err(fl["ux"], vxr), uy=norm_err(fl["uy"], vyr))
+    # velocity components are normalised by the speed scale max|v| (u_x alone
+    # is ~1e-6 while |v| ~ 1e-2 here, so its own maximum is no scale)
+    vs = float(np.hypot(vxr, vyr).max())
+    errs.update(rho=norm_err(fl["rho"], rr), ux=norm_err(fl["ux"], vxr, vs), uy=norm_err(fl["uy"], vyr, vs))
     for k, v in errs.items():
         assert v < TOL_200, (k, v, errs)
     h = sim.heat_flux()
@@ -126,8 +129,9 @@ def test_fields_and_mass_match_oracle(lb):
     P = oracle_params(cfg, rho0, superheat=0.01, Gw=0.1)
     rr, vxr, vyr, Tr = oracle_fields(torch.tensor(f0, dtype=torch.float64), torch.tensor(th0, dtype=torch.float64), P)
     assert norm_err(fl["rho"], rr) < TOL_ONE_STEP
-    assert norm_err(fl["ux"], vxr) < 1e-5
-    assert norm_err(fl["uy"], vyr) < 1e-5
+    vs = float(np.hypot(vxr, vyr).max())
+    assert norm_err(fl["ux"], vxr, vs) < 1e-5
+    assert norm_err(fl["uy"], vyr, vs) < 1e-5
     assert norm_err(fl["T"], Tr) < 1e-6
     assert abs(sim.mass() / float(np.asarray(f0, np.float64).sum()) - 1) < 1e-12
 
@@ -145,14 +149,18 @@ def test_mass_conserved_periodic(lb):
 
 
 def test_eos_domain_and_nonfinite_flags(lb):
+    """A density beyond the EOS limit (psi argument < 0) and a NaN, both
+    planted on the host, come back as LB_E_EOS_DOMAIN and LB_E_NONFINITE at
+    the next synchronising call; the context stays usable."""
     cfg = lb.Config(Lx=16, Ly=8, bc_y=2)
     rv, rl = coex(lb, cfg)
-    rho0 = np.full((8, 16), rl, dtype=np.float32)
-    sim = lb.Simulation(cfg, rho0=rho0)
+    P = oracle_params(cfg, np.full((8, 16), rl, dtype=np.float32))
+    rho_bad = 9.9
+    T = torch.tensor([P.Ts], dtype=torch.float64)
+    assert bool(O.pseudopotential(torch.tensor([rho_bad], dtype=torch.float64), T, P)[1][0])
+    sim = lb.Simulation(cfg, rho0=np.full((8, 16), rl, dtype=np.float32))
     f, th = sim.get_state()
-    f2 = f.copy()
-    f2[:, 3, 4] *= 9.9 / rl  # density beyond the EOS limit -> psi argument < 0
-    sim.set_state(f2, th)
+    sim.set_state(f * np.float32(rho_bad / rl), th)
     sim.step(1)
     with pytest.raises(lb.LBError) as ei:
         sim.sync()
@@ -165,6 +173,9 @@ def test_eos_domain_and_nonfinite_flags(lb):
     with pytest.raises(lb.LBError) as ei:
         sim.sync()
     assert ei.value.code == -4
+    sim.set_state(f, th)
+    sim.step(1)
+    sim.sync()
 
 
 def test_save_load_roundtrip(lb):
@@ -204,7 +215,7 @@ def test_wall_temperature_profile_and_superheat_step(lb):
     fr, tr, _ = run_oracle(f.numpy(), th.numpy(), P, 20)
     fg, tg = sim.get_state()
     assert norm_err(fg, fr.numpy()) < 1e-5
-    assert norm_err(tg, tr.numpy()) < 1e-5
+    assert theta_err(tg, tr.numpy(), 0.02) < 1e-5
 
 
 def test_full_size_sampled_rows(lb):
@@ -237,4 +248,5 @@ def test_full_size_sampled_rows(lb):
         else:
             rows = list(range(7, band - 7))
         assert norm_err(fg[:, y0 + rows[0]:y0 + rows[-1] + 1], fr.numpy()[:, rows[0]:rows[-1] + 1]) < TOL_ONE_STEP
-        assert norm_err(tg[y0 + rows[0]:y0 + rows[-1] + 1], tr.numpy()[rows[0]:rows[-1] + 1]) < TOL_ONE_STEP
+        assert theta_err(tg[y0 + rows[0]:y0 + rows[-1] + 1], tr.numpy()[rows[0]:rows[-1] + 1],
+                         P.theta_b[0].item()) < TOL_ONE_STEP
