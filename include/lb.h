@@ -162,9 +162,15 @@ int lb_sync(lb_handle* h);
  * (a multiple of 32; 10 of them are x-halo columns) and rows per segment. */
 int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblocks);
 
-/* Override the launch shape (block_x in [64, 1024] multiple of 32 and
- * seg_rows >= 1; 0 keeps the automatic choice). Used by the autotuner. */
+/* Override the launch shape of the current kernel (seg_rows >= 1; 0 keeps
+ * the automatic choice). The paired kernel takes block_x 128 or 256, the
+ * row-wise kernel any multiple of 32 in [64, 512]. Used by the autotuner. */
 int lb_set_launch(lb_handle* h, int block_x, int seg_rows);
+
+/* Select the step kernel: 1 (default) advances two rows per iteration with
+ * paired FP32 arithmetic; 0 is the row-wise scalar kernel. Both compute the
+ * same update; the launch shape returns to its automatic choice. */
+int lb_set_kernel(lb_handle* h, int kernel);
 
 /* Checkpoint: lb_save_bytes gives the blob size; lb_save writes the state,
  * step count, accumulators and wall profile into host memory; lb_load

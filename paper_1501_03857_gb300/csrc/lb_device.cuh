@@ -43,6 +43,7 @@ struct StepParams {
     // Peng-Robinson EOS (Eq. 21): phi(T) = (k0 - k1 sqrt(T))^2 with
     // k0 = 1 + kappa, k1 = kappa / sqrt(Tc); psi^2 = two_over_G (p - rho/3).
     float Ts, a, b, R, two_over_G, k0, k1, G;
+    float k0k1, k1k1;  // phi'(T) = k1^2 - k0 k1 / sqrt(T)
     // MRT collision (Eqs. 2, 4, 8)
     float s_e, s_z, s_q, sig_e, sig_z;
     float rho_v, inv_drho, tau_v, dtau;

@@ -233,6 +233,8 @@ void fill_params(lb_handle* h) {
     P.two_over_G = (float)(2.0 / e.G);
     P.k0 = (float)(1.0 + kappa);
     P.k1 = (float)(kappa / std::sqrt(h->Tc));
+    P.k0k1 = (float)((1.0 + kappa) * kappa / std::sqrt(h->Tc));
+    P.k1k1 = (float)(kappa * kappa / h->Tc);
     P.s_e = (float)t.s_e;
     P.s_z = (float)t.s_zeta;
     P.s_q = (float)t.s_q;
@@ -251,16 +253,23 @@ void fill_params(lb_handle* h) {
     P.inv_cv = (float)(1.0 / t.cv);
 }
 
-int choose_launch(lb_handle* h, int block_x, int seg_rows) {
+int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
     int dev = 0, nsm = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     const int Lx = h->grid.Lx, Ly = h->grid.Ly;
-    int bx = block_x;
-    if (bx <= 0) bx = (Lx + 2 * HALO <= 256) ? std::max(64, (Lx + 2 * HALO + 31) / 32 * 32) : 256;
-    if (bx < 64 || bx > 1024 || bx % 32) return fail(LB_E_INVAL, "block_x %d must be a multiple of 32 in [64, 1024]", bx);
-    int occ = 0;
-    LB_CUDA((cudaError_t)step_occupancy(bx, &occ), "occupancy");
+    if (kernel != KERNEL_ROWS && kernel != KERNEL_PAIRS) return fail(LB_E_INVAL, "unknown kernel %d", kernel);
+    int bx = block_x, occ = 0;
+    if (kernel == KERNEL_PAIRS) {
+        if (bx <= 0) bx = 128;
+        if (!pairs_supported(bx)) return fail(LB_E_INVAL, "the paired kernel takes block_x 128 or 256, not %d", bx);
+        LB_CUDA(pairs_occupancy(bx, &occ), "occupancy");
+    } else {
+        if (bx <= 0) bx = (Lx + 2 * HALO <= 256) ? std::max(64, (Lx + 2 * HALO + 31) / 32 * 32) : 256;
+        if (bx < 64 || bx > 1024 || bx % 32)
+            return fail(LB_E_INVAL, "block_x %d must be a multiple of 32 in [64, 1024]", bx);
+        LB_CUDA((cudaError_t)step_occupancy(bx, &occ), "occupancy");
+    }
     if (occ < 1) return fail(LB_E_INVAL, "block_x %d does not fit on an SM", bx);
     const int nout = bx - 2 * HALO;
     const int nstrips = (Lx + nout - 1) / nout;
@@ -270,6 +279,8 @@ int choose_launch(lb_handle* h, int block_x, int seg_rows) {
         const int nseg = std::max(1, slots / nstrips);
         seg = std::max(8, (Ly + nseg - 1) / nseg);
     }
+    if (kernel == KERNEL_PAIRS) seg += seg & 1;  // segments start on even rows
+    h->launch.kernel = kernel;
     h->launch.block_x = bx;
     h->launch.seg_rows = seg;
     h->launch.nstrips = nstrips;
@@ -417,10 +428,11 @@ int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_th
     }
     h->rho_ave = sum / ((double)Lx * Ly);
     fill_params(h);
-    rc = choose_launch(h, 0, 0);
-    if (rc) { release(h); return rc; }
     cudaError_t e = step_prepare(1024);
+    if (e == cudaSuccess) e = pairs_prepare();
     if (e != cudaSuccess) { release(h); return cuda_fail(e, "cudaFuncSetAttribute"); }
+    rc = choose_launch(h, KERNEL_PAIRS, 0, 0);
+    if (rc) { release(h); return rc; }
 
     auto bail = [&](cudaError_t err, const char* what) { release(h); return cuda_fail(err, what); };
     if ((e = cudaMemsetAsync(h->acc, 0, sizeof(Acc), h->st)) != cudaSuccess) return bail(e, "clear accumulators");
@@ -573,7 +585,12 @@ int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblo
 int lb_set_launch(lb_handle* h, int block_x, int seg_rows) {
     if (!h) return fail(LB_E_INVAL, "null handle");
     if (seg_rows < 0) return fail(LB_E_INVAL, "seg_rows must be >= 0");
-    return choose_launch(h, block_x, seg_rows);
+    return choose_launch(h, h->launch.kernel, block_x, seg_rows);
+}
+
+int lb_set_kernel(lb_handle* h, int kernel) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    return choose_launch(h, kernel, 0, 0);
 }
 
 namespace {

@@ -12,12 +12,21 @@ namespace lbgpu {
 // output columns), seg_rows rows per block, nstrips x nseg blocks.
 struct Launch {
     int block_x, seg_rows, nstrips, nseg;
+    int kernel;  // KERNEL_ROWS or KERNEL_PAIRS
 };
+
+enum { KERNEL_ROWS = 0, KERNEL_PAIRS = 1 };
 
 size_t step_smem_bytes(int block_x);
 cudaError_t step_prepare(int block_x);  // opt in to the dynamic shared memory
 cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
 int step_occupancy(int block_x, int* blocks_per_sm);
+
+// The two-rows-per-iteration kernel with paired FP32 arithmetic (lb_step2.cu).
+bool pairs_supported(int block_x);
+cudaError_t pairs_prepare();
+cudaError_t pairs_occupancy(int block_x, int* blocks_per_sm);
+cudaError_t pairs_launch(const StepParams& P, const Launch& L, cudaStream_t st);
 
 // Initial state: f* = w_a rho0 (rest equilibrium), theta = 0 with the wall
 // rows at their Dirichlet values. rho0 is pitched [Ly][pitch].

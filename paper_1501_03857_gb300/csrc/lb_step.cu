@@ -390,6 +390,7 @@ int step_occupancy(int block_x, int* blocks_per_sm) {
 }
 
 cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st) {
+    if (L.kernel == KERNEL_PAIRS) return pairs_launch(P, L, st);
     lb_fused_step<<<L.nstrips * L.nseg, L.block_x, step_smem_bytes(L.block_x), st>>>(P);
     return cudaGetLastError();
 }

@@ -65,6 +65,7 @@ def _load():
         "lb_sync": [P],
         "lb_info": [P, I64P, C.POINTER(I), C.POINTER(I), C.POINTER(I)],
         "lb_set_launch": [P, I, I],
+        "lb_set_kernel": [P, I],
         "lb_save_bytes": [P, C.POINTER(C.c_size_t)],
         "lb_save": [P, P, SZ],
         "lb_load": [P, P, SZ],
@@ -201,6 +202,10 @@ class Simulation:
 
     def set_launch(self, block_x: int = 0, seg_rows: int = 0):
         check(lib.lb_set_launch(self.h, int(block_x), int(seg_rows)))
+
+    def set_kernel(self, kernel: int):
+        """1: two rows per iteration with paired FP32 math (default); 0: row-wise."""
+        check(lib.lb_set_kernel(self.h, int(kernel)))
 
     def info(self):
         st, bx, sr, nb = C.c_int64(), C.c_int(), C.c_int(), C.c_int()

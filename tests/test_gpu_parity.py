@@ -48,13 +48,15 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", [1, 0])
 @pytest.mark.parametrize("Lx,Ly,bc,ghost,Gw,iso", CASES)
-def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso):
+def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
     cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, ghost_layer=ghost, isothermal=iso)
     rv, rl = coex(lb, cfg)
     rho0, f0, th0 = inputs.random_state(Lx, Ly, rl, rv, Ly * 0.45, seed=Lx * 1000 + Ly)
     sim = lb.Simulation(cfg, superheat=0.012, Gw=Gw, rho0=rho0)
-    sim.set_launch(0, 5)  # several segments even on small grids
+    sim.set_kernel(kernel)
+    sim.set_launch(0, 6)  # several segments even on small grids
     sim.set_state(f0, th0)
     sim.step(1)
     fg, tg = sim.get_state()
@@ -102,13 +104,21 @@ def test_200_steps_config1(lb, outflow):
     assert abs(h["q_mean"] / np.mean(qs) - 1) < 1e-5
 
 
-def test_launch_shape_does_not_change_results(lb):
+SHAPES = {0: ((0, 0), (64, 1), (96, 7), (256, 57), (512, 3), (128, 1000)),
+          1: ((0, 0), (128, 2), (256, 6), (128, 1000), (256, 58), (128, 14))}
+
+
+@pytest.mark.parametrize("kernel", [1, 0])
+def test_launch_shape_does_not_change_results(lb, kernel):
+    """Each cell's arithmetic is the same whatever the strip width and segment
+    height, so the results are bit-identical across launch shapes."""
     cfg = lb.Config(Lx=263, Ly=57, bc_y=0)
     rv, rl = coex(lb, cfg)
     rho0, f0, th0 = inputs.random_state(cfg.Lx, cfg.Ly, rl, rv, 25, seed=5)
     ref = None
-    for bx, seg in ((0, 0), (64, 1), (96, 7), (256, 57), (512, 3), (128, 1000)):
+    for bx, seg in SHAPES[kernel]:
         sim = lb.Simulation(cfg, superheat=0.01, Gw=0.05, rho0=rho0)
+        sim.set_kernel(kernel)
         sim.set_launch(bx, seg)
         sim.set_state(f0, th0)
         sim.step(3)
