@@ -253,7 +253,14 @@ def run_ours(args):
         traffic = None
         tp = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tp):
-            traffic = json.load(open(tp)).get("lb_fused_step")
+            # DRAM bytes per launch from the committed ncu capture, only while
+            # the kernel source is the one that was profiled
+            import hashlib
+            rec = json.load(open(tp))
+            src = os.path.join(ROOT, "paper_1501_03857_gb300", "csrc", "lb_step3.cu")
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            if rec.get("source_sha256_16") == sha:
+                traffic = rec.get("lb_step_dual")
         info = sim.info()
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
@@ -261,7 +268,7 @@ def run_ours(args):
                 "config": dict(WORKLOAD, parallelism=f"replicas{world}", launch=info),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_source": src,
-                             "kernel": "lb_fused_step", "bytes_per_lu": BYTES_PER_LU,
+                             "kernel": "lb_step_dual (paired-FP32 dual-strip fused step)", "bytes_per_lu": BYTES_PER_LU,
                              "avg_kernel_ms": avg_ms},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
         if not args.no_cpu_baseline:

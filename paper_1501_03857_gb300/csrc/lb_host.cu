@@ -258,9 +258,14 @@ int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     const int Lx = h->grid.Lx, Ly = h->grid.Ly;
-    if (kernel != KERNEL_ROWS && kernel != KERNEL_PAIRS) return fail(LB_E_INVAL, "unknown kernel %d", kernel);
+    if (kernel < KERNEL_ROWS || kernel > KERNEL_DUAL_SCALAR) return fail(LB_E_INVAL, "unknown kernel %d", kernel);
+    const bool dual = kernel == KERNEL_DUAL || kernel == KERNEL_DUAL_SCALAR;
     int bx = block_x, occ = 0;
-    if (kernel == KERNEL_PAIRS) {
+    if (dual) {
+        if (bx <= 0) bx = (Lx <= 2 * (64 - 2 * HALO)) ? 64 : 128;
+        if (!dual_supported(bx)) return fail(LB_E_INVAL, "the dual-strip kernel takes block_x 64, 128 or 256, not %d", bx);
+        LB_CUDA(dual_occupancy(bx, kernel == KERNEL_DUAL, &occ), "occupancy");
+    } else if (kernel == KERNEL_PAIRS) {
         if (bx <= 0) bx = 128;
         if (!pairs_supported(bx)) return fail(LB_E_INVAL, "the paired kernel takes block_x 128 or 256, not %d", bx);
         LB_CUDA(pairs_occupancy(bx, &occ), "occupancy");
@@ -272,7 +277,8 @@ int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
     }
     if (occ < 1) return fail(LB_E_INVAL, "block_x %d does not fit on an SM", bx);
     const int nout = bx - 2 * HALO;
-    const int nstrips = (Lx + nout - 1) / nout;
+    const int cols = dual ? 2 * nout : nout;  // output columns per block
+    const int nstrips = (Lx + cols - 1) / cols;
     int seg = seg_rows;
     if (seg <= 0) {
         const int slots = nsm * occ;
@@ -430,8 +436,9 @@ int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_th
     fill_params(h);
     cudaError_t e = step_prepare(1024);
     if (e == cudaSuccess) e = pairs_prepare();
+    if (e == cudaSuccess) e = dual_prepare();
     if (e != cudaSuccess) { release(h); return cuda_fail(e, "cudaFuncSetAttribute"); }
-    rc = choose_launch(h, KERNEL_PAIRS, 0, 0);
+    rc = choose_launch(h, KERNEL_DUAL, 0, 0);  // paired-FP32 dual-strip kernel by default
     if (rc) { release(h); return rc; }
 
     auto bail = [&](cudaError_t err, const char* what) { release(h); return cuda_fail(err, what); };

@@ -15,7 +15,7 @@ struct Launch {
     int kernel;  // KERNEL_ROWS or KERNEL_PAIRS
 };
 
-enum { KERNEL_ROWS = 0, KERNEL_PAIRS = 1 };
+enum { KERNEL_ROWS = 0, KERNEL_PAIRS = 1, KERNEL_DUAL = 2, KERNEL_DUAL_SCALAR = 3 };
 
 size_t step_smem_bytes(int block_x);
 cudaError_t step_prepare(int block_x);  // opt in to the dynamic shared memory
@@ -27,6 +27,12 @@ bool pairs_supported(int block_x);
 cudaError_t pairs_prepare();
 cudaError_t pairs_occupancy(int block_x, int* blocks_per_sm);
 cudaError_t pairs_launch(const StepParams& P, const Launch& L, cudaStream_t st);
+
+// One row per iteration, two column strips per block in paired FP32 (lb_step3.cu).
+bool dual_supported(int block_x);
+cudaError_t dual_prepare();
+cudaError_t dual_occupancy(int block_x, bool paired, int* blocks_per_sm);
+cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st);
 
 // Initial state: f* = w_a rho0 (rest equilibrium), theta = 0 with the wall
 // rows at their Dirichlet values. rho0 is pitched [Ly][pitch].

@@ -391,6 +391,8 @@ int step_occupancy(int block_x, int* blocks_per_sm) {
 
 cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st) {
     if (L.kernel == KERNEL_PAIRS) return pairs_launch(P, L, st);
+    if (L.kernel == KERNEL_DUAL) return dual_launch(P, L, true, st);
+    if (L.kernel == KERNEL_DUAL_SCALAR) return dual_launch(P, L, false, st);
     lb_fused_step<<<L.nstrips * L.nseg, L.block_x, step_smem_bytes(L.block_x), st>>>(P);
     return cudaGetLastError();
 }

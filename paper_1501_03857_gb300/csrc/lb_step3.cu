@@ -1,0 +1,607 @@
+// The fused time step, one row per iteration, two column strips per block,
+// with paired FP32 arithmetic.
+//
+// Same pipeline as the row-wise kernel (lb_step.cu): a block marches up a
+// segment of rows; every population and temperature value is read from HBM
+// once and written once per step. Here a block owns TWO adjacent column
+// strips of (BD - 10) output columns each, and thread lc computes column lc
+// of both; the two cells are packed in one float2 (strip A in .x, strip B in
+// .y). A stencil neighbour of the pair is then again an aligned float2 in
+// shared memory, and every row-level condition (walls, ghost layer, first
+// fluid row) holds for both halves, so the whole update runs on Blackwell's
+// paired FP32 instructions (__ffma2_rn / __fadd2_rn / __fmul2_rn: two FP32
+// operations per issue slot) with no repacking. Barriers and ring indexing
+// are shared by the two cells. Reciprocals and 1/sqrt use the MUFU
+// approximations (__fdividef, rsqrtf; <= 2 ulp); psi itself is correctly
+// rounded (__fsqrt_rn).
+//
+//   P  row L    : pull f (loads issued one iteration ahead), wall fill,
+//                 rho, psi(rho, T^t)                       (Eqs. 3, 6, 21)
+//   B  row L-1  : F_m, F_ads, F_b, v, MRT collision, store f*   (Eqs. 2-9, 22)
+//   C  row L-2  : grad rho, div v, RK stage 1 of Eq. 18        (Eqs. 18-20)
+//   D  row L-3  : RK stage 2
+//   E  row L-4  : RK stage 3
+//   F  row L-5  : RK stage 4, store theta^{t+1}
+#include "lb_internal.h"
+
+namespace lbgpu {
+
+namespace {
+
+// Two cells (strip A, strip B) in paired FP32: one __ffma2_rn / __fadd2_rn /
+// __fmul2_rn does both.
+struct P2 {
+    float2 v;
+    __device__ __forceinline__ P2() {}
+    __device__ __forceinline__ explicit P2(float2 a) : v(a) {}
+    __device__ __forceinline__ P2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ float x() const { return v.x; }
+    __device__ __forceinline__ float y() const { return v.y; }
+    __device__ __forceinline__ float2 f2() const { return v; }
+    static __device__ __forceinline__ P2 bc(float s) { return P2(s, s); }
+};
+__device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ P2 operator-(P2 a) { return P2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ P2 operator*(float s, P2 b) { return P2(__fmul2_rn(make_float2(s, s), b.v)); }
+__device__ __forceinline__ P2 fma2(P2 a, P2 b, P2 c) { return P2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// The same two cells with scalar FP32 instructions.
+struct S2 {
+    float a, b;
+    __device__ __forceinline__ S2() {}
+    __device__ __forceinline__ explicit S2(float2 v) : a(v.x), b(v.y) {}
+    __device__ __forceinline__ S2(float x, float y) : a(x), b(y) {}
+    __device__ __forceinline__ float x() const { return a; }
+    __device__ __forceinline__ float y() const { return b; }
+    __device__ __forceinline__ float2 f2() const { return make_float2(a, b); }
+    static __device__ __forceinline__ S2 bc(float s) { return S2(s, s); }
+};
+__device__ __forceinline__ S2 operator+(S2 p, S2 q) { return S2(p.a + q.a, p.b + q.b); }
+__device__ __forceinline__ S2 operator-(S2 p, S2 q) { return S2(p.a - q.a, p.b - q.b); }
+__device__ __forceinline__ S2 operator-(S2 p) { return S2(-p.a, -p.b); }
+__device__ __forceinline__ S2 operator*(S2 p, S2 q) { return S2(p.a * q.a, p.b * q.b); }
+__device__ __forceinline__ S2 operator*(float s, S2 q) { return S2(s * q.a, s * q.b); }
+__device__ __forceinline__ S2 fma2(S2 p, S2 q, S2 r) { return S2(fmaf(p.a, q.a, r.a), fmaf(p.b, q.b, r.b)); }
+
+template <class T>
+__device__ __forceinline__ T rcp2(T a) { return T(__fdividef(1.f, a.x()), __fdividef(1.f, a.y())); }
+template <class T>
+__device__ __forceinline__ T rsqrt2(T a) { return T(rsqrtf(a.x()), rsqrtf(a.y())); }
+
+// y = v mod n for pipeline rows (|v| is within a few rows of [0, n)).
+__device__ __forceinline__ int wrap_row(int v, int n) {
+    if (v < 0) v += n;
+    if (v >= n) v -= n;
+    if ((unsigned)v >= (unsigned)n) v = wrap(v, n);
+    return v;
+}
+
+// Pulled populations (Eq. 3: f_a(x) = f*_a(x - e_a)) and theta of row y for
+// the two columns; sources beyond a wall read 0 (filled by Zou-He), with the
+// outflow top the source row is clamped to the top row.
+template <class T>
+__device__ __forceinline__ void load_row2(const StepParams& P, int y, int xa, int xam, int xap, int xb, int xbm,
+                                          int xbp, T (&f)[9], T& th) {
+    const float* __restrict__ F = P.f_in;
+    const int pl = P.plane, pitch = P.pitch;
+    int ym = y - 1, yp = y + 1;
+    bool okm = true, okp = true;
+    if (P.bc == BC_PERIODIC) {
+        if (ym < 0) ym += P.Ly;
+        if (yp >= P.Ly) yp -= P.Ly;
+    } else {
+        okm = ym >= 0;
+        if (yp >= P.Ly) {
+            if (P.bc == BC_TOP_OUTFLOW) yp = P.Ly - 1;
+            else okp = false;
+        }
+    }
+    const float* Rc = F + y * pitch;
+    const float* Rm = F + ym * pitch;
+    const float* Rp = F + yp * pitch;
+    f[0] = T(__ldg(Rc + xa), __ldg(Rc + xb));
+    f[1] = T(__ldg(Rc + pl + xam), __ldg(Rc + pl + xbm));
+    f[3] = T(__ldg(Rc + 3 * pl + xap), __ldg(Rc + 3 * pl + xbp));
+    if (okm) {
+        f[2] = T(__ldg(Rm + 2 * pl + xa), __ldg(Rm + 2 * pl + xb));
+        f[5] = T(__ldg(Rm + 5 * pl + xam), __ldg(Rm + 5 * pl + xbm));
+        f[6] = T(__ldg(Rm + 6 * pl + xap), __ldg(Rm + 6 * pl + xbp));
+    } else {
+        f[2] = f[5] = f[6] = T::bc(0.f);
+    }
+    if (okp) {
+        f[4] = T(__ldg(Rp + 4 * pl + xa), __ldg(Rp + 4 * pl + xb));
+        f[7] = T(__ldg(Rp + 7 * pl + xap), __ldg(Rp + 7 * pl + xbp));
+        f[8] = T(__ldg(Rp + 8 * pl + xam), __ldg(Rp + 8 * pl + xbm));
+    } else {
+        f[4] = f[7] = f[8] = T::bc(0.f);
+    }
+    const float* Tc = P.th_in + y * pitch;
+    th = T(__ldg(Tc + xa), __ldg(Tc + xb));
+}
+
+// Isotropic central differences (Lee and Lin; Sec. 2 after Eq. 20) at
+// column s, rows m (below), c, p (above) of float2 ring rows. The first
+// derivatives use the weights 1/3 (axis) and 1/12 (diagonal), the same as
+// sum_a w_a phi(x + e_a) e_a of Eq. 7.
+template <class T>
+struct St2 {
+    T dx, dy, lap, c;
+};
+
+template <class T>
+__device__ __forceinline__ St2<T> stencil2(const float2* __restrict__ m, const float2* __restrict__ c,
+                                           const float2* __restrict__ p, bool want_lap) {
+    const T W(c[-1]), C(c[0]), E(c[1]);
+    const T SW(m[-1]), S(m[0]), SE(m[1]);
+    const T NW(p[-1]), N(p[0]), NE(p[1]);
+    const T d1 = NE - SW, d2 = SE - NW;
+    St2<T> o;
+    o.dx = fma2(E - W, T::bc(1.f / 3.f), (d1 + d2) * T::bc(1.f / 12.f));
+    o.dy = fma2(N - S, T::bc(1.f / 3.f), (d1 - d2) * T::bc(1.f / 12.f));
+    if (want_lap) {
+        const T ax4 = (E + W) + (N + S);
+        const T dg = (NE + SW) + (NW + SE);
+        o.lap = fma2(T::bc(-20.f), C, fma2(T::bc(4.f), ax4, dg)) * T::bc(1.f / 6.f);
+    } else {
+        o.lap = T::bc(0.f);
+    }
+    o.c = C;
+    return o;
+}
+
+// Per-cell coefficients of K(T), Eq. 18, with rho and v frozen at level t:
+// K = ax dT/dx + ay dT/dy + chi lap T - T (cA - cB phi'(T)), where
+// ax = -v_x + chi d_x rho / rho (div(lambda grad T)/(rho c_v) with
+// lambda = c_v chi rho), cA - cB phi' = (dp/dT)_rho div v / (rho c_v) and
+// phi'(T) = k1^2 - k0 k1 / sqrt(T) (derivative of Eq. 21's phi).
+template <class T>
+struct Coef2 {
+    T ax, ay, cA, cB;
+};
+
+template <class T>
+__device__ __forceinline__ T rhs_K2(const St2<T>& u, const Coef2<T>& k, const StepParams& P) {
+    const T Tt = u.c + T::bc(P.Ts);
+    const T dphi = fma2(T::bc(-P.k0k1), rsqrt2(Tt), T::bc(P.k1k1));
+    const T src = Tt * fma2(-k.cB, dphi, k.cA);
+    return fma2(k.ax, u.dx, fma2(k.ay, u.dy, fma2(T::bc(P.chi), u.lap, -src)));
+}
+
+// psi of Sec. 2 with the Peng-Robinson EOS of Eq. 21 for two cells.
+template <class T>
+__device__ __forceinline__ T eos_psi2(T rho, T Tt, const StepParams& P, bool& bad) {
+    const T sT = Tt * rsqrt2(Tt);
+    T ph = fma2(T::bc(-P.k1), sT, T::bc(P.k0));
+    ph = ph * ph;
+    const T br = P.b * rho;
+    const T i1 = rcp2(T::bc(1.f) - br);
+    const T i2 = rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));  // 1 + 2 b rho - b^2 rho^2
+    const T p = (P.R * rho) * Tt * i1 - (P.a * ph) * (rho * rho) * i2;
+    const T arg = P.two_over_G * fma2(rho, T::bc(-1.f / 3.f), p);
+    const float ax = arg.x(), ay = arg.y();
+    bad |= (ax < 0.f) | (ay < 0.f);
+    // correctly rounded: psi multiplies the neighbour sums of Eq. 7, so its
+    // relative error reaches the velocity amplified by |F_m| / (rho |v|)
+    return T(__fsqrt_rn(fmaxf(ax, 0.f)), __fsqrt_rn(fmaxf(ay, 0.f)));
+}
+
+// MRT collision, Eq. 2 with the forcing moments S of Eq. 8, in the exactly
+// equivalent additive form f* = f + M^-1 dm, dm = -Lambda (m - m^eq) +
+// (I - Lambda/2) S, for two cells. dm is small (non-equilibrium moments and
+// forces), so FP32 rounding stays at ~1 ulp of f and dm_rho = 0 conserves
+// mass exactly; the non-equilibrium moments use rho v = j + F/2 (Eq. 6).
+template <class T>
+__device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T Fx, T Fy, T Fmx, T Fmy, T psi,
+                                         const StepParams& P, T (&o)[9]) {
+    const T sa = (f[1] + f[3]) + (f[2] + f[4]);
+    const T sd = (f[5] + f[7]) + (f[6] + f[8]);
+    const T dxd = (f[5] - f[7]) + (f[8] - f[6]);
+    const T dyd = (f[5] - f[7]) + (f[6] - f[8]);
+    const T rv2 = rho * fma2(vx, vx, vy * vy);
+    const T ne1 = fma2(T::bc(-2.f), f[0], fma2(T::bc(4.f), sd, sa)) - 3.f * rv2;
+    const T ne2 = 3.f * ((f[0] - sa) + rv2);
+    const T ne4 = fma2(T::bc(2.f), dxd, fma2(T::bc(0.5f), Fx, f[3] - f[1]));
+    const T ne6 = fma2(T::bc(2.f), dyd, fma2(T::bc(0.5f), Fy, f[4] - f[2]));
+    const T ne7 = ((f[1] + f[3]) - (f[2] + f[4])) - rho * fma2(vx, vx, -(vy * vy));
+    const T ne8 = ((f[5] + f[7]) - (f[6] + f[8])) - rho * (vx * vy);
+    const T vF = fma2(vx, Fx, vy * Fy);
+    const T psi2 = psi * psi;
+    const T fm2 = fma2(Fmx, Fmx, Fmy * Fmy);
+    const T ratio(psi2.x() > 0.f ? __fdividef(fm2.x(), psi2.x()) : 0.f,
+                  psi2.y() > 0.f ? __fdividef(fm2.y(), psi2.y()) : 0.f);
+    const T S1 = fma2(T::bc(6.f), vF, P.sig_e * ratio);
+    const T S2 = -fma2(T::bc(6.f), vF, P.sig_z * ratio);
+    const T S7 = 2.f * fma2(vx, Fx, -(vy * Fy));
+    const T S8 = fma2(vx, Fy, vy * Fx);
+    // tau_nu(rho): linear between the coexistence densities, clamped
+    const T sr = (rho - T::bc(P.rho_v)) * T::bc(P.inv_drho);
+    const T sfr(fminf(fmaxf(sr.x(), 0.f), 1.f), fminf(fmaxf(sr.y(), 0.f), 1.f));
+    const T snu = rcp2(fma2(T::bc(P.dtau), sfr, T::bc(P.tau_v)));
+    const T dm1 = fma2(T::bc(-P.s_e), ne1, (1.f - 0.5f * P.s_e) * S1);
+    const T dm2 = fma2(T::bc(-P.s_z), ne2, (1.f - 0.5f * P.s_z) * S2);
+    const T dm4 = fma2(T::bc(-P.s_q), ne4, (0.5f * P.s_q - 1.f) * Fx);
+    const T dm6 = fma2(T::bc(-P.s_q), ne6, (0.5f * P.s_q - 1.f) * Fy);
+    const T hnu = fma2(T::bc(-0.5f), snu, T::bc(1.f));
+    const T dm7 = fma2(-snu, ne7, hnu * S7);
+    const T dm8 = fma2(-snu, ne8, hnu * S8);
+    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); dm_j = F
+    const T n1 = dm1 * T::bc(1.f / 36.f), n2 = dm2 * T::bc(1.f / 36.f);
+    const T n3 = Fx * T::bc(1.f / 6.f), n4 = dm4 * T::bc(1.f / 12.f);
+    const T n5 = Fy * T::bc(1.f / 6.f), n6 = dm6 * T::bc(1.f / 12.f);
+    const T n7 = dm7 * T::bc(0.25f), n8 = dm8 * T::bc(0.25f);
+    const T ax_ = fma2(T::bc(-2.f), n2, -n1);
+    const T dg = fma2(T::bc(2.f), n1, n2);
+    const T cx = fma2(T::bc(-2.f), n4, n3), cy = fma2(T::bc(-2.f), n6, n5);
+    const T dxx = n3 + n4, dyy = n5 + n6;
+    o[0] = fma2(T::bc(4.f), n2 - n1, f[0]);
+    o[1] = f[1] + ((ax_ + cx) + n7);
+    o[2] = f[2] + ((ax_ + cy) - n7);
+    o[3] = f[3] + ((ax_ - cx) + n7);
+    o[4] = f[4] + ((ax_ - cy) - n7);
+    o[5] = f[5] + ((dg + dxx) + (dyy + n8));
+    o[6] = f[6] + ((dg - dxx) + (dyy - n8));
+    o[7] = f[7] + ((dg - dxx) - (dyy - n8));
+    o[8] = f[8] + ((dg + dxx) - (dyy + n8));
+}
+
+}  // namespace
+
+template <int BD, int MINB, class T>
+__global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
+    constexpr int W = BD + 2;
+    extern __shared__ float2 sm2[];
+    __shared__ double red[BD / 32];
+    float2* const sPSI = sm2;
+    float2* const sRHO = sPSI + RING * W;
+    float2* const sVX = sRHO + RING * W;
+    float2* const sVY = sVX + RING * W;
+    float2* const sU2 = sVY + RING * W;
+    float2* const sU3 = sU2 + RING * W;
+    float2* const sU4 = sU3 + RING * W;
+    float2* const sTH = sU4 + RING * W;   // TRING slots
+    float2* const sCO = sTH + TRING * W;  // [4 coefficients][RING slots][BD], own column
+    for (int i = threadIdx.x; i < SM_ROWS * W + 4 * RING * BD; i += BD) sm2[i] = make_float2(0.f, 0.f);
+
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int strip = blockIdx.x % P.nstrips;  // a pair of column strips
+    const int seg = blockIdx.x / P.nstrips;
+    const int nout = P.nout;
+    const int x0 = strip * 2 * nout;
+    const int nva = min(nout, Lx - x0);
+    const int nvb = min(nout, Lx - x0 - nout);
+    const int lc = threadIdx.x;
+    const int s = lc + 1;
+    const int xa = wrap(x0 - HALO + lc, Lx);
+    const int xb = wrap(x0 + nout - HALO + lc, Lx);
+    const int xam = xa == 0 ? Lx - 1 : xa - 1, xap = xa == Lx - 1 ? 0 : xa + 1;
+    const int xbm = xb == 0 ? Lx - 1 : xb - 1, xbp = xb == Lx - 1 ? 0 : xb + 1;
+    const bool outa = lc >= HALO && lc < HALO + nva;
+    const bool outb = lc >= HALO && lc < HALO + nvb;
+    const bool periodic = P.bc == BC_PERIODIC;
+    const int ys = seg * P.seg_h;
+    const int ye = min(ys + P.seg_h, Ly);
+    auto lo = [&](int d) { return periodic ? ys - d : max(ys - d, 0); };
+    auto hi = [&](int d) { return periodic ? ye + d : min(ye + d, Ly); };
+    const int loP = lo(5), hiP = hi(5), loB = lo(4), hiB = hi(4), loC = lo(3), hiC = hi(3);
+    const int loD = lo(2), hiD = hi(2), loE = lo(1), hiE = hi(1);
+    const bool thermal = !P.isothermal;
+    bool eos_bad = false, nonfinite = false;
+    const T zero = T::bc(0.f);
+
+    T fc[9], tc = zero;
+    if (loP < hiP) load_row2(P, wrap_row(loP, Ly), xa, xam, xap, xb, xbm, xbp, fc, tc);
+    T fP[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fP[a] = zero;
+    T acc1 = zero, acc2 = zero, acc3 = zero;
+    // the RK coefficients of row r live in slot (r & 3) of sCO
+    auto coef = [&](int r) {
+        const float2* c = sCO + (r & 3) * BD + lc;
+        return Coef2<T>{T(c[0]), T(c[RING * BD]), T(c[2 * RING * BD]), T(c[3 * RING * BD])};
+    };
+    __syncthreads();
+
+    int yL = wrap_row(loP, Ly);  // physical row of pipeline row L
+    for (int L = loP; L <= ye + 4; ++L) {
+        // ---- prefetch the pulled populations of row L+1
+        T fn[9], tn = zero;
+        const int yN = yL + 1 == Ly ? 0 : yL + 1;
+        if (L + 1 < hiP) {
+            load_row2(P, yN, xa, xam, xap, xb, xbm, xbp, fn, tn);
+        } else {
+#pragma unroll
+            for (int a = 0; a < 9; ++a) fn[a] = zero;
+        }
+
+        // ---- P: wall fill, rho, psi of row L
+        if (L < hiP) {
+            const int y = yL;
+            if (!periodic && y == 0) {  // Zou-He bottom wall, u = 0
+                const T d = 0.5f * (fc[1] - fc[3]);
+                fc[2] = fc[4];
+                fc[5] = fc[7] - d;
+                fc[6] = fc[8] + d;
+            }
+            if (P.bc == BC_WALLS && y == Ly - 1) {  // Zou-He top wall, u = 0
+                const T d = 0.5f * (fc[1] - fc[3]);
+                fc[4] = fc[2];
+                fc[7] = fc[5] + d;
+                fc[8] = fc[6] - d;
+            }
+            const T rhoN = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
+            const T psiN = eos_psi2(rhoN, tc + T::bc(P.Ts), P, eos_bad);
+            sPSI[(L & 3) * W + s] = psiN.f2();
+            sRHO[(L & 3) * W + s] = rhoN.f2();
+            sTH[(L & 7) * W + s] = tc.f2();
+        }
+        __syncthreads();
+
+        // ---- bottom-wall heat flux of level t (Sec. 3.2), one sample per step
+        if (!periodic && ys == 0 && L == 2) {
+            double qv = 0.0;
+            const float2 r0 = sRHO[0 * W + s], t0 = sTH[0 * W + s], t1 = sTH[1 * W + s], t2 = sTH[2 * W + s];
+            if (outa) qv += -(double)P.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
+            if (outb) qv += -(double)P.cvchi * r0.y * (-3.0 * t0.y + 4.0 * t1.y - t2.y) * 0.5;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) qv += __shfl_down_sync(0xffffffffu, qv, o);
+            if ((lc & 31) == 0) red[lc >> 5] = qv;
+            __syncthreads();
+            if (lc == 0) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < BD / 32; ++w) sum += red[w];
+                Acc* A = P.acc;
+                atomicAdd(&A->q_partial, sum);
+                __threadfence();
+                const unsigned t = atomicAdd(&A->count, 1u);
+                if (t == (unsigned)P.nstrips - 1u) {
+                    __threadfence();
+                    const double tot = __longlong_as_double(
+                        (long long)atomicExch((unsigned long long*)&A->q_partial, 0ull));
+                    const double qt = tot / (double)Lx;
+                    A->q_last = qt;
+                    A->q_sum += qt;
+                    A->q_sum2 += qt * qt;
+                    A->q_n += 1.0;
+                    atomicExch(&A->count, 0u);
+                }
+            }
+        }
+
+        // ---- B: forces, velocity, collision of row L-1
+        {
+            const int r = L - 1;
+            if (r >= loB && r < hiB) {
+                const int y = yL == 0 ? Ly - 1 : yL - 1;
+                const bool wall = !periodic && (y == 0 || y == Ly - 1);
+                const T rhoP(sRHO[(r & 3) * W + s]);
+                const T psiP(sPSI[(r & 3) * W + s]);
+                const T jxP = (fP[1] - fP[3]) + (fP[5] - fP[6]) + (fP[8] - fP[7]);
+                const T jyP = (fP[2] - fP[4]) + (fP[5] + fP[6]) - (fP[7] + fP[8]);
+                T Fmx = zero, Fmy = zero;
+                if (!wall || P.ghost) {
+                    const float2* pc = sPSI + (r & 3) * W + s;
+                    const float2* pn = (wall && y == Ly - 1) ? pc : sPSI + ((r + 1) & 3) * W + s;
+                    const float2* ps = (wall && y == 0) ? pc : sPSI + ((r - 1) & 3) * W + s;
+                    const St2<T> g = stencil2<T>(ps, pc, pn, false);  // sum_a w_a psi(x + e_a) e_a, Eq. 7
+                    Fmx = (-P.G) * (psiP * g.dx);
+                    Fmy = (-P.G) * (psiP * g.dy);
+                }
+                T Fy = Fmy;
+                if (!wall) {
+                    if (!periodic && y == 1) Fy = fma2(T::bc(P.gw6), psiP * psiP, Fy);  // Eq. 22
+                    Fy = fma2(T::bc(-P.g), rhoP - T::bc(P.rho_ave), Fy);                // Eq. 9
+                }
+                const T Fx = Fmx;
+                const T irho = rcp2(rhoP);
+                const T vx = fma2(T::bc(0.5f), Fx, jxP) * irho;  // Eq. 6
+                const T vy = fma2(T::bc(0.5f), Fy, jyP) * irho;
+                sVX[(r & 3) * W + s] = vx.f2();
+                sVY[(r & 3) * W + s] = vy.f2();
+                const bool st = r >= ys && r < ye;
+                if (st && (outa || outb)) {
+                    T o[9];
+                    collide2(fP, rhoP, vx, vy, Fx, Fy, Fmx, Fmy, psiP, P, o);
+                    const int pl = P.plane;
+                    float* out = P.f_out + y * P.pitch;
+                    if (outa) {
+                        if (!finite_f(rhoP.x())) nonfinite = true;
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) out[a * pl + xa] = o[a].x();
+                    }
+                    if (outb) {
+                        if (!finite_f(rhoP.y())) nonfinite = true;
+#pragma unroll
+                        for (int a = 0; a < 9; ++a) out[a * pl + xb] = o[a].y();
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // Stage C makes the coefficients of row L-2 (kept in sCO); D, E, F work
+        // on rows whose coefficients C made 1, 2 and 3 iterations ago.
+        T accC = zero;
+        if (thermal) {
+            // ---- C: frozen-flow coefficients and RK stage 1 of row L-2
+            {
+                const int r = L - 2;
+                if (r >= loC && r < hiC) {
+                    const int y = wrap_row(yL - 2, Ly);
+                    const T thr(sTH[(r & 7) * W + s]);
+                    T u2 = thr;
+                    if (periodic || (y != 0 && y != Ly - 1)) {
+                        const int om = ((r - 1) & 3) * W + s, oc = (r & 3) * W + s, op = ((r + 1) & 3) * W + s;
+                        const St2<T> gr = stencil2<T>(sRHO + om, sRHO + oc, sRHO + op, false);
+                        const St2<T> gvx = stencil2<T>(sVX + om, sVX + oc, sVX + op, false);
+                        const St2<T> gvy = stencil2<T>(sVY + om, sVY + oc, sVY + op, false);
+                        const T rho = gr.c;
+                        const T irho = rcp2(rho);
+                        const T divv = gvx.dx + gvy.dy;
+                        const T br = P.b * rho;
+                        Coef2<T> kC;
+                        kC.ax = fma2(T::bc(P.chi), gr.dx * irho, -gvx.c);
+                        kC.ay = fma2(T::bc(P.chi), gr.dy * irho, -gvy.c);
+                        kC.cA = (P.R * P.inv_cv) * divv * rcp2(T::bc(1.f) - br);
+                        kC.cB = (P.a * P.inv_cv) * (divv * rho) * rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));
+                        float2* c = sCO + (r & 3) * BD + lc;
+                        c[0] = kC.ax.f2();
+                        c[RING * BD] = kC.ay.f2();
+                        c[2 * RING * BD] = kC.cA.f2();
+                        c[3 * RING * BD] = kC.cB.f2();
+                        const St2<T> ut = stencil2<T>(sTH + ((r - 1) & 7) * W + s, sTH + (r & 7) * W + s,
+                                                      sTH + ((r + 1) & 7) * W + s, true);
+                        accC = rhs_K2(ut, kC, P);
+                        u2 = fma2(T::bc(0.5f), accC, thr);
+                    }
+                    sU2[(r & 3) * W + s] = u2.f2();
+                }
+            }
+            __syncthreads();
+            // ---- D: RK stage 2 of row L-3
+            {
+                const int r = L - 3;
+                if (r >= loD && r < hiD) {
+                    const int y = wrap_row(yL - 3, Ly);
+                    const T thr(sTH[(r & 7) * W + s]);
+                    T u3 = thr;
+                    if (periodic || (y != 0 && y != Ly - 1)) {
+                        const St2<T> u = stencil2<T>(sU2 + ((r - 1) & 3) * W + s, sU2 + (r & 3) * W + s,
+                                                     sU2 + ((r + 1) & 3) * W + s, true);
+                        const T h2 = rhs_K2(u, coef(r), P);
+                        u3 = fma2(T::bc(0.5f), h2, thr);
+                        acc1 = fma2(T::bc(2.f), h2, acc1);
+                    }
+                    sU3[(r & 3) * W + s] = u3.f2();
+                }
+            }
+            __syncthreads();
+            // ---- E: RK stage 3 of row L-4
+            {
+                const int r = L - 4;
+                if (r >= loE && r < hiE) {
+                    const int y = wrap_row(yL - 4, Ly);
+                    const T thr(sTH[(r & 7) * W + s]);
+                    T u4 = thr;
+                    if (periodic || (y != 0 && y != Ly - 1)) {
+                        const St2<T> u = stencil2<T>(sU3 + ((r - 1) & 3) * W + s, sU3 + (r & 3) * W + s,
+                                                     sU3 + ((r + 1) & 3) * W + s, true);
+                        const T h3 = rhs_K2(u, coef(r), P);
+                        u4 = thr + h3;
+                        acc2 = fma2(T::bc(2.f), h3, acc2);
+                    }
+                    sU4[(r & 3) * W + s] = u4.f2();
+                }
+            }
+            __syncthreads();
+        }
+        // ---- F: RK stage 4 and theta^{t+1} of row L-5
+        {
+            const int r = L - 5;
+            if (r >= ys && r < ye && (outa || outb)) {
+                const int y = wrap_row(yL - 5, Ly);
+                const T thr(sTH[(r & 7) * W + s]);
+                T tnew = thr;
+                if (thermal) {
+                    if (!periodic && y == 0) {
+                        tnew = T(__ldg(P.thb + xa), __ldg(P.thb + xb));
+                    } else if (!periodic && y == Ly - 1) {
+                        tnew = zero;
+                    } else {
+                        const St2<T> u = stencil2<T>(sU4 + ((r - 1) & 3) * W + s, sU4 + (r & 3) * W + s,
+                                                     sU4 + ((r + 1) & 3) * W + s, true);
+                        const T h4 = rhs_K2(u, coef(r), P);
+                        tnew = fma2(acc3 + h4, T::bc(1.f / 6.f), thr);
+                    }
+                }
+                float* out = P.th_out + y * P.pitch;
+                if (outa) {
+                    if (!finite_f(tnew.x())) nonfinite = true;
+                    out[xa] = tnew.x();
+                }
+                if (outb) {
+                    if (!finite_f(tnew.y())) nonfinite = true;
+                    out[xb] = tnew.y();
+                }
+            }
+        }
+        // rotate per-thread carries
+        acc3 = acc2;
+        acc2 = acc1;
+        acc1 = accC;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            fP[a] = fc[a];
+            fc[a] = fn[a];
+        }
+        tc = tn;
+        yL = yN;
+    }
+    if (eos_bad) atomicOr(&P.acc->err, ERR_EOS);
+    if (nonfinite) atomicOr(&P.acc->err, ERR_NONFINITE);
+}
+
+namespace {
+
+template <int BD, int MINB, class T>
+struct DualKernel {
+    static size_t smem() { return sizeof(float2) * ((size_t)SM_ROWS * (BD + 2) + 4 * RING * BD); }
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(lb_step_dual<BD, MINB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem());
+    }
+    static cudaError_t occupancy(int* n) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lb_step_dual<BD, MINB, T>, BD, smem());
+    }
+    static cudaError_t launch(const StepParams& P, int nblocks, cudaStream_t st) {
+        lb_step_dual<BD, MINB, T><<<nblocks, BD, smem(), st>>>(P);
+        return cudaGetLastError();
+    }
+};
+
+// the instantiations a launch can pick: (block size, paired FP32 or scalar)
+template <class T>
+cudaError_t dual_prepare_t() {
+    cudaError_t e = DualKernel<64, 8, T>::prepare();
+    if (e == cudaSuccess) e = DualKernel<128, 4, T>::prepare();
+    if (e == cudaSuccess) e = DualKernel<256, 2, T>::prepare();
+    return e;
+}
+
+template <class T>
+cudaError_t dual_occupancy_t(int block_x, int* n) {
+    if (block_x == 64) return DualKernel<64, 8, T>::occupancy(n);
+    if (block_x == 128) return DualKernel<128, 4, T>::occupancy(n);
+    return DualKernel<256, 2, T>::occupancy(n);
+}
+
+template <class T>
+cudaError_t dual_launch_t(const StepParams& P, const Launch& L, cudaStream_t st) {
+    const int nb = L.nstrips * L.nseg;
+    if (L.block_x == 64) return DualKernel<64, 8, T>::launch(P, nb, st);
+    if (L.block_x == 128) return DualKernel<128, 4, T>::launch(P, nb, st);
+    return DualKernel<256, 2, T>::launch(P, nb, st);
+}
+
+}  // namespace
+
+bool dual_supported(int block_x) { return block_x == 64 || block_x == 128 || block_x == 256; }
+
+cudaError_t dual_prepare() {
+    cudaError_t e = dual_prepare_t<P2>();
+    if (e == cudaSuccess) e = dual_prepare_t<S2>();
+    return e;
+}
+
+cudaError_t dual_occupancy(int block_x, bool paired, int* n) {
+    return paired ? dual_occupancy_t<P2>(block_x, n) : dual_occupancy_t<S2>(block_x, n);
+}
+
+cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st) {
+    return paired ? dual_launch_t<P2>(P, L, st) : dual_launch_t<S2>(P, L, st);
+}
+
+}  // namespace lbgpu

@@ -48,7 +48,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", [1, 0])
+@pytest.mark.parametrize("kernel", [2, 3, 1, 0])
 @pytest.mark.parametrize("Lx,Ly,bc,ghost,Gw,iso", CASES)
 def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
     cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, ghost_layer=ghost, isothermal=iso)
@@ -105,10 +105,12 @@ def test_200_steps_config1(lb, outflow):
 
 
 SHAPES = {0: ((0, 0), (64, 1), (96, 7), (256, 57), (512, 3), (128, 1000)),
-          1: ((0, 0), (128, 2), (256, 6), (128, 1000), (256, 58), (128, 14))}
+          1: ((0, 0), (128, 2), (256, 6), (128, 1000), (256, 58), (128, 14)),
+          2: ((0, 0), (64, 1), (128, 5), (256, 57), (64, 1000), (128, 13)),
+          3: ((0, 0), (64, 1), (128, 5), (256, 57), (64, 1000), (128, 13))}
 
 
-@pytest.mark.parametrize("kernel", [1, 0])
+@pytest.mark.parametrize("kernel", [2, 3, 1, 0])
 def test_launch_shape_does_not_change_results(lb, kernel):
     """Each cell's arithmetic is the same whatever the strip width and segment
     height, so the results are bit-identical across launch shapes."""
