@@ -183,6 +183,41 @@ int lb_load(lb_handle* h, const void* host_buf, size_t bytes);
 /* Release the handle (the workspace stays the caller's). */
 int lb_destroy(lb_handle* h);
 
+/* ---- no-allocation variant (not part of the paper's method) -------------- */
+
+/* Largest grid (Lx * Ly cells) lb_fields_noalloc accepts. */
+#define LB_NOALLOC_MAX_CELLS 262144
+
+/* lb_fields without a handle, a workspace or any device allocation. The
+ * paper has no counterpart; this exists for callers that cannot allocate
+ * device memory themselves: code running inside another framework's memory
+ * pool or allocator hook, processes that are not allowed to create
+ * allocations after start-up, and real-time loops that must not touch the
+ * allocator. Such a caller already holds the state in device memory and only
+ * needs the macroscopic fields of it.
+ *
+ * Inputs (device pointers, unpitched, row-major as everywhere in this
+ * header): fpost[9*Ly*Lx] post-collision populations and theta[Ly*Lx] =
+ * T - T_s; rho_ave is the mean initial density of Eq. 9 and Gw the strength
+ * of Eq. 22. Outputs (device, [Ly*Lx] each, any may be NULL): rho, ux, uy
+ * and T exactly as lb_fields computes them. Grid fields other than Lx, Ly,
+ * bc_y and ghost_layer, and the pool fields of th, are ignored.
+ *
+ * Scratch: the intermediate planes live in one static device array of
+ * 4 * LB_NOALLOC_MAX_CELLS floats (4 MiB) plus 256 bytes inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Grids larger than LB_NOALLOC_MAX_CELLS are rejected with LB_E_INVAL. The
+ * first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before starting
+ * any stream capture. All calls share the one array: calls that overlap on
+ * the GPU (other streams, other host threads) race on it, so serialise
+ * them. The call is issued on `stream` and synchronises it before
+ * returning; it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Returns LB_E_EOS_DOMAIN if a cell's density lies outside the EOS domain. */
+int lb_fields_noalloc(const lb_grid* grid, const lb_eos* eos, const lb_thermal* th,
+                      double Gw, double rho_ave, const float* fpost, const float* theta,
+                      float* rho, float* ux, float* uy, float* T, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* lb_last_error(void);
 

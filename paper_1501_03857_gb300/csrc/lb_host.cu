@@ -185,6 +185,8 @@ Layout layout(const lb_grid* g) {
 
 }  // namespace
 
+void lbgpu::set_last_error(const char* msg) { g_err = msg; }
+
 struct lb_handle {
     lb_grid grid;
     lb_eos eos;

@@ -43,6 +43,9 @@ cudaError_t launch_init(const StepParams& P, const float* rho0, float* f, float*
 cudaError_t launch_macro(const StepParams& P, float* scratch, float* rho, float* ux, float* uy,
                          float* T, int ostride, cudaStream_t st);
 
+// Record the message lb_last_error() returns on this thread.
+void set_last_error(const char* msg);
+
 // acc->mass = sum over cells and directions of f (FP64).
 cudaError_t launch_mass(const StepParams& P, const float* f, cudaStream_t st);
 

@@ -70,6 +70,8 @@ def _load():
         "lb_save": [P, P, SZ],
         "lb_load": [P, P, SZ],
         "lb_destroy": [P],
+        "lb_fields_noalloc": [C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), D, D, P, P, P, P, P,
+                              P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -155,6 +157,24 @@ def workspace_bytes(cfg: Config) -> int:
     return n.value
 
 
+NOALLOC_MAX_CELLS = 262144
+
+
+def fields_noalloc(cfg: Config, Gw: float, rho_ave: float, fpost, theta, rho=None, ux=None, uy=None, T=None,
+                   stream=None):
+    """Macroscopic fields of a device-resident state without a handle or any
+    device allocation (lb_fields_noalloc). fpost [9, Ly, Lx] and theta
+    [Ly, Lx] are contiguous float32 CUDA tensors; outputs are preallocated
+    float32 CUDA tensors [Ly, Lx] or None. Grids above NOALLOC_MAX_CELLS cells
+    are rejected."""
+    import torch
+    g, e, t = cfg.structs()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ptr = lambda x: None if x is None else x.data_ptr()
+    check(lib.lb_fields_noalloc(C.byref(g), C.byref(e), C.byref(t), float(Gw), float(rho_ave), ptr(fpost),
+                                ptr(theta), ptr(rho), ptr(ux), ptr(uy), ptr(T), st.cuda_stream))
+
+
 def _host_ptr(a: Optional[np.ndarray], dtype):
     if a is None:
         return None, None
@@ -232,6 +252,12 @@ class Simulation:
         th = np.empty((self.Ly, self.Lx), dtype=np.float32)
         check(lib.lb_get_state(self.h, f.ctypes.data, th.ctypes.data, 0))
         return f, th
+
+    def get_state_device(self, fpost=None, theta=None):
+        """Copy the state into preallocated contiguous float32 CUDA tensors
+        fpost [9, Ly, Lx] and theta [Ly, Lx] (either may be None)."""
+        ptr = lambda t: None if t is None else t.data_ptr()
+        check(lib.lb_get_state(self.h, ptr(fpost), ptr(theta), 1))
 
     def set_state(self, fpost=None, theta=None):
         f, fp = _host_ptr(fpost, np.float32)
