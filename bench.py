@@ -133,6 +133,62 @@ def cpu_baseline(seconds: float = 12.0, rows: int = 48):
                       f"{el:.1f} s"}
 
 
+# Wettability ladder standing in for the contact-angle axis of the batched
+# curve (Sec. 3.3 gives G_w = 0, 0.065, 0.105 for ~44.5, 50, 55.5 degrees; the
+# last two rungs extend the ladder, uncalibrated).
+GW_LADDER = (0.0, 0.065, 0.105, 0.15, 0.2)
+CURVE_STEPS = 50000  # steps of one boiling-curve simulation
+
+
+def batched_curve(torch, lb, steps_batch=64, steps_seq=32):
+    """48 boiling-curve instances (uneven 200-400 x 200-600 domains, superheat
+    0.02-0.4 Tc, wettability ladder) in one launch per step vs. the same
+    instances stepped one after another through the plain path."""
+    from paper_1501_03857_gb300 import inputs, tune
+    pts = inputs.boiling_curve_batch(48, seed=3)
+    insts = []
+    for i, d in enumerate(pts):
+        cfg = lb.Config(Lx=d["Lx"], Ly=d["Ly"], bc_y=lb.BC_WALLS, pool_height=0.4 * d["Ly"], seed=100 + i)
+        Tc = lb.critical_temperature(cfg)
+        insts.append({"cfg": cfg, "superheat": d["superheat_frac"] * Tc, "Gw": GW_LADDER[d["wet_index"]]})
+    cells = sum(d["cfg"].Lx * d["cfg"].Ly for d in insts)
+    st = torch.cuda.current_stream()
+    batch = lb.Batch(insts, stream=st)
+    bx, seg, _ = tune.tune_batch(batch)
+    batch.step(GRAPH_WARM)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    batch.step(steps_batch)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    t_b = ev[0].elapsed_time(ev[1]) / steps_batch
+    batch.sync()
+    info = batch.info()
+    batch.close()
+    t_seq = 0.0
+    for d in insts:
+        sim = lb.Simulation(d["cfg"], superheat=d["superheat"], Gw=d["Gw"], stream=st)
+        sim.step(3)
+        torch.cuda.synchronize()
+        ev[0].record(st)
+        sim.step(steps_seq)
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        t_seq += ev[0].elapsed_time(ev[1]) / steps_seq
+        sim.close()
+    sph = lambda t: len(insts) * 3600.0 / (CURVE_STEPS * t * 1e-3)
+    return {"instances": len(insts), "cells": cells, "steps_per_sim": CURVE_STEPS,
+            "ms_per_step_batched": t_b, "ms_per_step_sequential": t_seq,
+            "sims_per_hour_batched": sph(t_b), "sims_per_hour_sequential": sph(t_seq),
+            "speedup": t_seq / t_b, "mlups_batched": cells / (t_b * 1e3),
+            "launch": {"block_x": bx, "seg_rows": seg, "blocks": info["blocks"],
+                       "graph": "32-step captured graphs"}}
+
+
+GRAPH_WARM = 32
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -271,6 +327,8 @@ def run_ours(args):
                              "kernel": "lb_step_dual (paired-FP32 dual-strip fused step)", "bytes_per_lu": BYTES_PER_LU,
                              "avg_kernel_ms": avg_ms},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
+        if not args.no_batched:
+            line["batched"] = batched_curve(torch, lb)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -286,6 +344,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched boiling-curve measurement")
     ap.add_argument("--size", type=int, default=4096, help="domain edge (profiling of smaller cases)")
     args = ap.parse_args()
     global L

@@ -183,6 +183,65 @@ int lb_load(lb_handle* h, const void* host_buf, size_t bytes);
 /* Release the handle (the workspace stays the caller's). */
 int lb_destroy(lb_handle* h);
 
+/* ---- batches: many independent simulations, one launch per step ---------- */
+
+/* One instance of a batch (the points of a boiling curve, Sec. 3.2-3.3:
+ * superheat x wettability): its grid, parameters, bottom-wall superheat
+ * T_b(x) - T_s = superheat + (Tb_profile ? Tb_profile[x] : 0) (host, may be
+ * NULL), G_w of Eq. 22, and an optional host initial density rho0[Ly*Lx]
+ * (NULL: the pool of th). */
+typedef struct lb_batch_desc {
+    lb_grid grid;
+    lb_eos eos;
+    lb_thermal th;
+    double superheat, Gw;
+    const double* Tb_profile;
+    const float* rho0;
+} lb_batch_desc;
+
+typedef struct lb_batch lb_batch;
+
+/* Device workspace for n instances (each laid out as for lb_init, plus the
+ * per-step parameter tables). */
+int lb_batch_workspace_bytes(const lb_batch_desc* d, int n, size_t* bytes);
+
+/* Create n instances in one caller workspace on `stream`. Every instance is
+ * initialised exactly as lb_init would. Synchronises the stream. */
+int lb_batch_init(lb_batch** b, const lb_batch_desc* d, int n, void* dev_workspace,
+                  size_t workspace_bytes, void* stream);
+
+/* Advance every instance by nsteps: one launch of the fused step covers all
+ * instances (each block belongs to one instance); runs of 32 steps are
+ * replayed from a captured CUDA graph on a private stream ordered after and
+ * before `stream`. Asynchronous. Results per instance are identical to
+ * stepping the instance alone with the same launch shape. */
+int lb_batch_step(lb_batch* b, int nsteps);
+
+/* Launch shape shared by all instances: block_x 64 or 128; seg_rows 0 gives
+ * every instance a share of one full wave proportional to its cells. */
+int lb_batch_set_launch(lb_batch* b, int block_x, int seg_rows);
+
+/* Per-instance heat-flux statistics into arrays of n entries (any may be
+ * NULL); see lb_heat_flux. Synchronises. */
+int lb_batch_heat_flux(lb_batch* b, double* q_inst, double* q_mean, double* q_std,
+                       int64_t* nsamples, int reset);
+
+/* Per-instance state copies and parameter changes (see the single-instance
+ * calls of the same name). */
+int lb_batch_get_state(lb_batch* b, int i, float* fpost, float* theta, int on_device);
+int lb_batch_set_state(lb_batch* b, int i, const float* fpost, const float* theta, int on_device);
+int lb_batch_set_wall_temperature(lb_batch* b, int i, const double* Tb_profile, double superheat);
+int lb_batch_set_wettability(lb_batch* b, int i, double Gw);
+
+/* Steps taken, block size and blocks per launch. */
+int lb_batch_info(lb_batch* b, int64_t* steps, int* block_x, int* nblocks);
+
+/* Wait and report latched device faults of any instance. */
+int lb_batch_sync(lb_batch* b);
+
+/* Release the batch (the workspace stays the caller's). */
+int lb_batch_destroy(lb_batch* b);
+
 /* ---- no-allocation variant (not part of the paper's method) -------------- */
 
 /* Largest grid (Lx * Ly cells) lb_fields_noalloc accepts. */

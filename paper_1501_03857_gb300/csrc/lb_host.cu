@@ -687,3 +687,309 @@ int lb_destroy(lb_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many independent simulations advanced by one launch per step
+// ---------------------------------------------------------------------------
+
+struct lb_batch {
+    std::vector<lb_handle*> inst;
+    std::vector<size_t> ws_off;  // workspace offset of each instance
+    StepParams* table;           // device [2][n]: parameters by step parity
+    int* block_off;              // device [n + 1]: first block of each instance
+    std::vector<int> h_off;
+    std::vector<StepParams> h_table;
+    int block_x, seg_req;        // launch shape (seg_req 0: automatic)
+    int nblocks;
+    bool dirty;                  // tables no longer match the instances' buffers
+    int64_t steps;
+    cudaStream_t st;             // the caller's stream
+    cudaStream_t gs;             // private stream the captured graphs run on
+    cudaEvent_t ev_in, ev_out;
+    cudaGraphExec_t graph;       // GRAPH_STEPS steps starting at parity 0
+};
+
+namespace {
+
+constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity returns)
+
+size_t batch_tail_offset(const lb_batch_desc* d, int n, std::vector<size_t>* offs) {
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        if (offs) offs->push_back(off);
+        off += layout(&d[i].grid).total;
+    }
+    return off;
+}
+
+// Common block size, per-instance segment height and block offsets. With an
+// automatic segment height every instance gets a share of one full wave
+// proportional to its cells.
+int batch_layout(lb_batch* b) {
+    const int n = (int)b->inst.size();
+    int dev = 0, nsm = 0, occ = 0;
+    LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    LB_CUDA(batch_occupancy(b->block_x, &occ), "occupancy");
+    if (occ < 1) return fail(LB_E_INVAL, "batch block_x %d does not fit on an SM", b->block_x);
+    const int nout = b->block_x - 2 * HALO;
+    long long cells = 0;
+    for (lb_handle* h : b->inst) cells += (long long)h->grid.Lx * h->grid.Ly;
+    b->h_off.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        lb_handle* h = b->inst[i];
+        const int nstrips = (h->grid.Lx + 2 * nout - 1) / (2 * nout);
+        int seg = b->seg_req;
+        if (seg <= 0) {
+            const double share = (double)h->grid.Lx * h->grid.Ly / (double)cells;
+            const int nseg = std::max(1, (int)(share * nsm * occ / nstrips));
+            seg = std::max(8, (h->grid.Ly + nseg - 1) / nseg);
+        }
+        h->launch.kernel = KERNEL_DUAL;
+        h->launch.block_x = b->block_x;
+        h->launch.seg_rows = seg;
+        h->launch.nstrips = nstrips;
+        h->launch.nseg = (h->grid.Ly + seg - 1) / seg;
+        h->base.nout = nout;
+        h->base.nstrips = nstrips;
+        h->base.seg_h = seg;
+        b->h_off[i + 1] = b->h_off[i] + nstrips * h->launch.nseg;
+    }
+    b->nblocks = b->h_off[n];
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    LB_CUDA(cudaMemcpyAsync(b->block_off, b->h_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->st),
+            "batch offsets upload");
+    b->dirty = true;
+    return LB_OK;
+}
+
+// Parameter tables relative to each instance's current buffer: parity p
+// reads buffer cur ^ p. Uploaded in stream order (the host copy is staged
+// by the driver before the call returns).
+int batch_upload(lb_batch* b) {
+    if (!b->dirty) return LB_OK;
+    const int n = (int)b->inst.size();
+    b->h_table.resize(2 * n);
+    for (int p = 0; p < 2; ++p)
+        for (int i = 0; i < n; ++i) {
+            lb_handle* h = b->inst[i];
+            StepParams P = h->base;
+            const int c = h->cur ^ p;
+            P.f_in = h->f[c];
+            P.f_out = h->f[1 - c];
+            P.th_in = h->t[c];
+            P.th_out = h->t[1 - c];
+            b->h_table[p * n + i] = P;
+        }
+    LB_CUDA(cudaMemcpyAsync(b->table, b->h_table.data(), 2 * n * sizeof(StepParams), cudaMemcpyHostToDevice, b->st),
+            "batch table upload");
+    b->dirty = false;
+    return LB_OK;
+}
+
+int batch_launch_one(lb_batch* b, cudaStream_t s, int parity) {
+    const int n = (int)b->inst.size();
+    LB_CUDA(batch_launch(b->block_x, b->table + parity * n, b->block_off, n, b->nblocks, s), "batch step launch");
+    return LB_OK;
+}
+
+int batch_graph(lb_batch* b, cudaGraphExec_t* out) {
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        LB_CUDA(cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int rc = LB_OK;
+        for (int k = 0; k < GRAPH_STEPS && rc == LB_OK; ++k) rc = batch_launch_one(b, b->gs, k & 1);
+        cudaError_t e = cudaStreamEndCapture(b->gs, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    }
+    *out = b->graph;
+    return LB_OK;
+}
+
+void batch_release(lb_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->gs) cudaStreamSynchronize(b->gs);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->gs) cudaStreamDestroy(b->gs);
+    for (lb_handle* h : b->inst) release(h);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_batch_workspace_bytes(const lb_batch_desc* d, int n, size_t* bytes) {
+    if (!d || n < 1 || !bytes) return fail(LB_E_INVAL, "need n >= 1 descriptors and an output");
+    for (int i = 0; i < n; ++i)
+        if (d[i].grid.Lx < 1 || d[i].grid.Ly < 3) return fail(LB_E_INVAL, "instance %d: grid too small", i);
+    size_t off = batch_tail_offset(d, n, nullptr);
+    off = align256(off) + align256(2 * n * sizeof(StepParams)) + align256((n + 1) * sizeof(int));
+    *bytes = off;
+    return LB_OK;
+}
+
+int lb_batch_init(lb_batch** out, const lb_batch_desc* d, int n, void* dev_workspace, size_t workspace_bytes,
+                  void* stream) {
+    if (!out) return fail(LB_E_INVAL, "null batch pointer");
+    *out = nullptr;
+    size_t need = 0;
+    int rc = lb_batch_workspace_bytes(d, n, &need);
+    if (rc) return rc;
+    if (!dev_workspace || workspace_bytes < need)
+        return fail(LB_E_INVAL, "batch workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, need);
+    if (((uintptr_t)dev_workspace) & 255) return fail(LB_E_INVAL, "workspace must be 256-byte aligned");
+    lb_batch* b = new lb_batch();
+    b->table = nullptr;
+    b->block_off = nullptr;
+    b->graph = nullptr;
+    b->st = (cudaStream_t)stream;
+    b->gs = nullptr;
+    b->ev_in = b->ev_out = nullptr;
+    b->steps = 0;
+    b->block_x = 128;
+    b->seg_req = 0;
+    b->dirty = true;
+    char* ws = (char*)dev_workspace;
+    const size_t tail = batch_tail_offset(d, n, &b->ws_off);
+    for (int i = 0; i < n; ++i) {
+        lb_handle* h = nullptr;
+        rc = lb_init(&h, &d[i].grid, &d[i].eos, &d[i].th, d[i].Tb_profile, d[i].superheat, d[i].Gw, d[i].rho0,
+                     ws + b->ws_off[i], layout(&d[i].grid).total, stream);
+        if (rc) {
+            const std::string msg = g_err;
+            batch_release(b);
+            return fail(rc, "instance %d: %s", i, msg.c_str());
+        }
+        b->inst.push_back(h);
+    }
+    b->table = (StepParams*)(ws + align256(tail));
+    b->block_off = (int*)(ws + align256(tail) + align256(2 * n * sizeof(StepParams)));
+    cudaError_t e = batch_prepare();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        batch_release(b);
+        return cuda_fail(e, "batch set-up");
+    }
+    rc = batch_layout(b);
+    if (rc == LB_OK) rc = batch_upload(b);
+    if (rc == LB_OK && (e = cudaStreamSynchronize(b->st)) != cudaSuccess) rc = cuda_fail(e, "batch init sync");
+    if (rc) {
+        batch_release(b);
+        return rc;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_set_launch(lb_batch* b, int block_x, int seg_rows) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    if (!batch_supported(block_x)) return fail(LB_E_INVAL, "batch block_x must be 64 or 128, not %d", block_x);
+    if (seg_rows < 0) return fail(LB_E_INVAL, "seg_rows must be >= 0");
+    b->block_x = block_x;
+    b->seg_req = seg_rows;
+    return batch_layout(b);
+}
+
+int lb_batch_step(lb_batch* b, int nsteps) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    if (nsteps < 0) return fail(LB_E_INVAL, "nsteps must be >= 0");
+    int rc = batch_upload(b);
+    if (rc) return rc;
+    int left = nsteps, parity = 0;
+    if (left >= GRAPH_STEPS) {
+        // whole chunks as a captured graph on the private stream, ordered
+        // after and before the caller's stream
+        cudaGraphExec_t g = nullptr;
+        rc = batch_graph(b, &g);
+        if (rc) return rc;
+        LB_CUDA(cudaEventRecord(b->ev_in, b->st), "cudaEventRecord");
+        LB_CUDA(cudaStreamWaitEvent(b->gs, b->ev_in, 0), "cudaStreamWaitEvent");
+        for (; left >= GRAPH_STEPS; left -= GRAPH_STEPS) LB_CUDA(cudaGraphLaunch(g, b->gs), "cudaGraphLaunch");
+        LB_CUDA(cudaEventRecord(b->ev_out, b->gs), "cudaEventRecord");
+        LB_CUDA(cudaStreamWaitEvent(b->st, b->ev_out, 0), "cudaStreamWaitEvent");
+    }
+    for (; left > 0; --left, parity ^= 1) {
+        rc = batch_launch_one(b, b->st, parity);
+        if (rc) return rc;
+    }
+    for (lb_handle* h : b->inst) {
+        h->cur ^= (nsteps & 1);
+        h->steps += nsteps;
+    }
+    if (nsteps & 1) b->dirty = true;  // tables follow each instance's current buffer
+    b->steps += nsteps;
+    return LB_OK;
+}
+
+int lb_batch_heat_flux(lb_batch* b, double* q_inst, double* q_mean, double* q_std, int64_t* nsamples, int reset) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+        int rc = lb_heat_flux(b->inst[i], q_inst ? q_inst + i : nullptr, q_mean ? q_mean + i : nullptr,
+                              q_std ? q_std + i : nullptr, nsamples ? nsamples + i : nullptr, reset);
+        if (rc) return rc;
+    }
+    return LB_OK;
+}
+
+int lb_batch_get_state(lb_batch* b, int i, float* fpost, float* theta, int on_device) {
+    if (!b || i < 0 || i >= (int)b->inst.size()) return fail(LB_E_INVAL, "bad batch or instance index");
+    return lb_get_state(b->inst[i], fpost, theta, on_device);
+}
+
+int lb_batch_set_state(lb_batch* b, int i, const float* fpost, const float* theta, int on_device) {
+    if (!b || i < 0 || i >= (int)b->inst.size()) return fail(LB_E_INVAL, "bad batch or instance index");
+    return lb_set_state(b->inst[i], fpost, theta, on_device);
+}
+
+int lb_batch_set_wall_temperature(lb_batch* b, int i, const double* Tb_profile, double superheat) {
+    if (!b || i < 0 || i >= (int)b->inst.size()) return fail(LB_E_INVAL, "bad batch or instance index");
+    return lb_set_wall_temperature(b->inst[i], Tb_profile, superheat);
+}
+
+int lb_batch_set_wettability(lb_batch* b, int i, double Gw) {
+    if (!b || i < 0 || i >= (int)b->inst.size()) return fail(LB_E_INVAL, "bad batch or instance index");
+    int rc = lb_set_wettability(b->inst[i], Gw);
+    if (rc == LB_OK) b->dirty = true;
+    return rc;
+}
+
+int lb_batch_info(lb_batch* b, int64_t* steps, int* block_x, int* nblocks) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    if (steps) *steps = b->steps;
+    if (block_x) *block_x = b->block_x;
+    if (nblocks) *nblocks = b->nblocks;
+    return LB_OK;
+}
+
+int lb_batch_sync(lb_batch* b) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    for (lb_handle* h : b->inst) {
+        int rc = check_device_errors(h);
+        if (rc) return rc;
+    }
+    return LB_OK;
+}
+
+int lb_batch_destroy(lb_batch* b) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    batch_release(b);
+    return LB_OK;
+}
+
+}  // extern "C"

@@ -34,6 +34,15 @@ cudaError_t dual_prepare();
 cudaError_t dual_occupancy(int block_x, bool paired, int* blocks_per_sm);
 cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st);
 
+// The same step over a table of independent instances in one launch
+// (paired FP32, block_x 64 or 128); instance i owns blocks
+// [block_off[i], block_off[i+1]).
+bool batch_supported(int block_x);
+cudaError_t batch_prepare();
+cudaError_t batch_occupancy(int block_x, int* blocks_per_sm);
+cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,
+                         cudaStream_t st);
+
 // Initial state: f* = w_a rho0 (rest equilibrium), theta = 0 with the wall
 // rows at their Dirichlet values. rho0 is pitched [Ly][pitch].
 cudaError_t launch_init(const StepParams& P, const float* rho0, float* f, float* th, cudaStream_t st);

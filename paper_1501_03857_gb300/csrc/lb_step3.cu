@@ -249,8 +249,9 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
 
 }  // namespace
 
-template <int BD, int MINB, class T>
-__global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
+// The whole step for block `block` of the launch described by P.
+template <int BD, class T>
+__device__ __forceinline__ void step_body(const StepParams& P, const int block) {
     constexpr int W = BD + 2;
     extern __shared__ float2 sm2[];
     __shared__ double red[BD / 32];
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
     for (int i = threadIdx.x; i < SM_ROWS * W + 4 * RING * BD; i += BD) sm2[i] = make_float2(0.f, 0.f);
 
     const int Lx = P.Lx, Ly = P.Ly;
-    const int strip = blockIdx.x % P.nstrips;  // a pair of column strips
-    const int seg = blockIdx.x / P.nstrips;
+    const int strip = block % P.nstrips;  // a pair of column strips
+    const int seg = block / P.nstrips;
     const int nout = P.nout;
     const int x0 = strip * 2 * nout;
     const int nva = min(nout, Lx - x0);
@@ -544,6 +545,38 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
     if (nonfinite) atomicOr(&P.acc->err, ERR_NONFINITE);
 }
 
+template <int BD, int MINB, class T>
+__global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
+    step_body<BD, T>(P, blockIdx.x);
+}
+
+// Many independent simulations in one launch (the boiling-curve batch): the
+// blocks of instance i are [block_off[i], block_off[i+1]); each block copies
+// its instance's parameters to shared memory and runs the same step.
+template <int BD, int MINB, class T>
+__global__ void __launch_bounds__(BD, MINB) lb_step_batch(const StepParams* __restrict__ table,
+                                                        const int* __restrict__ block_off, int n) {
+    __shared__ StepParams sP;
+    __shared__ int s_inst;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;  // largest i with block_off[i] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (block_off[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_inst = lo;
+    }
+    __syncthreads();
+    const int inst = s_inst;
+    constexpr int NW = (int)(sizeof(StepParams) / sizeof(int));
+    static_assert(sizeof(StepParams) % sizeof(int) == 0, "StepParams is copied as ints");
+    for (int k = threadIdx.x; k < NW; k += BD)
+        reinterpret_cast<int*>(&sP)[k] = __ldg(reinterpret_cast<const int*>(table + inst) + k);
+    __syncthreads();
+    step_body<BD, T>(sP, blockIdx.x - block_off[inst]);
+}
+
 namespace {
 
 template <int BD, int MINB, class T>
@@ -560,6 +593,17 @@ struct DualKernel {
         lb_step_dual<BD, MINB, T><<<nblocks, BD, smem(), st>>>(P);
         return cudaGetLastError();
     }
+    static cudaError_t prepare_batch() {
+        return cudaFuncSetAttribute(lb_step_batch<BD, MINB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem());
+    }
+    static cudaError_t occupancy_batch(int* n) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lb_step_batch<BD, MINB, T>, BD, smem());
+    }
+    static cudaError_t launch_batch(const StepParams* table, const int* off, int n, int nblocks, cudaStream_t st) {
+        lb_step_batch<BD, MINB, T><<<nblocks, BD, smem(), st>>>(table, off, n);
+        return cudaGetLastError();
+    }
 };
 
 // the instantiations a launch can pick: (block size, paired FP32 or scalar)
@@ -568,6 +612,12 @@ cudaError_t dual_prepare_t() {
     cudaError_t e = DualKernel<64, 8, T>::prepare();
     if (e == cudaSuccess) e = DualKernel<128, 4, T>::prepare();
     if (e == cudaSuccess) e = DualKernel<256, 2, T>::prepare();
+    return e;
+}
+
+cudaError_t batch_prepare_t() {
+    cudaError_t e = DualKernel<64, 8, P2>::prepare_batch();
+    if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_batch();
     return e;
 }
 
@@ -602,6 +652,20 @@ cudaError_t dual_occupancy(int block_x, bool paired, int* n) {
 
 cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st) {
     return paired ? dual_launch_t<P2>(P, L, st) : dual_launch_t<S2>(P, L, st);
+}
+
+bool batch_supported(int block_x) { return block_x == 64 || block_x == 128; }
+
+cudaError_t batch_prepare() { return batch_prepare_t(); }
+
+cudaError_t batch_occupancy(int block_x, int* n) {
+    return block_x == 64 ? DualKernel<64, 8, P2>::occupancy_batch(n) : DualKernel<128, 4, P2>::occupancy_batch(n);
+}
+
+cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,
+                         cudaStream_t st) {
+    return block_x == 64 ? DualKernel<64, 8, P2>::launch_batch(table, block_off, n, nblocks, st)
+                         : DualKernel<128, 4, P2>::launch_batch(table, block_off, n, nblocks, st);
 }
 
 }  // namespace lbgpu

@@ -132,3 +132,22 @@ def random_state(Lx, Ly, rho_l, rho_v, pool_height, seed, pop_amp=0.05, rho_amp=
     f = D2Q9_WEIGHTS[:, None, None] * rho0[None] * (1.0 + pop_amp * u)
     th = theta_max * uniform01(seed + 2, np.arange(Lx * Ly, dtype=np.uint64).reshape(Ly, Lx))
     return rho0.astype(np.float32), f.astype(np.float32), th.astype(np.float32)
+
+
+def boiling_curve_batch(n=48, seed=3, superheat_range=(0.02, 0.4), n_wettability=5,
+                        lx_range=(200, 400), ly_range=(200, 600), step=8):
+    """The points of a batched boiling curve: instance i has superheat
+    fraction s_i = lo + (hi - lo) i/(n-1) (of T_c), wettability index
+    i mod n_wettability, and a domain size drawn uniformly from the multiples
+    of `step` in the given ranges (two draws of the seed's stream per
+    instance). Returns a list of dicts (Lx, Ly, superheat_frac, wet_index)."""
+    out = []
+    nx = (lx_range[1] - lx_range[0]) // step + 1
+    ny = (ly_range[1] - ly_range[0]) // step + 1
+    u = uniform01(seed, np.arange(2 * n, dtype=np.uint64))
+    for i in range(n):
+        Lx = lx_range[0] + step * min(int(u[2 * i] * nx), nx - 1)
+        Ly = ly_range[0] + step * min(int(u[2 * i + 1] * ny), ny - 1)
+        frac = superheat_range[0] + (superheat_range[1] - superheat_range[0]) * i / max(n - 1, 1)
+        out.append({"Lx": Lx, "Ly": Ly, "superheat_frac": frac, "wet_index": i % n_wettability})
+    return out

@@ -42,6 +42,11 @@ class lb_thermal(C.Structure):
                                           "s_q", "pool_height", "noise_amp")] + [("seed", C.c_uint64)]
 
 
+class lb_batch_desc(C.Structure):
+    _fields_ = [("grid", lb_grid), ("eos", lb_eos), ("th", lb_thermal), ("superheat", C.c_double),
+                ("Gw", C.c_double), ("Tb_profile", C.c_void_p), ("rho0", C.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_1501_03857_gb300.build")
@@ -70,6 +75,18 @@ def _load():
         "lb_save": [P, P, SZ],
         "lb_load": [P, P, SZ],
         "lb_destroy": [P],
+        "lb_batch_workspace_bytes": [C.POINTER(lb_batch_desc), I, C.POINTER(C.c_size_t)],
+        "lb_batch_init": [C.POINTER(P), C.POINTER(lb_batch_desc), I, P, SZ, P],
+        "lb_batch_step": [P, I],
+        "lb_batch_set_launch": [P, I, I],
+        "lb_batch_heat_flux": [P, P, P, P, P, I],
+        "lb_batch_get_state": [P, I, FP, FP, I],
+        "lb_batch_set_state": [P, I, FP, FP, I],
+        "lb_batch_set_wall_temperature": [P, I, P, D],
+        "lb_batch_set_wettability": [P, I, D],
+        "lb_batch_info": [P, I64P, C.POINTER(I), C.POINTER(I)],
+        "lb_batch_sync": [P],
+        "lb_batch_destroy": [P],
         "lb_fields_noalloc": [C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), D, D, P, P, P, P, P,
                               P, P],
     }
@@ -286,6 +303,93 @@ class Simulation:
     def close(self):
         if getattr(self, "h", None):
             lib.lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent boiling domains advanced by one launch per step
+    (lb_batch_*). instances: a list of dicts with keys cfg (Config) and
+    optionally superheat, Gw, profile, rho0."""
+
+    def __init__(self, instances, stream=None):
+        import torch
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        n = len(instances)
+        self.n = n
+        self.cfgs = [d["cfg"] for d in instances]
+        self._keep = []
+        descs = (lb_batch_desc * n)()
+        for i, d in enumerate(instances):
+            g, e, t = d["cfg"].structs()
+            descs[i].grid, descs[i].eos, descs[i].th = g, e, t
+            descs[i].superheat = float(d.get("superheat", 0.0))
+            descs[i].Gw = float(d.get("Gw", 0.0))
+            prof, pp = _host_ptr(d.get("profile"), np.float64)
+            r0, rp = _host_ptr(d.get("rho0"), np.float32)
+            self._keep += [prof, r0]
+            descs[i].Tb_profile = pp
+            descs[i].rho0 = rp
+        nb = C.c_size_t()
+        check(lib.lb_batch_workspace_bytes(descs, n, C.byref(nb)))
+        self.workspace = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        ws = base + ((-base) % 256)
+        h = C.c_void_p()
+        check(lib.lb_batch_init(C.byref(h), descs, n, ws, nb.value, self.stream.cuda_stream))
+        self._keep = []
+        self.h = h
+
+    def step(self, n: int = 1):
+        check(lib.lb_batch_step(self.h, int(n)))
+
+    def set_launch(self, block_x: int = 128, seg_rows: int = 0):
+        check(lib.lb_batch_set_launch(self.h, int(block_x), int(seg_rows)))
+
+    def info(self):
+        st, bx, nb = C.c_int64(), C.c_int(), C.c_int()
+        check(lib.lb_batch_info(self.h, C.byref(st), C.byref(bx), C.byref(nb)))
+        return {"steps": st.value, "block_x": bx.value, "blocks": nb.value}
+
+    def heat_flux(self, reset: bool = False):
+        out = {k: np.zeros(self.n) for k in ("q_inst", "q_mean", "q_std")}
+        ns = np.zeros(self.n, dtype=np.int64)
+        check(lib.lb_batch_heat_flux(self.h, out["q_inst"].ctypes.data, out["q_mean"].ctypes.data,
+                                     out["q_std"].ctypes.data, ns.ctypes.data, int(reset)))
+        out["n"] = ns
+        return out
+
+    def get_state(self, i: int):
+        c = self.cfgs[i]
+        f = np.empty((9, c.Ly, c.Lx), dtype=np.float32)
+        th = np.empty((c.Ly, c.Lx), dtype=np.float32)
+        check(lib.lb_batch_get_state(self.h, int(i), f.ctypes.data, th.ctypes.data, 0))
+        return f, th
+
+    def set_state(self, i: int, fpost=None, theta=None):
+        f, fp = _host_ptr(fpost, np.float32)
+        t, tp = _host_ptr(theta, np.float32)
+        check(lib.lb_batch_set_state(self.h, int(i), fp, tp, 0))
+
+    def set_wall_temperature(self, i: int, superheat: float, profile=None):
+        prof, pp = _host_ptr(profile, np.float64)
+        check(lib.lb_batch_set_wall_temperature(self.h, int(i), pp, float(superheat)))
+
+    def set_wettability(self, i: int, Gw: float):
+        check(lib.lb_batch_set_wettability(self.h, int(i), float(Gw)))
+
+    def sync(self):
+        check(lib.lb_batch_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.lb_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

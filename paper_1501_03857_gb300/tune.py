@@ -1,0 +1,76 @@
+"""Launch-shape autotuner for the fused step.
+
+Times candidate launch shapes (threads per block and rows per segment) with
+CUDA events on the simulation's stream over a few steps and keeps the
+fastest. Results are cached per problem signature (grid sizes, boundary
+condition) for the life of the process. The state is saved before tuning and
+restored afterwards, so tuning does not advance the simulation.
+"""
+
+from __future__ import annotations
+
+from typing import Dict, Iterable, Optional, Tuple
+
+_CACHE: Dict[tuple, tuple] = {}
+
+SIM_CANDIDATES = tuple((bx, seg) for bx in (64, 128, 256) for seg in (0, 32, 64, 128, 256))
+BATCH_CANDIDATES = tuple((bx, seg) for bx in (64, 128) for seg in (0, 16, 32, 64, 128))
+
+
+def _time(torch, stream, fn, steps: int) -> float:
+    fn(2)  # warm-up for this shape
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn(steps)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def tune_simulation(sim, candidates: Optional[Iterable[Tuple[int, int]]] = None, steps: int = 8):
+    """Pick the fastest (block_x, seg_rows) of the default kernel for `sim`
+    and apply it. Returns (block_x, seg_rows, ms_per_step)."""
+    c = sim.cfg
+    key = ("sim", c.Lx, c.Ly, c.bc_y, c.isothermal)
+    if key not in _CACHE:
+        blob = sim.save()
+        best = None
+        for bx, seg in (candidates or SIM_CANDIDATES):
+            try:
+                sim.set_launch(bx, seg)
+            except Exception:
+                continue
+            ms = _time(sim.torch, sim.stream, sim.step, steps)
+            if best is None or ms < best[2]:
+                best = (bx, seg, ms)
+        sim.load(blob)
+        _CACHE[key] = best
+    bx, seg, ms = _CACHE[key]
+    sim.set_launch(bx, seg)
+    return bx, seg, ms
+
+
+def tune_batch(batch, candidates: Optional[Iterable[Tuple[int, int]]] = None, steps: int = 8):
+    """Pick the fastest (block_x, seg_rows) shared by all instances of
+    `batch` and apply it. Returns (block_x, seg_rows, ms_per_step). The
+    instances' states are restored; their heat-flux accumulators keep the
+    samples of the timing steps (reset them after tuning if that matters)."""
+    key = ("batch",) + tuple((c.Lx, c.Ly, c.bc_y) for c in batch.cfgs)
+    if key not in _CACHE:
+        saved = [batch.get_state(i) for i in range(batch.n)]
+        best = None
+        for bx, seg in (candidates or BATCH_CANDIDATES):
+            try:
+                batch.set_launch(bx, seg)
+            except Exception:
+                continue
+            ms = _time(batch.torch, batch.stream, batch.step, steps)
+            if best is None or ms < best[2]:
+                best = (bx, seg, ms)
+        for i, (f, th) in enumerate(saved):
+            batch.set_state(i, f, th)
+        _CACHE[key] = best
+    bx, seg, ms = _CACHE[key]
+    batch.set_launch(bx, seg)
+    return bx, seg, ms
