@@ -189,6 +189,56 @@ def batched_curve(torch, lb, steps_batch=64, steps_seq=32):
 GRAPH_WARM = 32
 
 
+def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
+    """Gradient of the mean wall heat flux over a 2000-step window of a 256 x 256
+    boiling domain w.r.t. the 256-cell wall temperature profile and G_w
+    (checkpoint every 100 steps): cost against the forward steps alone, and a
+    check against central differences of the same FP32 forward (uniform T_b
+    mode and G_w, h = 1e-4)."""
+    cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
+    Tc = lb.critical_temperature(cfg)
+    sh, Gw = 0.1 * Tc, 0.065
+    st = torch.cuda.current_stream()
+    sim = lb.Simulation(cfg, superheat=sh, Gw=Gw, stream=st)
+    sim.step(200)  # leave the initial transient
+    blob = sim.save()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def forward_J(dtb=0.0, dgw=0.0):
+        sim.load(blob)
+        sim.set_wall_temperature(sh + dtb)
+        sim.set_wettability(Gw + dgw)
+        sim.heat_flux(reset=True)
+        sim.step(nsteps)
+        return sim.heat_flux()["q_mean"]
+
+    forward_J()  # warm-up
+    sim.load(blob)
+    sim.set_wall_temperature(sh)
+    sim.set_wettability(Gw)
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    sim.step(nsteps)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1])
+    sim.load(blob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, dTb, dGw = sim.adjoint(nsteps, ckpt)
+    t_adj = (time.perf_counter() - t0) * 1e3
+    h = 1e-4
+    fd_tb = (forward_J(dtb=h) - forward_J(dtb=-h)) / (2 * h)
+    fd_gw = (forward_J(dgw=h) - forward_J(dgw=-h)) / (2 * h)
+    sim.close()
+    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "J": J,
+            "ms_forward": t_fwd, "ms_adjoint_total": t_adj, "cost_ratio": t_adj / t_fwd,
+            "dJ_dTb_uniform": float(dTb.sum()), "fd_uniform": fd_tb,
+            "rel_err_uniform": abs(float(dTb.sum()) - fd_tb) / abs(fd_tb),
+            "dJ_dGw": dGw, "fd_Gw": fd_gw, "rel_err_Gw": abs(dGw - fd_gw) / abs(fd_gw),
+            "fd": "central differences of the FP32 GPU forward, h = 1e-4"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -329,6 +379,8 @@ def run_ours(args):
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
         if not args.no_batched:
             line["batched"] = batched_curve(torch, lb)
+        if not args.no_adjoint:
+            line["adjoint"] = adjoint_window(torch, lb)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -345,6 +397,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched boiling-curve measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--size", type=int, default=4096, help="domain edge (profiling of smaller cases)")
     args = ap.parse_args()
     global L

@@ -183,6 +183,25 @@ int lb_load(lb_handle* h, const void* host_buf, size_t bytes);
 /* Release the handle (the workspace stays the caller's). */
 int lb_destroy(lb_handle* h);
 
+/* ---- gradients (discrete adjoint) ----------------------------------------- */
+
+/* Device scratch lb_adjoint needs for nsteps steps with a checkpoint every
+ * ckpt_every steps (work fields, checkpoints, one recomputed segment). */
+int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* bytes);
+
+/* Gradient of the window-averaged bottom-wall heat flux
+ * J = (1/nsteps) sum_{n} q(t_n) over the next nsteps steps (Sec. 3.2) with
+ * respect to the bottom-wall temperature profile T_b(x) (dJ_dTb, host [Lx])
+ * and the wettability strength G_w of Eq. 22 (dJ_dGw, host), by the discrete
+ * adjoint (reverse mode) of the step. The state at the window start is held
+ * fixed except its bottom wall row, which is T_b. Runs the nsteps forward
+ * steps (the simulation advances; its heat-flux accumulators are not
+ * touched) storing a checkpoint every ckpt_every steps, then sweeps back
+ * recomputing each segment from its checkpoint. J (host) receives the value.
+ * Wall-bounded runs without ghost layer only. Synchronises. */
+int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes,
+               double* J, double* dJ_dTb, double* dJ_dGw);
+
 /* ---- batches: many independent simulations, one launch per step ---------- */
 
 /* One instance of a batch (the points of a boiling curve, Sec. 3.2-3.3:

@@ -207,6 +207,29 @@ struct lb_handle {
     float* wall_pinned;      // pinned staging of theta_b(x) for the upload
     cudaEvent_t wall_done;   // the last upload from wall_pinned has run
     bool wall_pending;
+    // adjoint: private stream for captured segment graphs, keyed by
+    // (segment length, lambda parity, scratch base)
+    cudaStream_t adj_stream;
+    cudaEvent_t adj_in, adj_out;
+    cudaStream_t adj_stream2;           // recompute stream of the adjoint
+    cudaEvent_t adj_ready[2], adj_free[2];  // segment buffer filled / released
+    struct AdjGraph {
+        int kind;  // 0: recompute into a segment buffer, 1: reverse sweep over it
+        int len, cur, buf, C, nsteps;
+        void* scratch;
+        StepParams params;  // baked into the graph's kernel nodes
+        Launch launch;
+        cudaGraphExec_t exec;
+    };
+    std::vector<AdjGraph> adj_graphs;
+    // plain stepping: STEP_GRAPH-step graphs keyed by the parameters of their
+    // first step (buffers, accumulators, constants) and the launch shape
+    struct StepGraph {
+        StepParams first;
+        Launch launch;
+        cudaGraphExec_t exec;
+    };
+    std::vector<StepGraph> step_graphs;
 };
 
 namespace {
@@ -326,10 +349,103 @@ int upload_wall(lb_handle* h) {
 
 void release(lb_handle* h) {
     if (!h) return;
+    if (h->adj_stream) cudaStreamSynchronize(h->adj_stream);
+    if (h->adj_stream2) cudaStreamSynchronize(h->adj_stream2);
+    for (auto& g : h->adj_graphs) cudaGraphExecDestroy(g.exec);
+    for (int k = 0; k < 2; ++k) {
+        if (h->adj_ready[k]) cudaEventDestroy(h->adj_ready[k]);
+        if (h->adj_free[k]) cudaEventDestroy(h->adj_free[k]);
+    }
+    if (h->adj_stream2) cudaStreamDestroy(h->adj_stream2);
+    for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
+    if (h->adj_in) cudaEventDestroy(h->adj_in);
+    if (h->adj_out) cudaEventDestroy(h->adj_out);
+    if (h->adj_stream) cudaStreamDestroy(h->adj_stream);
     if (h->wall_pending) cudaEventSynchronize(h->wall_done);
     if (h->wall_done) cudaEventDestroy(h->wall_done);
     if (h->wall_pinned) cudaFreeHost(h->wall_pinned);
     delete h;
+}
+
+
+// ---------------------------------------------------------------------------
+// Stepping: runs of STEP_GRAPH steps are replayed from a captured CUDA graph
+// on the handle's private stream (ordered after and before the caller's
+// stream), the rest are single launches. `P` carries the accumulators and
+// constants; its buffers follow h->cur.
+// ---------------------------------------------------------------------------
+
+constexpr int STEP_GRAPH = 32;  // even: the buffer parity returns
+
+int aux_stream(lb_handle* h) {
+    if (!h->adj_stream) {
+        LB_CUDA(cudaStreamCreateWithFlags(&h->adj_stream, cudaStreamNonBlocking), "private stream");
+        LB_CUDA(cudaEventCreateWithFlags(&h->adj_in, cudaEventDisableTiming), "private stream event");
+        LB_CUDA(cudaEventCreateWithFlags(&h->adj_out, cudaEventDisableTiming), "private stream event");
+    }
+    return LB_OK;
+}
+
+int launch_one(lb_handle* h, const StepParams& base, int cur, cudaStream_t q) {
+    StepParams P = base;
+    P.f_in = h->f[cur];
+    P.f_out = h->f[1 - cur];
+    P.th_in = h->t[cur];
+    P.th_out = h->t[1 - cur];
+    LB_CUDA(launch_step(P, h->launch, q), "step launch");
+    return LB_OK;
+}
+
+int run_steps(lb_handle* h, const StepParams& base, int nsteps) {
+    int left = nsteps;
+    if (left >= STEP_GRAPH) {
+        int rc = aux_stream(h);
+        if (rc) return rc;
+        StepParams first = base;
+        first.f_in = h->f[h->cur];
+        first.f_out = h->f[1 - h->cur];
+        first.th_in = h->t[h->cur];
+        first.th_out = h->t[1 - h->cur];
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : h->step_graphs)
+            if (memcmp(&g.first, &first, sizeof(StepParams)) == 0 && memcmp(&g.launch, &h->launch, sizeof(Launch)) == 0)
+                exec = g.exec;
+        cudaStream_t gs = h->adj_stream;
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            LB_CUDA(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int k = 0; k < STEP_GRAPH && rc == LB_OK; ++k) rc = launch_one(h, base, h->cur ^ (k & 1), gs);
+            cudaError_t e = cudaStreamEndCapture(gs, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "step graph");
+            if (h->step_graphs.size() >= 8) {
+                cudaStreamSynchronize(gs);
+                cudaGraphExecDestroy(h->step_graphs.front().exec);
+                h->step_graphs.erase(h->step_graphs.begin());
+            }
+            h->step_graphs.push_back({first, h->launch, exec});
+        }
+        LB_CUDA(cudaEventRecord(h->adj_in, h->st), "cudaEventRecord");
+        LB_CUDA(cudaStreamWaitEvent(gs, h->adj_in, 0), "cudaStreamWaitEvent");
+        for (; left >= STEP_GRAPH; left -= STEP_GRAPH) {
+            LB_CUDA(cudaGraphLaunch(exec, gs), "cudaGraphLaunch");
+            h->steps += STEP_GRAPH;
+        }
+        LB_CUDA(cudaEventRecord(h->adj_out, gs), "cudaEventRecord");
+        LB_CUDA(cudaStreamWaitEvent(h->st, h->adj_out, 0), "cudaStreamWaitEvent");
+    }
+    for (; left > 0; --left) {
+        int rc = launch_one(h, base, h->cur, h->st);
+        if (rc) return rc;
+        h->cur ^= 1;
+        h->steps++;
+    }
+    return LB_OK;
 }
 
 }  // namespace
@@ -409,6 +525,10 @@ int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_th
     h->wall_pinned = nullptr;
     h->wall_done = nullptr;
     h->wall_pending = false;
+    h->adj_stream = nullptr;
+    h->adj_in = h->adj_out = nullptr;
+    h->adj_stream2 = nullptr;
+    h->adj_ready[0] = h->adj_ready[1] = h->adj_free[0] = h->adj_free[1] = nullptr;
     {
         cudaError_t e0 = cudaMallocHost((void**)&h->wall_pinned, grid->Lx * sizeof(float));
         if (e0 == cudaSuccess) e0 = cudaEventCreateWithFlags(&h->wall_done, cudaEventDisableTiming);
@@ -460,17 +580,8 @@ int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_th
 int lb_step(lb_handle* h, int nsteps) {
     if (!h) return fail(LB_E_INVAL, "null handle");
     if (nsteps < 0) return fail(LB_E_INVAL, "nsteps must be >= 0");
-    for (int n = 0; n < nsteps; ++n) {
-        StepParams P = h->base;
-        P.f_in = h->f[h->cur];
-        P.f_out = h->f[1 - h->cur];
-        P.th_in = h->t[h->cur];
-        P.th_out = h->t[1 - h->cur];
-        LB_CUDA(launch_step(P, h->launch, h->st), "step launch");
-        h->cur ^= 1;
-        h->steps++;
-    }
-    return LB_OK;
+    StepParams P = h->base;
+    return run_steps(h, P, nsteps);
 }
 
 int lb_set_wall_temperature(lb_handle* h, const double* Tb_profile, double superheat) {
@@ -990,6 +1101,211 @@ int lb_batch_destroy(lb_batch* b) {
     if (!b) return fail(LB_E_INVAL, "null batch");
     batch_release(b);
     return LB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Gradients of the window-averaged wall heat flux (discrete adjoint)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct AdjLayout {
+    size_t work, acc, lam, ckpt, seg, total;
+    int nck;
+};
+
+AdjLayout adj_layout(const lb_handle* h, const StepParams& P, int nsteps, int C) {
+    AdjLayout L;
+    const size_t state = align256(sizeof(float) * 10 * (size_t)P.plane);
+    L.nck = nsteps / C + 1;
+    L.work = 0;
+    L.acc = align256(L.work + adjoint_work_bytes(P));
+    L.lam = align256(L.acc + sizeof(Acc));
+    L.ckpt = L.lam + 2 * state;
+    L.seg = L.ckpt + (size_t)L.nck * state;
+    L.total = L.seg + 2 * (size_t)C * state;  // two segment buffers
+    (void)h;
+    return L;
+}
+
+int adjoint_check(lb_handle* h, int nsteps, int C) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (nsteps < 1 || C < 1) return fail(LB_E_INVAL, "need nsteps >= 1 and ckpt_every >= 1");
+    if (h->grid.bc_y != LB_BC_WALLS || h->grid.ghost_layer || h->grid.isothermal)
+        return fail(LB_E_INVAL, "the adjoint supports wall-bounded, non-ghost, thermal runs only");
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* bytes) {
+    int rc = adjoint_check(h, nsteps, ckpt_every);
+    if (rc) return rc;
+    if (!bytes) return fail(LB_E_INVAL, "null output");
+    *bytes = adj_layout(h, h->base, nsteps, ckpt_every).total;
+    return LB_OK;
+}
+
+int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes, double* J,
+               double* dJ_dTb, double* dJ_dGw) {
+    int rc = adjoint_check(h, nsteps, ckpt_every);
+    if (rc) return rc;
+    const int C = ckpt_every;
+    const StepParams base = h->base;
+    const AdjLayout L = adj_layout(h, base, nsteps, C);
+    if (!dev_scratch || scratch_bytes < L.total)
+        return fail(LB_E_INVAL, "adjoint scratch of %zu bytes is smaller than the %zu needed", scratch_bytes, L.total);
+    if (((uintptr_t)dev_scratch) & 255) return fail(LB_E_INVAL, "scratch must be 256-byte aligned");
+    char* s = (char*)dev_scratch;
+    const size_t pl = (size_t)base.plane;
+    const size_t state = align256(sizeof(float) * 10 * pl);
+    void* work = s + L.work;
+    Acc* acc = (Acc*)(s + L.acc);
+    auto sf = [&](size_t off, int k) { return (float*)(s + off + (size_t)k * state); };
+    float* lam[2] = {sf(L.lam, 0), sf(L.lam, 1)};
+    cudaStream_t st = h->st;
+
+    // forward: nsteps steps from the current state, J = mean q(t), checkpoints
+    LB_CUDA(cudaMemsetAsync(acc, 0, sizeof(Acc), st), "clear adjoint accumulators");
+    auto save = [&](float* dst, const float* f, const float* t) -> int {
+        LB_CUDA(cudaMemcpyAsync(dst, f, sizeof(float) * 9 * pl, cudaMemcpyDeviceToDevice, st), "checkpoint copy");
+        LB_CUDA(cudaMemcpyAsync(dst + 9 * pl, t, sizeof(float) * pl, cudaMemcpyDeviceToDevice, st),
+                "checkpoint copy");
+        return LB_OK;
+    };
+    if ((rc = save(sf(L.ckpt, 0), h->f[h->cur], h->t[h->cur]))) return rc;
+    {
+        StepParams P = base;
+        P.acc = acc;
+        for (int n0 = 0; n0 < nsteps; n0 += C) {
+            const int len = std::min(C, nsteps - n0);
+            if ((rc = run_steps(h, P, len))) return rc;
+            if (n0 + len == nsteps) break;
+            if ((rc = save(sf(L.ckpt, (n0 + len) / C), h->f[h->cur], h->t[h->cur]))) return rc;
+        }
+    }
+    Acc a;
+    LB_CUDA(cudaMemcpyAsync(&a, acc, sizeof(Acc), cudaMemcpyDeviceToHost, st), "read J");
+    LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (a.err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature in the window");
+    if (a.err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument < 0 in the window (EOS domain)");
+    const double Jv = a.q_n > 0 ? a.q_sum / a.q_n : 0.0;
+    const float lq = (float)(1.0 / nsteps);
+
+    // reverse: segments from the last checkpoint back to the first. Segment
+    // k is recomputed from its checkpoint into one of two buffers on one
+    // private stream while the reverse sweep of segment k + 1 runs on another;
+    // both are captured CUDA graphs.
+    LB_CUDA(cudaMemsetAsync(lam[0], 0, state, st), "clear lambda");
+    LB_CUDA(adjoint_grads_reset(base, work, st), "clear gradients");
+    if ((rc = aux_stream(h))) return rc;
+    if (!h->adj_stream2) {
+        LB_CUDA(cudaStreamCreateWithFlags(&h->adj_stream2, cudaStreamNonBlocking), "adjoint stream");
+        for (int b2 = 0; b2 < 2; ++b2) {
+            LB_CUDA(cudaEventCreateWithFlags(&h->adj_ready[b2], cudaEventDisableTiming), "adjoint event");
+            LB_CUDA(cudaEventCreateWithFlags(&h->adj_free[b2], cudaEventDisableTiming), "adjoint event");
+        }
+    }
+    cudaStream_t rs = h->adj_stream;   // reverse sweeps
+    cudaStream_t cs = h->adj_stream2;  // recomputation
+    LB_CUDA(cudaEventRecord(h->adj_in, st), "cudaEventRecord");
+    LB_CUDA(cudaStreamWaitEvent(rs, h->adj_in, 0), "cudaStreamWaitEvent");
+    LB_CUDA(cudaStreamWaitEvent(cs, h->adj_in, 0), "cudaStreamWaitEvent");
+    auto seg_state = [&](int buf, int j) { return sf(L.seg, buf * C + j); };
+    auto recompute = [&](int len, int buf, cudaStream_t q) -> int {
+        for (int j = 1; j < len; ++j) {
+            StepParams P = base;
+            P.acc = acc;
+            P.f_in = seg_state(buf, j - 1);
+            P.th_in = seg_state(buf, j - 1) + 9 * pl;
+            P.f_out = seg_state(buf, j);
+            P.th_out = seg_state(buf, j) + 9 * pl;
+            LB_CUDA(launch_step(P, h->launch, q), "adjoint recompute step");
+        }
+        return LB_OK;
+    };
+    auto sweep = [&](int len, int buf, int c0, cudaStream_t q) -> int {
+        int c = c0;
+        for (int j = len - 1; j >= 0; --j) {
+            const float* fs = seg_state(buf, j);
+            LB_CUDA(adjoint_reverse_step(base, work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl, lam[1 - c],
+                                         lam[1 - c] + 9 * pl, lq, q),
+                    "adjoint reverse step");
+            c ^= 1;
+        }
+        return LB_OK;
+    };
+    auto graph_of = [&](int kind, int len, int buf, int c0, cudaStream_t q, cudaGraphExec_t* out) -> int {
+        for (auto& g : h->adj_graphs)
+            if (g.kind == kind && g.len == len && g.buf == buf && g.cur == c0 && g.C == C && g.nsteps == nsteps &&
+                g.scratch == dev_scratch && memcmp(&g.params, &base, sizeof(StepParams)) == 0 &&
+                memcmp(&g.launch, &h->launch, sizeof(Launch)) == 0) {
+                *out = g.exec;
+                return LB_OK;
+            }
+        cudaGraph_t graph = nullptr;
+        LB_CUDA(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int r = kind == 0 ? recompute(len, buf, q) : sweep(len, buf, c0, q);
+        cudaError_t e = cudaStreamEndCapture(q, &graph);
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint graph");
+        if (h->adj_graphs.size() >= 16) {
+            cudaStreamSynchronize(rs);
+            cudaStreamSynchronize(cs);
+            cudaGraphExecDestroy(h->adj_graphs.front().exec);
+            h->adj_graphs.erase(h->adj_graphs.begin());
+        }
+        h->adj_graphs.push_back({kind, len, c0, buf, C, nsteps, dev_scratch, base, h->launch, exec});
+        *out = exec;
+        return LB_OK;
+    };
+    const int kmax = (nsteps - 1) / C;
+    auto fill = [&](int k) -> int {  // recompute segment k into buffer k & 1
+        const int buf = k & 1, len = std::min(C, nsteps - k * C);
+        if (k + 2 <= kmax) LB_CUDA(cudaStreamWaitEvent(cs, h->adj_free[buf], 0), "cudaStreamWaitEvent");
+        LB_CUDA(cudaMemcpyAsync(seg_state(buf, 0), sf(L.ckpt, k), sizeof(float) * 10 * pl, cudaMemcpyDeviceToDevice,
+                                cs),
+                "checkpoint copy");
+        if (len > 1) {
+            cudaGraphExec_t g = nullptr;
+            int r = graph_of(0, len, buf, 0, cs, &g);
+            if (r) return r;
+            LB_CUDA(cudaGraphLaunch(g, cs), "cudaGraphLaunch");
+        }
+        LB_CUDA(cudaEventRecord(h->adj_ready[buf], cs), "cudaEventRecord");
+        return LB_OK;
+    };
+    if ((rc = fill(kmax))) return rc;
+    int cur = 0;
+    for (int k = kmax; k >= 0; --k) {
+        const int buf = k & 1, len = std::min(C, nsteps - k * C);
+        if (k > 0 && (rc = fill(k - 1))) return rc;  // overlaps the sweep below
+        LB_CUDA(cudaStreamWaitEvent(rs, h->adj_ready[buf], 0), "cudaStreamWaitEvent");
+        cudaGraphExec_t g = nullptr;
+        if ((rc = graph_of(1, len, buf, cur, rs, &g))) return rc;
+        LB_CUDA(cudaGraphLaunch(g, rs), "cudaGraphLaunch");
+        LB_CUDA(cudaEventRecord(h->adj_free[buf], rs), "cudaEventRecord");
+        cur ^= (len & 1);
+    }
+    LB_CUDA(cudaEventRecord(h->adj_out, rs), "cudaEventRecord");
+    LB_CUDA(cudaStreamWaitEvent(st, h->adj_out, 0), "cudaStreamWaitEvent");
+    LB_CUDA(cudaStreamWaitEvent(cs, h->adj_out, 0), "cudaStreamWaitEvent");
+    double dGw = 0.0;
+    LB_CUDA(adjoint_grads_finish(base, work, lam[cur] + 9 * pl, dJ_dTb, &dGw, st), "read gradients");
+    LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (J) *J = Jv;
+    if (dJ_dGw) *dJ_dGw = dGw;
+    return check_device_errors(h);
 }
 
 }  // extern "C"

@@ -52,6 +52,17 @@ cudaError_t launch_init(const StepParams& P, const float* rho0, float* f, float*
 cudaError_t launch_macro(const StepParams& P, float* scratch, float* rho, float* ux, float* uy,
                          float* T, int ostride, cudaStream_t st);
 
+// Discrete adjoint of one step (lb_adjoint.cu): work bytes, reset of the
+// FP64 gradient accumulators, one reverse step, and the final read-out
+// (which adds the initial wall row's lambda_theta to dJ/d theta_b).
+size_t adjoint_work_bytes(const StepParams& P);
+cudaError_t adjoint_grads_reset(const StepParams& P, void* work, cudaStream_t st);
+cudaError_t adjoint_reverse_step(const StepParams& P, void* work, const float* fstar, const float* theta,
+                                 const float* lf_in, const float* lt_in, float* lf_out, float* lt_out, float lq,
+                                 cudaStream_t st);
+cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* lt0, double* dTb_host,
+                                 double* dGw_host, cudaStream_t st);
+
 // Record the message lb_last_error() returns on this thread.
 void set_last_error(const char* msg);
 

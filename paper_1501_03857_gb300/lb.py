@@ -87,6 +87,8 @@ def _load():
         "lb_batch_info": [P, I64P, C.POINTER(I), C.POINTER(I)],
         "lb_batch_sync": [P],
         "lb_batch_destroy": [P],
+        "lb_adjoint_scratch_bytes": [P, I, I, C.POINTER(C.c_size_t)],
+        "lb_adjoint": [P, I, I, P, SZ, DP, P, DP],
         "lb_fields_noalloc": [C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), D, D, P, P, P, P, P,
                               P, P],
     }
@@ -289,6 +291,21 @@ class Simulation:
     def sync(self):
         check(lib.lb_sync(self.h))
 
+    def adjoint(self, nsteps: int, ckpt_every: int = 100):
+        """J = mean wall heat flux over the next nsteps steps and its gradients
+        dJ/d(T_b(x) - T_s) [Lx] and dJ/dG_w by the discrete adjoint
+        (lb_adjoint). Advances the simulation by nsteps."""
+        torch = self.torch
+        n = C.c_size_t()
+        check(lib.lb_adjoint_scratch_bytes(self.h, int(nsteps), int(ckpt_every), C.byref(n)))
+        scratch = torch.empty(n.value + 256, dtype=torch.uint8, device="cuda")
+        base = scratch.data_ptr()
+        J, dGw = C.c_double(), C.c_double()
+        dTb = np.zeros(self.Lx, dtype=np.float64)
+        check(lib.lb_adjoint(self.h, int(nsteps), int(ckpt_every), base + ((-base) % 256), n.value, C.byref(J),
+                             dTb.ctypes.data, C.byref(dGw)))
+        return J.value, dTb, dGw.value
+
     def save(self) -> bytes:
         n = C.c_size_t()
         check(lib.lb_save_bytes(self.h, C.byref(n)))
@@ -397,3 +414,36 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_fn():
+    import torch
+
+    class HeatFluxWindow(torch.autograd.Function):
+        """J = mean bottom-wall heat flux over a window of `nsteps` steps as a
+        differentiable function of the wall superheat profile Tb (tensor [Lx],
+        T_b(x) - T_s) and the wettability Gw (0-d tensor); the window starts
+        from the state saved in `blob`. Gradients come from the hand-written
+        discrete adjoint (lb_adjoint)."""
+
+        @staticmethod
+        def forward(ctx, Tb, Gw, sim, blob, nsteps, ckpt_every):
+            sim.load(blob)
+            sim.set_wall_temperature(0.0, Tb.detach().double().cpu().numpy())
+            sim.set_wettability(float(Gw))
+            J, dTb, dGw = sim.adjoint(int(nsteps), int(ckpt_every))
+            ctx.save_for_backward(torch.as_tensor(dTb, dtype=Tb.dtype, device=Tb.device),
+                                  torch.as_tensor(dGw, dtype=Gw.dtype, device=Gw.device))
+            return torch.as_tensor(J, dtype=torch.float64, device=Tb.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dTb, dGw = ctx.saved_tensors
+            return gJ.to(dTb.dtype) * dTb, gJ.to(dGw.dtype) * dGw, None, None, None, None
+
+    return HeatFluxWindow
+
+
+def heat_flux_window(Tb, Gw, sim, blob, nsteps, ckpt_every=100):
+    """Differentiable J(Tb, Gw); see HeatFluxWindow."""
+    return _autograd_fn().apply(Tb, Gw, sim, blob, nsteps, ckpt_every)

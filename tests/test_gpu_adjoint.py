@@ -1,0 +1,118 @@
+"""The hand-written discrete adjoint against the FP64 oracle: gradients of
+the window-averaged wall heat flux with respect to the wall temperature
+profile and G_w, compared with the oracle's autograd adjoint and with FP64
+central differences of the oracle (the benchmark spec's bound: 1e-3 relative)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1501_03857_gb300 import inputs
+from parity_util import oracle_initial_fp32, oracle_params
+
+pytestmark = pytest.mark.gpu
+F64 = torch.float64
+
+
+@pytest.fixture(scope="module")
+def lb():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1501_03857_gb300 import lb as lbmod
+    return lbmod
+
+
+def setup(lb, Lx=24, Ly=16, superheat=0.012, Gw=0.05, seed=3):
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_WALLS, pool_height=0.45 * Ly)
+    rv, rl = lb.coexistence(cfg)
+    rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.45 * Ly, noise_amp=1e-2, seed=seed)
+    prof = superheat + 0.003 * np.sin(2 * np.pi * np.arange(Lx) / Lx)
+    P = oracle_params(cfg, rho0, superheat=0.0, profile=prof, Gw=Gw)
+    f0, th0 = oracle_initial_fp32(rho0, P)
+    return cfg, rho0, prof, P, f0, th0
+
+
+def oracle_J(P, f0, th0, tb, gw, n):
+    """J(theta_b, G_w) of the oracle with the window-start wall row = theta_b."""
+    P.theta_b = tb
+    P.Gw = gw
+    f = torch.tensor(f0, dtype=F64)
+    th = torch.cat([tb.view(1, -1), torch.tensor(th0[1:], dtype=F64)], 0)
+    qs = []
+    for _ in range(n):
+        f, th, info = O.step(f, th, P)
+        qs.append(info.q)
+    return torch.stack(qs).mean()
+
+
+def gpu_adjoint(lb, cfg, rho0, prof, Gw, f0, th0, n, ckpt):
+    sim = lb.Simulation(cfg, superheat=0.0, profile=prof, Gw=Gw, rho0=rho0)
+    sim.set_state(f0, th0)
+    return sim.adjoint(n, ckpt)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_adjoint_matches_oracle_autograd(lb):
+    n = 12
+    cfg, rho0, prof, P, f0, th0 = setup(lb)
+    tb = torch.tensor(prof, dtype=F64, requires_grad=True)
+    gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
+    Jo = oracle_J(P, f0, th0, tb, gw, n)
+    gtb, ggw = torch.autograd.grad(Jo, (tb, gw))
+    J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=5)
+    print(f"J rel {abs(J / float(Jo) - 1):.2e} dTb rel {rel(dTb, gtb.numpy()):.2e} "
+          f"dGw rel {abs(dGw / float(ggw) - 1):.2e}")
+    assert abs(J / float(Jo) - 1) < 1e-5
+    assert rel(dTb, gtb.numpy()) < 1e-3, rel(dTb, gtb.numpy())
+    assert abs(dGw / float(ggw) - 1) < 1e-3, (dGw, float(ggw))
+
+
+def test_adjoint_matches_central_differences(lb):
+    """Central differences (h = 1e-4) of the FP64 oracle on single cells of
+    T_b, the uniform T_b mode and G_w."""
+    n = 30
+    cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=32, Ly=20, seed=5)
+    J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=7)
+    h = 1e-4
+    tb0 = torch.tensor(prof, dtype=F64)
+    Jf = lambda tb, gw: float(oracle_J(P, f0, th0, tb, torch.tensor(gw, dtype=F64), n))
+    for x in (0, 9, 31):
+        e = torch.zeros(cfg.Lx, dtype=F64)
+        e[x] = h
+        fd = (Jf(tb0 + e, 0.05) - Jf(tb0 - e, 0.05)) / (2 * h)
+        print(f"x={x} adjoint {dTb[x]:.6e} fd {fd:.6e} rel {abs(dTb[x] - fd) / abs(fd):.2e}")
+        assert abs(dTb[x] - fd) <= 1e-3 * abs(fd) + 1e-9, (x, dTb[x], fd)
+    fd = (Jf(tb0 + h, 0.05) - Jf(tb0 - h, 0.05)) / (2 * h)
+    assert abs(dTb.sum() - fd) <= 1e-3 * abs(fd), (dTb.sum(), fd)
+    fd = (Jf(tb0, 0.05 + h) - Jf(tb0, 0.05 - h)) / (2 * h)
+    assert abs(dGw - fd) <= 1e-3 * abs(fd), (dGw, fd)
+
+
+def test_checkpoint_interval_does_not_change_gradients(lb):
+    n = 20
+    cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=30, Ly=14, seed=7)
+    a = gpu_adjoint(lb, cfg, rho0, prof, 0.08, f0, th0, n, ckpt=1)
+    b = gpu_adjoint(lb, cfg, rho0, prof, 0.08, f0, th0, n, ckpt=6)
+    c = gpu_adjoint(lb, cfg, rho0, prof, 0.08, f0, th0, n, ckpt=100)
+    for other in (b, c):
+        assert other[0] == a[0]
+        assert np.array_equal(other[1], a[1])
+        assert abs(other[2] - a[2]) <= 1e-12 * abs(a[2])
+
+
+def test_autograd_function(lb):
+    cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=20, Ly=12, seed=9)
+    sim = lb.Simulation(cfg, superheat=0.0, profile=prof, Gw=0.05, rho0=rho0)
+    sim.set_state(f0, th0)
+    blob = sim.save()
+    Tb = torch.tensor(prof, dtype=F64, requires_grad=True)
+    Gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
+    J = lb.heat_flux_window(Tb, Gw, sim, blob, 10, 4)
+    J.backward()
+    _, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, 10, 4)
+    assert np.allclose(Tb.grad.numpy(), dTb, rtol=1e-12, atol=0)
+    assert abs(float(Gw.grad) - dGw) <= 1e-12 * abs(dGw)
