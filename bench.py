@@ -363,8 +363,8 @@ def run_ours(args):
             # the kernel source is the one that was profiled
             import hashlib
             rec = json.load(open(tp))
-            src = os.path.join(ROOT, "paper_1501_03857_gb300", "csrc", "lb_step3.cu")
-            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            ksrc = os.path.join(ROOT, "paper_1501_03857_gb300", "csrc", "lb_step3.cu")
+            sha = hashlib.sha256(open(ksrc, "rb").read()).hexdigest()[:16]
             if rec.get("source_sha256_16") == sha:
                 traffic = rec.get("lb_step_dual")
         info = sim.info()

@@ -41,8 +41,10 @@ struct P2 {
     static __device__ __forceinline__ P2 bc(float s) { return P2(s, s); }
 };
 __device__ __forceinline__ P2 operator+(P2 a, P2 b) { return P2(__fadd2_rn(a.v, b.v)); }
-__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
-__device__ __forceinline__ P2 operator-(P2 a) { return P2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+// a - b is a paired add of -b: the negation is an operand modifier, so no
+// (-1, -1) register pair has to be held for it
+__device__ __forceinline__ P2 operator-(P2 a, P2 b) { return P2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
+__device__ __forceinline__ P2 operator-(P2 a) { return P2(make_float2(-a.v.x, -a.v.y)); }
 __device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(__fmul2_rn(a.v, b.v)); }
 __device__ __forceinline__ P2 operator*(float s, P2 b) { return P2(__fmul2_rn(make_float2(s, s), b.v)); }
 __device__ __forceinline__ P2 fma2(P2 a, P2 b, P2 c) { return P2(__ffma2_rn(a.v, b.v, c.v)); }
