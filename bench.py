@@ -194,7 +194,8 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     boiling domain w.r.t. the 256-cell wall temperature profile and G_w
     (checkpoint every 100 steps): cost against the forward steps alone, and a
     check against central differences of the same FP32 forward (uniform T_b
-    mode and G_w, h = 1e-4)."""
+    mode and G_w, h = 1e-4). The timed adjoint call follows an untimed one, so
+    graph capture and scratch allocation are not in it."""
     cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
     Tc = lb.critical_temperature(cfg)
     sh, Gw = 0.1 * Tc, 0.065
@@ -223,6 +224,8 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     torch.cuda.synchronize()
     t_fwd = ev[0].elapsed_time(ev[1])
     sim.load(blob)
+    sim.adjoint(nsteps, ckpt)  # warm-up: captures the segment graphs
+    sim.load(blob)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     J, dTb, dGw = sim.adjoint(nsteps, ckpt)
@@ -233,10 +236,57 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     sim.close()
     return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "J": J,
             "ms_forward": t_fwd, "ms_adjoint_total": t_adj, "cost_ratio": t_adj / t_fwd,
+            "mlups_adjoint": L * L * nsteps / (t_adj * 1e-3) / 1e6,
+            "mlups_forward": L * L * nsteps / (t_fwd * 1e-3) / 1e6,
             "dJ_dTb_uniform": float(dTb.sum()), "fd_uniform": fd_tb,
             "rel_err_uniform": abs(float(dTb.sum()) - fd_tb) / abs(fd_tb),
             "dJ_dGw": dGw, "fd_Gw": fd_gw, "rel_err_Gw": abs(dGw - fd_gw) / abs(fd_gw),
             "fd": "central differences of the FP32 GPU forward, h = 1e-4"}
+
+
+# Algorithmic bytes per lattice update of one reverse step: the stored state
+# (9 populations + theta) read once and the adjoint state read and written
+# once, plus the forward recomputation of the step from its checkpoint.
+ADJ_BYTES_PER_LU = 40 + 80 + 80
+
+
+def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
+    """The adjoint on a domain larger than L2 (2048 x 2048: 168 MB per state):
+    reverse-sweep time per step = (adjoint call - forward steps) / nsteps, and
+    its HBM roofline at ADJ_BYTES_PER_LU."""
+    cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
+    Tc = lb.critical_temperature(cfg)
+    st = torch.cuda.current_stream()
+    sim = lb.Simulation(cfg, superheat=0.1 * Tc, Gw=0.065, stream=st)
+    sim.step(20)
+    blob = sim.save()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sim.step(nsteps)
+    sim.load(blob)
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    sim.step(nsteps)
+    ev[1].record(st)
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1])
+    sim.load(blob)
+    sim.adjoint(nsteps, ckpt)  # warm-up: graph capture, scratch
+    sim.load(blob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.adjoint(nsteps, ckpt)
+    t_adj = (time.perf_counter() - t0) * 1e3
+    sim.close()
+    cells = L * L
+    rev_ms = (t_adj - t_fwd) / nsteps
+    peak, _ = measured_peaks()
+    achieved = ADJ_BYTES_PER_LU * cells / (rev_ms * 1e-3) / 1e9
+    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "ms_forward_per_step": t_fwd / nsteps,
+            "ms_reverse_per_step": rev_ms, "mlups_reverse": cells / (rev_ms * 1e-3) / 1e6,
+            "mlups_adjoint": cells * nsteps / (t_adj * 1e-3) / 1e6,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "bytes_per_lu": ADJ_BYTES_PER_LU,
+                         "what": "reverse sweep incl. forward recomputation, per step"}}
 
 
 def run_reference(args):
@@ -381,6 +431,7 @@ def run_ours(args):
             line["batched"] = batched_curve(torch, lb)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_window(torch, lb)
+            line["adjoint"]["large"] = adjoint_roofline(torch, lb)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -399,7 +450,15 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched boiling-curve measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--size", type=int, default=4096, help="domain edge (profiling of smaller cases)")
+    ap.add_argument("--adjoint-only", type=str, default=None, metavar="L,STEPS,CKPT",
+                    help="only the large-domain adjoint measurement, e.g. 2048,8,4 (profiling)")
     args = ap.parse_args()
+    if args.adjoint_only:
+        import torch
+        from paper_1501_03857_gb300 import lb
+        Ls, ns, ck = (int(v) for v in args.adjoint_only.split(","))
+        print(json.dumps({"adjoint_large": adjoint_roofline(torch, lb, Ls, ns, ck)}), flush=True)
+        return
     global L
     L = args.size
     WORKLOAD["Lx"] = WORKLOAD["Ly"] = L
