@@ -6,3 +6,4 @@ product path (``paper_1501_03857_gb300``) never imports, links or executes it.
 """
 
 from .lbm import *  # noqa: F401,F403
+from .wetting import cap_density, contact_angle_cap  # noqa: F401

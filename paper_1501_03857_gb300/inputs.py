@@ -76,6 +76,19 @@ def droplet_density(Lx, Ly, rho_l, rho_v, radius, cx=None, cy=None, width=5.0, n
     return _finish(rho, noise_amp, seed)
 
 
+def sessile_density(Lx, Ly, rho_l, rho_v, radius, cx=None, cy=0.0, width=5.0, noise_amp=0.0, seed=1):
+    """A liquid circle of the given radius centred at (cx, cy) in vapour, for a
+    droplet on the bottom wall (cy = 0: a half disc standing on the wall row);
+    tanh interface, periodic in x (minimum-image distance)."""
+    cx = Lx / 2.0 if cx is None else cx
+    y, x = np.mgrid[0:Ly, 0:Lx].astype(np.float64)
+    dx = np.abs(x - cx)
+    dx = np.minimum(dx, Lx - dx)
+    r = np.hypot(dx, y - cy)
+    rho = 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * np.tanh(2.0 * (r - radius) / width)
+    return _finish(rho, noise_amp, seed)
+
+
 def bubble_layout(Lx, Ly, n_bubbles, r_min, r_max, seed, wall_gap=3, max_tries=200000):
     """Non-overlapping circles (cx, cy, r), radius uniform in [r_min, r_max],
     centres uniform, rejection-sampled with draws from the seed's stream."""
