@@ -261,6 +261,44 @@ int lb_batch_sync(lb_batch* b);
 /* Release the batch (the workspace stays the caller's). */
 int lb_batch_destroy(lb_batch* b);
 
+/* ---- pressure probes and the EOS pressure (Sec. 3.2, Fig. 3) ------------- */
+
+/* Fig. 3 follows the pressure at the central point of the top wall while
+ * bubbles rise and merge into the vapour above the pool. A probe records,
+ * after every step t run through lb_step (and the forward pass of
+ * lb_adjoint), the density rho^t, the temperature T^t = T_s + theta^t and
+ * the pressure p = p_EOS(rho^t, T^t) of Eq. 21 at one cell: exactly the rho
+ * and T the step used for psi there (rho^t is the sum of the stored
+ * post-collision populations, which the collision conserves). With probes
+ * set, each step is followed by one small single-block kernel.
+ *
+ * The ring is a caller-owned device buffer of lb_probe_ring_bytes(n,
+ * capacity) bytes, 256-byte aligned: a 256-byte header, then for probe k
+ * and record r the four floats (rho, T, p, 0) at float offset
+ * 64 + 4 * (k * capacity + r). The s-th probed step (from 0, counted
+ * since lb_set_probes) goes to record s % capacity, so the ring keeps the
+ * last `capacity` steps; lb_probe_read returns them in time order. The
+ * header's first 8 bytes are the count of probed steps (uint64). */
+#define LB_PROBE_MAX 8
+
+int lb_probe_ring_bytes(int n, int capacity, size_t* bytes);
+
+/* Probe cells (x[k], y[k]), k < n <= LB_PROBE_MAX, 0 <= x < Lx, 0 <= y < Ly;
+ * n = 0 removes the probes. Resets the ring's count. The ring must stay
+ * allocated while probes are set. */
+int lb_set_probes(lb_handle* h, int n, const int* x, const int* y, void* dev_ring, size_t ring_bytes,
+                  int capacity);
+
+/* Synchronises the handle's stream, then copies the newest m = min(count,
+ * capacity, max_records) records of every probe, oldest first, into
+ * out[k][j][0..2] = (rho, T, p) (host, n * m * 3 floats); *count = steps
+ * probed since lb_set_probes, *m_out = m. Does not clear the ring. */
+int lb_probe_read(lb_handle* h, int max_records, float* out, int64_t* count, int* m_out);
+
+/* p_EOS(rho_i, T_i) of Eq. 21 for n host values, in FP64 (diagnostics:
+ * pressure fields, the Laplace test of a bubble). */
+int lb_eos_pressure(const lb_eos* eos, int64_t n, const float* rho, const float* T, double* p);
+
 /* ---- no-allocation variant (not part of the paper's method) -------------- */
 
 /* Largest grid (Lx * Ly cells) lb_fields_noalloc accepts. */

@@ -130,4 +130,35 @@ cudaError_t launch_mass(const StepParams& P, const float* f, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One block: thread k < n handles probe k. rho^t is the sum of the stored
+// post-collision populations (the collision conserves it), T^t = T_s +
+// theta^t, and p the Peng-Robinson pressure of Eq. 21 in FP64.
+__global__ void probe_kernel(const ProbeArgs A) {
+    const int k = threadIdx.x;
+    unsigned long long* count = reinterpret_cast<unsigned long long*>(A.ring);
+    const unsigned long long s = *count;
+    __syncthreads();
+    if (k < A.n) {
+        const int i = A.y[k] * A.pitch + A.x[k];
+        float rho = 0.f;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) rho += A.f[a * A.plane + i];
+        const double r = rho, T = A.Ts + (double)A.th[i];
+        const double br = A.b * r, ph = A.k0 - A.k1 * sqrt(T);
+        const double p = A.R * r * T / (1.0 - br) - A.a * ph * ph * r * r / (1.0 + 2.0 * br - br * br);
+        float* rec = A.ring + 64 + 4 * ((size_t)k * A.cap + (size_t)(s % (unsigned long long)A.cap));
+        rec[0] = rho;
+        rec[1] = (float)T;
+        rec[2] = (float)p;
+        rec[3] = 0.f;
+    }
+    __syncthreads();
+    if (k == 0) *count = s + 1;
+}
+
+cudaError_t launch_probe(const ProbeArgs& A, cudaStream_t st) {
+    probe_kernel<<<1, 32, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
 }  // namespace lbgpu

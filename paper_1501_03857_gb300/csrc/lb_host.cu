@@ -227,9 +227,12 @@ struct lb_handle {
     struct StepGraph {
         StepParams first;
         Launch launch;
+        ProbeArgs probe;
         cudaGraphExec_t exec;
     };
     std::vector<StepGraph> step_graphs;
+    // pressure probes (n = 0: off); f and th are filled per launch
+    ProbeArgs probe;
 };
 
 namespace {
@@ -393,6 +396,12 @@ int launch_one(lb_handle* h, const StepParams& base, int cur, cudaStream_t q) {
     P.th_in = h->t[cur];
     P.th_out = h->t[1 - cur];
     LB_CUDA(launch_step(P, h->launch, q), "step launch");
+    if (h->probe.n > 0) {
+        ProbeArgs A = h->probe;
+        A.f = P.f_out;
+        A.th = P.th_in;
+        LB_CUDA(launch_probe(A, q), "probe launch");
+    }
     return LB_OK;
 }
 
@@ -408,7 +417,8 @@ int run_steps(lb_handle* h, const StepParams& base, int nsteps) {
         first.th_out = h->t[1 - h->cur];
         cudaGraphExec_t exec = nullptr;
         for (auto& g : h->step_graphs)
-            if (memcmp(&g.first, &first, sizeof(StepParams)) == 0 && memcmp(&g.launch, &h->launch, sizeof(Launch)) == 0)
+            if (memcmp(&g.first, &first, sizeof(StepParams)) == 0 && memcmp(&g.launch, &h->launch, sizeof(Launch)) == 0 &&
+                memcmp(&g.probe, &h->probe, sizeof(ProbeArgs)) == 0)
                 exec = g.exec;
         cudaStream_t gs = h->adj_stream;
         if (!exec) {
@@ -428,7 +438,7 @@ int run_steps(lb_handle* h, const StepParams& base, int nsteps) {
                 cudaGraphExecDestroy(h->step_graphs.front().exec);
                 h->step_graphs.erase(h->step_graphs.begin());
             }
-            h->step_graphs.push_back({first, h->launch, exec});
+            h->step_graphs.push_back({first, h->launch, h->probe, exec});
         }
         LB_CUDA(cudaEventRecord(h->adj_in, h->st), "cudaEventRecord");
         LB_CUDA(cudaStreamWaitEvent(gs, h->adj_in, 0), "cudaStreamWaitEvent");
@@ -788,6 +798,89 @@ int lb_load(lb_handle* h, const void* host_buf, size_t bytes) {
     rc = upload_wall(h);
     if (rc) return rc;
     LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    return LB_OK;
+}
+
+int lb_probe_ring_bytes(int n, int capacity, size_t* bytes) {
+    if (!bytes) return fail(LB_E_INVAL, "null output");
+    if (n < 1 || n > kProbeMax) return fail(LB_E_INVAL, "probe count %d outside 1..%d", n, kProbeMax);
+    if (capacity < 1 || capacity > (1 << 26)) return fail(LB_E_INVAL, "probe capacity %d outside 1..2^26", capacity);
+    *bytes = 256 + sizeof(float) * 4 * (size_t)n * (size_t)capacity;
+    return LB_OK;
+}
+
+int lb_set_probes(lb_handle* h, int n, const int* x, const int* y, void* dev_ring, size_t ring_bytes,
+                  int capacity) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (n == 0) {
+        memset(&h->probe, 0, sizeof(ProbeArgs));
+        return LB_OK;
+    }
+    size_t need = 0;
+    int rc = lb_probe_ring_bytes(n, capacity, &need);
+    if (rc) return rc;
+    if (!x || !y || !dev_ring) return fail(LB_E_INVAL, "null argument");
+    if (((uintptr_t)dev_ring) & 255) return fail(LB_E_INVAL, "probe ring must be 256-byte aligned");
+    if (ring_bytes < need) return fail(LB_E_INVAL, "probe ring of %zu bytes is smaller than the %zu needed", ring_bytes, need);
+    for (int k = 0; k < n; ++k)
+        if (x[k] < 0 || x[k] >= h->grid.Lx || y[k] < 0 || y[k] >= h->grid.Ly)
+            return fail(LB_E_INVAL, "probe %d at (%d, %d) is outside the %d x %d grid", k, x[k], y[k], h->grid.Lx,
+                        h->grid.Ly);
+    ProbeArgs A;
+    memset(&A, 0, sizeof(A));
+    A.ring = (float*)dev_ring;
+    A.plane = (int)h->lay.plane;
+    A.pitch = h->lay.pitch;
+    A.n = n;
+    A.cap = capacity;
+    for (int k = 0; k < n; ++k) {
+        A.x[k] = x[k];
+        A.y[k] = y[k];
+    }
+    const Pr e(h->eos);
+    A.a = e.a;
+    A.b = e.b;
+    A.R = e.R;
+    A.Ts = h->Ts;
+    A.k0 = 1.0 + e.kappa;
+    A.k1 = e.kappa / std::sqrt(e.Tc);
+    LB_CUDA(cudaMemsetAsync(dev_ring, 0, 256, h->st), "clear probe ring");
+    h->probe = A;
+    return LB_OK;
+}
+
+int lb_probe_read(lb_handle* h, int max_records, float* out, int64_t* count, int* m_out) {
+    if (!h) return fail(LB_E_INVAL, "null handle");
+    if (h->probe.n == 0) return fail(LB_E_INVAL, "no probes are set");
+    if (max_records < 0 || (max_records > 0 && !out)) return fail(LB_E_INVAL, "bad output buffer");
+    const ProbeArgs& A = h->probe;
+    unsigned long long n = 0;
+    LB_CUDA(cudaMemcpyAsync(&n, A.ring, sizeof(n), cudaMemcpyDeviceToHost, h->st), "read probe count");
+    LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    const long long m = std::min<long long>(std::min<long long>((long long)n, A.cap), max_records);
+    if (count) *count = (int64_t)n;
+    if (m_out) *m_out = (int)m;
+    if (m == 0) return LB_OK;
+    std::vector<float> ring((size_t)A.n * A.cap * 4);
+    LB_CUDA(cudaMemcpy(ring.data(), A.ring + 64, ring.size() * sizeof(float), cudaMemcpyDeviceToHost),
+            "read probe ring");
+    for (int k = 0; k < A.n; ++k)
+        for (long long j = 0; j < m; ++j) {
+            const unsigned long long step = n - (unsigned long long)m + (unsigned long long)j;
+            const float* r = &ring[((size_t)k * A.cap + (size_t)(step % (unsigned long long)A.cap)) * 4];
+            float* o = out + ((size_t)k * m + (size_t)j) * 3;
+            o[0] = r[0];
+            o[1] = r[1];
+            o[2] = r[2];
+        }
+    return LB_OK;
+}
+
+int lb_eos_pressure(const lb_eos* eos, int64_t n, const float* rho, const float* T, double* p) {
+    if (!eos || n < 0 || (n > 0 && (!rho || !T || !p))) return fail(LB_E_INVAL, "null argument");
+    if (!(eos->a > 0 && eos->b > 0 && eos->R > 0)) return fail(LB_E_INVAL, "EOS needs a, b, R > 0");
+    const Pr e(*eos);
+    for (int64_t i = 0; i < n; ++i) p[i] = e.p((double)rho[i], (double)T[i]);
     return LB_OK;
 }
 

@@ -69,4 +69,18 @@ void set_last_error(const char* msg);
 // acc->mass = sum over cells and directions of f (FP64).
 cudaError_t launch_mass(const StepParams& P, const float* f, cudaStream_t st);
 
+// Pressure probes (Fig. 3): after a step, record (rho^t, T^t, p_EOS) at up to
+// kProbeMax cells into a device ring (256-byte header whose first 8 bytes
+// count the probed steps, then float4 records [probe][cap]).
+constexpr int kProbeMax = 8;
+struct ProbeArgs {
+    const float* f;   // post-collision populations written by the step (level t)
+    const float* th;  // theta^t, the step's input temperature
+    float* ring;
+    int plane, pitch, n, cap;
+    int x[kProbeMax], y[kProbeMax];
+    double a, b, R, Ts, k0, k1;  // Eq. 21: phi(T) = (k0 - k1 sqrt(T))^2
+};
+cudaError_t launch_probe(const ProbeArgs& A, cudaStream_t st);
+
 }  // namespace lbgpu

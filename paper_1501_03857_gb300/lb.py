@@ -91,6 +91,10 @@ def _load():
         "lb_adjoint": [P, I, I, P, SZ, DP, P, DP],
         "lb_fields_noalloc": [C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), D, D, P, P, P, P, P,
                               P, P],
+        "lb_probe_ring_bytes": [I, I, C.POINTER(C.c_size_t)],
+        "lb_set_probes": [P, I, P, P, P, SZ, I],
+        "lb_probe_read": [P, I, FP, I64P, C.POINTER(I)],
+        "lb_eos_pressure": [C.POINTER(lb_eos), C.c_int64, FP, FP, FP],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -177,6 +181,18 @@ def workspace_bytes(cfg: Config) -> int:
 
 
 NOALLOC_MAX_CELLS = 262144
+PROBE_MAX = 8
+
+
+def eos_pressure(cfg: Config, rho, T) -> np.ndarray:
+    """p_EOS(rho, T) of Eq. 21 (FP64, host; lb_eos_pressure) for arrays of
+    equal shape."""
+    _, e, _ = cfg.structs()
+    r = np.ascontiguousarray(rho, dtype=np.float32)
+    t = np.ascontiguousarray(np.broadcast_to(T, r.shape), dtype=np.float32)
+    out = np.empty(r.shape, dtype=np.float64)
+    check(lib.lb_eos_pressure(C.byref(e), int(r.size), r.ctypes.data, t.ctypes.data, out.ctypes.data))
+    return out
 
 
 def fields_noalloc(cfg: Config, Gw: float, rho_ave: float, fpost, theta, rho=None, ux=None, uy=None, T=None,
@@ -243,13 +259,45 @@ class Simulation:
         check(lib.lb_set_launch(self.h, int(block_x), int(seg_rows)))
 
     def set_kernel(self, kernel: int):
-        """1: two rows per iteration with paired FP32 math (default); 0: row-wise."""
+        """2: dual-strip paired FP32 kernel (default); 3: the same with scalar
+        FP32; 1: two rows per iteration, paired FP32; 0: row-wise scalar."""
         check(lib.lb_set_kernel(self.h, int(kernel)))
 
     def info(self):
         st, bx, sr, nb = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
         check(lib.lb_info(self.h, C.byref(st), C.byref(bx), C.byref(sr), C.byref(nb)))
         return {"steps": st.value, "block_x": bx.value, "seg_rows": sr.value, "blocks": nb.value}
+
+    # -- pressure probes (Fig. 3) --------------------------------------------
+    def set_probes(self, points, capacity: int = 65536):
+        """Record (rho^t, T^t, p_EOS) after every step at the cells
+        points = [(x, y), ...] (at most PROBE_MAX) in a device ring keeping the
+        last `capacity` steps (lb_set_probes); [] removes the probes."""
+        torch = self.torch
+        n = len(points)
+        if n == 0:
+            check(lib.lb_set_probes(self.h, 0, None, None, None, 0, 0))
+            self._ring = None
+            return
+        nb = C.c_size_t()
+        check(lib.lb_probe_ring_bytes(n, int(capacity), C.byref(nb)))
+        ring = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+        base = ring.data_ptr()
+        xs = np.array([int(p[0]) for p in points], dtype=np.int32)
+        ys = np.array([int(p[1]) for p in points], dtype=np.int32)
+        check(lib.lb_set_probes(self.h, n, xs.ctypes.data, ys.ctypes.data, base + ((-base) % 256), nb.value,
+                                int(capacity)))
+        self._ring, self._probe_n, self._probe_cap = ring, n, int(capacity)
+
+    def probe_read(self, max_records: Optional[int] = None):
+        """The newest records of every probe, oldest first: {"count": steps
+        probed since set_probes, "rho", "T", "p": arrays [n_probes, m]}."""
+        mmax = self._probe_cap if max_records is None else int(max_records)
+        out = np.empty(self._probe_n * max(mmax, 1) * 3, dtype=np.float32)
+        cnt, m = C.c_int64(), C.c_int()
+        check(lib.lb_probe_read(self.h, mmax, out.ctypes.data, C.byref(cnt), C.byref(m)))
+        rec = out[: self._probe_n * m.value * 3].reshape(self._probe_n, m.value, 3)
+        return {"count": cnt.value, "rho": rec[..., 0].copy(), "T": rec[..., 1].copy(), "p": rec[..., 2].copy()}
 
     # -- read-back ----------------------------------------------------------
     def heat_flux(self, reset: bool = False):
