@@ -270,6 +270,32 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
             "fd": "central differences of the FP32 GPU forward, h = 1e-4"}
 
 
+CURVE_SUPERHEATS = (0.008, 0.01, 0.0137, 0.0165, 0.019, 0.021, 0.023, 0.025, 0.027, 0.029, 0.032, 0.035)
+
+
+def paper_experiments(torch):
+    """The boiling curves of Sec. 3.2-3.3 on the paper's 600 x 150 pool (12
+    superheats x G_w 0, 0.065, 0.105 in one batch; 20000 steps at the base
+    superheat, switch, 5000 settling, 15000 averaged) and Fig. 3's top-wall
+    pressure; compact summary and wall time."""
+    from paper_1501_03857_gb300 import experiments as E
+    t0 = time.perf_counter()
+    r = E.boiling_curve(CURVE_SUPERHEATS, Gw_values=(0.0, 0.065, 0.105))
+    t_curve = time.perf_counter() - t0
+    curves = {}
+    for gw, c in r["curves"].items():
+        grp = [x for x in r["cases"] if x["Gw"] == gw]
+        curves[str(gw)] = dict(c, superheats=[x["superheat"] for x in grp], q_mean=[x["q_mean"] for x in grp],
+                               regimes=[x["regime"] for x in grp])
+    t0 = time.perf_counter()
+    tp = E.top_wall_pressure((0.0137, 0.0165))
+    t_top = time.perf_counter() - t0
+    steps = r["t_switch"] + r["t_settle"] + r["t_avg"]
+    return {"grid": "600x150", "cases": len(r["cases"]), "steps_per_case": steps, "s_curves": t_curve,
+            "sims_per_hour": len(r["cases"]) * 3600.0 / t_curve, "curves": curves,
+            "top_wall_pressure": {str(k): v["p_top"] for k, v in tp["cases"].items()}, "s_top_wall_pressure": t_top}
+
+
 # Algorithmic bytes per lattice update of one reverse step: the stored state
 # (9 populations + theta) read once and the adjoint state read and written
 # once, plus the forward recomputation of the step from its checkpoint.
@@ -460,6 +486,8 @@ def run_ours(args):
         if not args.no_adjoint:
             line["adjoint"] = adjoint_window(torch, lb)
             line["adjoint"]["large"] = adjoint_roofline(torch, lb)
+        if not args.no_experiments:
+            line["experiments"] = paper_experiments(torch)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
@@ -477,6 +505,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched boiling-curve measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-experiments", action="store_true", help="skip the boiling-curve experiments")
     ap.add_argument("--size", type=int, default=4096, help="domain edge (profiling of smaller cases)")
     ap.add_argument("--adjoint-only", type=str, default=None, metavar="L,STEPS,CKPT",
                     help="only the large-domain adjoint measurement, e.g. 2048,8,4 (profiling)")

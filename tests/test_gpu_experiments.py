@@ -1,0 +1,85 @@
+"""The paper's boiling experiments on the GPU (Sec. 3.2-3.3): the regimes,
+critical heat flux and wettability effects its text states
+(tests/golden/paper_regimes.txt), and Fig. 3's rising top-wall pressure.
+Long boiling runs are chaotic, so these are the paper's qualitative
+statements, not values."""
+
+import os
+
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden():
+    regimes, out = {}, {}
+    for line in open(os.path.join(GOLDEN, "paper_regimes.txt")):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        if line[0] == "regime":
+            regimes[float(line[1])] = line[2]
+        else:
+            out[line[0]] = [float(v) for v in line[1:]]
+    return regimes, out
+
+
+@pytest.fixture(scope="module")
+def E():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1501_03857_gb300 import experiments
+    return experiments
+
+
+@pytest.fixture(scope="module")
+def curve(E):
+    dts0 = (0.008, 0.01, 0.0137, 0.0165, 0.019, 0.021, 0.023, 0.025, 0.027, 0.029, 0.032, 0.035)
+    r0 = E.boiling_curve(dts0, Gw_values=(0.0,))
+    r1 = E.boiling_curve((0.01, 0.0137, 0.019, 0.021, 0.023, 0.025), Gw_values=(0.105,))
+    return r0, r1
+
+
+def test_regimes_match_paper(curve):
+    regimes, _ = golden()
+    got = {c["superheat"]: c["regime"] for c in curve[0]["cases"]}
+    for dT, lab in regimes.items():
+        assert got[dT] == lab, (dT, got[dT], lab)
+
+
+def test_critical_heat_flux_and_hc(curve):
+    """CHF inside the superheat range Sec. 3.2 gives; the largest h_c at a
+    lower superheat than the CHF (Sec. 3.2, Fig. 8)."""
+    _, g = golden()
+    c0 = curve[0]["curves"][0.0]
+    lo, hi = g["chf_range"]
+    assert lo <= c0["chf_superheat"] <= hi
+    assert c0["hc_max_superheat"] < c0["chf_superheat"]
+
+
+def test_wettability_effects(curve):
+    """Sec. 3.3, Fig. 13: a larger contact angle lowers the critical heat
+    flux, and boiling starts at a lower superheat (G_w = 0.105 boils at
+    0.01, G_w = 0 does not); below the crossing of the curves the less
+    wettable surface transfers more heat."""
+    _, g = golden()
+    gw, dT = g["onset_gw"]
+    c1 = {c["superheat"]: c for c in curve[1]["cases"]}
+    c0 = {c["superheat"]: c for c in curve[0]["cases"]}
+    assert curve[1]["curves"][gw]["chf"] < curve[0]["curves"][0.0]["chf"]
+    assert c1[dT]["regime"] != "none" and c0[dT]["regime"] == "none"
+    assert c1[0.0137]["q_mean"] > c0[0.0137]["q_mean"]
+    assert c1[0.025]["q_mean"] < c0[0.025]["q_mean"]
+
+
+def test_top_wall_pressure_rises(E):
+    """Fig. 3: after the switch the pressure at the centre of the top wall
+    rises as bubbles reach the vapour above the pool, faster at the higher
+    superheat."""
+    r = E.top_wall_pressure((0.0137, 0.0165), t_after=10000)["cases"]
+    for dT in (0.0137, 0.0165):
+        p = r[dT]["p_top"]
+        assert p[-1] > p[0]
+    assert r[0.0165]["p_top"][-1] > r[0.0137]["p_top"][-1]
