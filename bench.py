@@ -380,9 +380,8 @@ def run_reference(args):
 
 def run_ours(args):
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1501_03857_gb300 import replicas
+    rank, world, local = replicas.rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -423,12 +422,9 @@ def run_ours(args):
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in ev]
     sim.sync()
-    ms_all = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = world * cells * args.steps / (ms_all * 1e-3) / 1e6
+    # replicas: every rank ran its own domain; the job took the slowest rank's time
+    ms_all = replicas.max_over_ranks(total_ms, dist, device="cuda")
+    value = replicas.job_throughput(world, cells * args.steps, ms_all) / 1e6
 
     # ---- end-to-end through the public API with host buffers
     prof = np.zeros(cfg.Lx, dtype=np.float64)
@@ -445,12 +441,8 @@ def run_ours(args):
         sim.step(1)
         sim.heat_flux()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * cells * e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
+    e2e = {"value": replicas.job_throughput(world, cells * e2e_steps, e2e_s * 1e3) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": cfg.Lx * 4, "d2h_bytes_per_step": 76, "steps": e2e_steps,
            "api": "lb_set_wall_temperature + lb_step(1) + lb_heat_flux per step"}
 
