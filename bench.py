@@ -19,12 +19,21 @@ roofline   the fused kernel's algorithmic 80 B per cell update (9 populations
 cpu_baseline / --impl reference
            the FP64 oracle on the host cores, on a bounded band of rows of the
            same workload.
+batched    48 boiling-curve instances (contact angles 40-150 deg through the
+           sessile-droplet G_w calibration) in one launch per step against
+           the same instances stepped one after another.
+adjoint    gradient of the window-mean wall heat flux: cost against the
+           forward steps and agreement with finite differences (256 x 256),
+           and the reverse sweep's roofline on a 2048 x 2048 domain.
+experiments the boiling curves and regimes of Sec. 3.2-3.3 and Fig. 3's
+           top-wall pressure on the paper's 600 x 150 pool.
 Multi-GPU (torchrun): independent replicas, one domain per rank (weak scaling).
 """
 
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -63,9 +72,10 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples (every 50 ms) kept only while the
+    timed region runs (host wall-clock window given to stop())."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -74,32 +84,37 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-i", str(index),
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0: float, t1: float):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.1)
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
-        sm, mx, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        rows = []
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[4:8]):
+        inside = [r for r in rows if t0 - 0.025 <= r[0] <= t1 + 0.025]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for r in inside:
+            for n, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+                "reasons": sorted(reasons), "samples": len(sm), "window_s": t1 - t0}
 
 
 def cpu_baseline(seconds: float = 12.0, rows: int = 48):
@@ -133,9 +148,8 @@ def cpu_baseline(seconds: float = 12.0, rows: int = 48):
                       f"{el:.1f} s"}
 
 
-# Wettability ladder standing in for the contact-angle axis of the batched
-# curve (Sec. 3.3 gives G_w = 0, 0.065, 0.105 for ~44.5, 50, 55.5 degrees; the
-# last two rungs extend the ladder, uncalibrated).
+# The batched curve's surfaces, by static contact angle; their G_w come from
+# the sessile-droplet calibration run by wettability_calibration.
 CURVE_ANGLES = (40.0, 60.0, 90.0, 120.0, 150.0)  # static contact angles of the curve's surfaces, deg
 CURVE_STEPS = 50000  # steps of one boiling-curve simulation
 CAL_LADDER = tuple(round(-0.125 + 0.025 * k, 3) for k in range(22))  # G_w -0.125 .. 0.4
@@ -411,6 +425,7 @@ def run_ours(args):
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    h0 = time.time()
     t_start.record(stream)
     for k in range(args.steps):
         ev[k][0].record(stream)
@@ -418,7 +433,8 @@ def run_ours(args):
         ev[k][1].record(stream)
     t_end.record(stream)
     barrier()
-    clocks = clk.stop() if clk else None
+    h1 = time.time()
+    clocks = clk.stop(h0, h1) if clk else None
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in ev]
     sim.sync()
@@ -491,7 +507,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
