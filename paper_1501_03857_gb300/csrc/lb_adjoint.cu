@@ -79,15 +79,16 @@ struct AdjFields {
     float* lf;           // lambda of the pulled populations, 9 planes
     float *lrho, *lpsi, *lFmx, *lFmy, *lvx, *lvy, *lth;
     float *lax, *lay, *lcA, *lcB, *mu, *mu_next, *ldrx, *ldry, *ldivv;
-    double* dTb;  // [Lx] dJ/d theta_b accumulators
-    double* dGw;  // dJ/dG_w accumulator
+    double* dTb;   // [Lx] dJ/d theta_b accumulators
+    double* dGwx;  // [Lx] dJ/dG_w contributions of each column's first fluid row
+    double* dGw;   // dJ/dG_w (sum of dGwx, formed at the end)
 };
 
 __device__ __forceinline__ bool cell(const StepParams& P, int& x, int& y, int& i) {
     x = blockIdx.x * blockDim.x + threadIdx.x;
-    y = blockIdx.y;
+    y = blockIdx.y * blockDim.y + threadIdx.y;
     i = y * P.pitch + x;
-    return x < P.Lx;
+    return x < P.Lx && y < P.Ly;
 }
 
 __device__ __forceinline__ Grid grid_of(const StepParams& P) { return Grid{P.Lx, P.Ly, P.pitch, P.bc}; }
@@ -435,7 +436,7 @@ __global__ void rev_collide(const StepParams P, AdjFields A) {
         lrho += -P.g * lFy;  // F_b (Eq. 9)
         if (P.bc != BC_PERIODIC && y == 1) {  // F_ads (Eq. 22) on the first fluid row
             lpsi += 2.f * P.gw6 * psi * lFy;
-            atomicAdd(A.dGw, (double)(psi2 * (1.f / 6.f) * lFy));
+            A.dGwx[x] += (double)(psi2 * (1.f / 6.f) * lFy);  // one cell per x on this row
         }
     } else {
         lFmx = lFmy = 0.f;  // no force is applied on wall rows
@@ -533,8 +534,8 @@ __global__ void rev_pull(const StepParams P, AdjFields A) {
     }
 }
 
-// Work-buffer layout: 54 field planes, then dJ/d theta_b [pitch doubles] and
-// dJ/dG_w.
+// Work-buffer layout: 54 field planes, then dJ/d theta_b [pitch doubles], the
+// per-column dJ/dG_w parts [pitch doubles] and dJ/dG_w.
 constexpr int kPlanes = 54;
 
 AdjFields fields_at(const StepParams& P, void* work) {
@@ -590,8 +591,23 @@ AdjFields fields_at(const StepParams& P, void* work) {
     A.ldry = next(1);
     A.ldivv = next(1);
     A.dTb = (double*)(w + kPlanes * pl);
-    A.dGw = A.dTb + P.pitch;
+    A.dGwx = A.dTb + P.pitch;
+    A.dGw = A.dGwx + P.pitch;
     return A;
+}
+
+// dGw = sum over x of dGwx (one block, fixed order: reproducible)
+__global__ void sum_columns(const double* __restrict__ v, int n, double* out) {
+    __shared__ double part[256];
+    double s = 0.0;
+    for (int x = threadIdx.x; x < n; x += 256) s += v[x];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0];
 }
 
 __global__ void add_wall_row(const StepParams P, const float* lt, double* dTb) {
@@ -602,18 +618,19 @@ __global__ void add_wall_row(const StepParams P, const float* lt, double* dTb) {
 }  // namespace
 
 size_t adjoint_work_bytes(const StepParams& P) {
-    return sizeof(float) * (size_t)kPlanes * (size_t)P.plane + sizeof(double) * ((size_t)P.pitch + 2);
+    return sizeof(float) * (size_t)kPlanes * (size_t)P.plane + sizeof(double) * (2 * (size_t)P.pitch + 2);
 }
 
 cudaError_t adjoint_grads_reset(const StepParams& P, void* work, cudaStream_t st) {
     AdjFields A = fields_at(P, work);
-    return cudaMemsetAsync(A.dTb, 0, sizeof(double) * ((size_t)P.pitch + 1), st);
+    return cudaMemsetAsync(A.dTb, 0, sizeof(double) * (2 * (size_t)P.pitch + 1), st);
 }
 
 cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* lt0, double* dTb_host,
                                  double* dGw_host, cudaStream_t st) {
     AdjFields A = fields_at(P, work);
     if (P.bc != BC_PERIODIC) add_wall_row<<<(P.Lx + 127) / 128, 128, 0, st>>>(P, lt0, A.dTb);
+    sum_columns<<<1, 256, 0, st>>>(A.dGwx, P.Lx, A.dGw);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && dTb_host)
         e = cudaMemcpyAsync(dTb_host, A.dTb, sizeof(double) * P.Lx, cudaMemcpyDeviceToHost, st);
@@ -633,7 +650,9 @@ cudaError_t adjoint_reverse_step(const StepParams& P, void* work, const float* f
     A.lt_in = lt_in;
     A.lf_out = lf_out;
     A.lt_out = lt_out;
-    const dim3 grid((P.Lx + 127) / 128, P.Ly), blk(128);
+    // 32 x 8 tiles: the vertical neighbours of a warp's cells are read by the
+    // warps above and below it in the same block, so they stay in L1
+    const dim3 blk(32, 8), grid((P.Lx + 31) / 32, (P.Ly + 7) / 8);
     fwd_pull<<<grid, blk, 0, st>>>(P, A);
     fwd_force<<<grid, blk, 0, st>>>(P, A);
     fwd_coef<<<grid, blk, 0, st>>>(P, A);
