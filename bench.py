@@ -517,7 +517,14 @@ def main():
     ap.add_argument("--size", type=int, default=4096, help="domain edge (profiling of smaller cases)")
     ap.add_argument("--adjoint-only", type=str, default=None, metavar="L,STEPS,CKPT",
                     help="only the large-domain adjoint measurement, e.g. 2048,8,4 (profiling)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched 48-instance step with G_w = 0 everywhere (profiling)")
     args = ap.parse_args()
+    if args.batched_only:
+        import torch
+        from paper_1501_03857_gb300 import lb
+        print(json.dumps({"batched": batched_curve(torch, lb, [0.0] * len(CURVE_ANGLES))}), flush=True)
+        return
     if args.adjoint_only:
         import torch
         from paper_1501_03857_gb300 import lb
