@@ -98,7 +98,10 @@ int lb_initial_density(const lb_grid* grid, const lb_eos* eos,
                        const lb_thermal* th, float* rho0);
 
 /* Device workspace bytes lb_init needs for this grid (populations and
- * temperature, double-buffered, plus accumulators). */
+ * temperature, double-buffered, plus accumulators). Population offsets are
+ * 32-bit: grids with 9 * pitch * Ly >= 2^31 (pitch = Lx rounded up to a
+ * multiple of 32; e.g. Ly > 14563 at Lx = 16384) are rejected with
+ * LB_E_INVAL, here and by lb_init. */
 int lb_workspace_bytes(const lb_grid* grid, size_t* bytes);
 
 /* ---- simulation --------------------------------------------------------- */

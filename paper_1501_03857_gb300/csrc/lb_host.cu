@@ -492,6 +492,8 @@ int lb_initial_density(const lb_grid* grid, const lb_eos* eos, const lb_thermal*
 int lb_workspace_bytes(const lb_grid* grid, size_t* bytes) {
     if (!grid || !bytes) return fail(LB_E_INVAL, "null argument");
     if (grid->Lx < 1 || grid->Ly < 3) return fail(LB_E_INVAL, "grid %dx%d: need Lx >= 1, Ly >= 3", grid->Lx, grid->Ly);
+    const long long pitch = (grid->Lx + 31) / 32 * 32;
+    if (9LL * pitch * grid->Ly >= (1LL << 31)) return fail(LB_E_INVAL, "grid too large for 32-bit plane offsets");
     *bytes = layout(grid).total;
     return LB_OK;
 }

@@ -39,24 +39,27 @@ def uniform01(seed: int, counter: np.ndarray) -> np.ndarray:
     return (splitmix64(seed, counter) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
-def cell_noise(Lx: int, Ly: int, seed: int) -> np.ndarray:
-    """Uniform [-1, 1) per cell, counter y * Lx + x."""
-    n = np.arange(Lx * Ly, dtype=np.uint64).reshape(Ly, Lx)
+def cell_noise(Lx: int, Ly: int, seed: int, y0: int = 0) -> np.ndarray:
+    """Uniform [-1, 1) per cell, counter y * Lx + x, for rows y0 .. y0 + Ly - 1."""
+    n = (np.arange(Lx * Ly, dtype=np.uint64) + np.uint64(y0 * Lx)).reshape(Ly, Lx)
     return 2.0 * uniform01(seed, n) - 1.0
 
 
-def _finish(rho: np.ndarray, noise_amp: float, seed: int) -> np.ndarray:
+def _finish(rho: np.ndarray, noise_amp: float, seed: int, y0: int = 0) -> np.ndarray:
     Ly, Lx = rho.shape
     if noise_amp:
-        rho = rho * (1.0 + noise_amp * cell_noise(Lx, Ly, seed))
+        rho = rho * (1.0 + noise_amp * cell_noise(Lx, Ly, seed, y0))
     return rho.astype(np.float32)
 
 
-def pool_density(Lx, Ly, rho_l, rho_v, pool_height, width=5.0, noise_amp=1e-4, seed=1):
-    """Liquid below y = pool_height, vapour above (Sec. 3.1), tanh interface."""
-    y = np.arange(Ly, dtype=np.float64)[:, None]
+def pool_density(Lx, Ly, rho_l, rho_v, pool_height, width=5.0, noise_amp=1e-4, seed=1, rows=None):
+    """Liquid below y = pool_height, vapour above (Sec. 3.1), tanh interface.
+    rows = (y0, y1) returns only rows y0 .. y1 - 1 of the Ly-row field (the
+    same values; for fields too large to build at once)."""
+    y0, y1 = (0, Ly) if rows is None else rows
+    y = np.arange(y0, y1, dtype=np.float64)[:, None]
     prof = 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * np.tanh(2.0 * (y - pool_height) / width)
-    return _finish(np.broadcast_to(prof, (Ly, Lx)).copy(), noise_amp, seed)
+    return _finish(np.broadcast_to(prof, (y1 - y0, Lx)).copy(), noise_amp, seed, y0)
 
 
 def slab_density(Lx, Ly, rho_l, rho_v, y0, y1, width=5.0, noise_amp=0.0, seed=1):

@@ -97,3 +97,13 @@ def test_null_handle_calls_fail_cleanly(lb):
     assert lb.lib.lb_step(None, 1) == -1
     assert lb.lib.lb_sync(None) == -1
     assert lb.lib.lb_destroy(None) == -1
+
+
+def test_largest_grid_accepted_one_row_more_rejected(lb):
+    """Population offsets are 32-bit: 9 * pitch * Ly < 2^31. At Lx = 16384
+    (pitch 16384) the largest Ly is 14563; one row more is rejected with a
+    message, before any device call."""
+    ok = lb.workspace_bytes(lb.Config(Lx=16384, Ly=14563))
+    assert ok >= 2 * 10 * 16384 * 14563 * 4
+    with pytest.raises(lb.LBError, match="too large"):
+        lb.workspace_bytes(lb.Config(Lx=16384, Ly=14564))

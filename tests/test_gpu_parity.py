@@ -262,3 +262,46 @@ def test_full_size_sampled_rows(lb):
         assert norm_err(fg[:, y0 + rows[0]:y0 + rows[-1] + 1], fr.numpy()[:, rows[0]:rows[-1] + 1]) < TOL_ONE_STEP
         assert theta_err(tg[y0 + rows[0]:y0 + rows[-1] + 1], tr.numpy()[rows[0]:rows[-1] + 1],
                          P.theta_b[0].item()) < TOL_ONE_STEP
+
+
+def test_maximum_size_sampled_rows(lb):
+    """The largest grid the 32-bit population offsets allow (16384 x 14563,
+    238.6 M cells, 19 GB of state), a pool initialised on the device from its
+    density, one step in the default launch shape: bands of rows (heated
+    wall, the interface in the middle, top wall) against the oracle run on
+    the band alone from the same densities; rows at least 7 away from a
+    band's artificial edge depend only on data inside the band."""
+    Lx, Ly, band = 16384, 14563, 16
+    y_if = 7000.5
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=0)
+    rv, rl = coex(lb, cfg)
+    sh = 0.1 * lb.critical_temperature(cfg)
+    rho0 = np.empty((Ly, Lx), dtype=np.float32)
+    for y0 in range(0, Ly, 1024):  # row chunks keep the host temporaries small
+        y1 = min(y0 + 1024, Ly)
+        rho0[y0:y1] = inputs.pool_density(Lx, Ly, rl, rv, y_if, noise_amp=1e-3, seed=11, rows=(y0, y1))
+    rho_ave = float(rho0.astype(np.float64).mean())
+    sim = lb.Simulation(cfg, superheat=sh, rho0=rho0)
+    sim.step(1)
+    fg = torch.empty((9, Ly, Lx), dtype=torch.float32, device="cuda")
+    tg = torch.empty((Ly, Lx), dtype=torch.float32, device="cuda")
+    sim.get_state_device(fg, tg)
+    q = sim.heat_flux()["q_inst"]
+    sim.close()
+    for y0, bc in ((0, 0), (int(y_if) - band // 2, 2), (Ly - band, 0)):
+        Pb = oracle_params(lb.Config(Lx=Lx, Ly=band, bc_y=bc), None, superheat=sh, rho_ave=rho_ave)
+        rb = torch.tensor(rho0[y0:y0 + band], dtype=torch.float64)
+        f0, th0 = O.initial_state(rb, Pb)
+        fr, tr, qs = run_oracle(f0.numpy().astype(np.float32), th0.numpy().astype(np.float32), Pb, 1)
+        if y0 == 0:
+            rows = list(range(0, band - 7))
+            assert abs(q - qs[0]) <= 1e-5 * abs(qs[0])
+        elif y0 == Ly - band:
+            rows = list(range(7, band))
+        else:
+            rows = list(range(7, band - 7))
+        r0, r1 = rows[0], rows[-1] + 1
+        got_f = fg[:, y0 + r0:y0 + r1].cpu().numpy()
+        got_t = tg[y0 + r0:y0 + r1].cpu().numpy()
+        assert norm_err(got_f, fr.numpy()[:, r0:r1]) < TOL_ONE_STEP
+        assert theta_err(got_t, tr.numpy()[r0:r1], sh) < TOL_ONE_STEP
