@@ -973,8 +973,8 @@ int batch_layout(lb_batch* b) {
 }
 
 // Parameter tables relative to each instance's current buffer: parity p
-// reads buffer cur ^ p. Uploaded in stream order (the host copy is staged
-// by the driver before the call returns).
+// reads buffer cur ^ p. Uploaded in stream order (cudaMemcpyAsync from
+// pageable host memory stages the source before it returns).
 int batch_upload(lb_batch* b) {
     if (!b->dirty) return LB_OK;
     const int n = (int)b->inst.size();
