@@ -143,9 +143,46 @@ def cpu_baseline(seconds: float = 12.0, rows: int = 48):
         if el > seconds and n >= 2:
             break
     mlups = n * L * rows / el / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": torch.get_num_threads(), "kind": "oracle",
+    threads = torch.get_num_threads()
+
+    def timed(fn, budget):
+        k, t0 = 0, time.perf_counter()
+        while True:
+            fn()
+            k += 1
+            dt = time.perf_counter() - t0
+            if dt > budget and k >= 2:
+                return k, dt
+
+    # the same band on one thread
+    torch.set_num_threads(1)
+    state = [f, th]
+
+    def one():
+        state[0], state[1], _ = O.step(state[0], state[1], P)
+
+    k1, t1 = timed(one, 3.0)
+    # the small 100 x 100 configuration (a = 2/49, pool to y = 40), all cores
+    torch.set_num_threads(threads)
+    a2 = 2 / 49
+    Tc2 = O.critical_temperature(a2, b, R)
+    rv2, rl2 = O.maxwell_coexistence(a2, b, R, om, 0.86 * Tc2)
+    r2 = torch.tensor(inputs.pool_density(100, 100, rl2, rv2, 40.0, seed=1), dtype=torch.float64)
+    P2 = O.Params(Lx=100, Ly=100, a=a2, b=b, R=R, omega=om)
+    P2.finalize(rho0=r2, superheat=0.1 * Tc2, rho_v=rv2, rho_l=rl2)
+    st2 = list(O.initial_state(r2, P2))
+
+    def small():
+        st2[0], st2[1], _ = O.step(st2[0], st2[1], P2)
+
+    k2, t2 = timed(small, 3.0)
+    return {"value": mlups, "unit": "MLUPS", "cores": threads, "kind": "oracle",
             "sample": f"FP64 oracle (PyTorch CPU), {n} steps of a {L}x{rows} bottom band of the workload, "
-                      f"{el:.1f} s"}
+                      f"{el:.1f} s",
+            "single_thread": {"value": k1 * L * rows / t1 / 1e6, "unit": "MLUPS", "cores": 1,
+                              "sample": f"{k1} steps of the same band, {t1:.1f} s"},
+            "config_100x100": {"value": k2 * 100 * 100 / t2 / 1e6, "unit": "MLUPS", "cores": threads,
+                               "sample": f"{k2} steps of the 100 x 100 pool (a = 2/49), {t2:.1f} s"}}
 
 
 # The batched curve's surfaces, by static contact angle; their G_w come from
