@@ -104,6 +104,36 @@ def test_200_steps_config1(lb, outflow):
     assert abs(h["q_mean"] / np.mean(qs) - 1) < 1e-5
 
 
+def test_2000_steps_config1_long_run(lb):
+    """The 100 x 100 configuration (walls, superheat 0.1 T_c) for 2000 steps,
+    ten times the 200-step horizon, GPU against the FP64 oracle: no bubble
+    has nucleated yet, so the run is still deterministic and the fields stay
+    within the same 1e-5 bound (measured f 1e-6, theta 3e-6) and the mean
+    wall heat flux of the second half within 1e-4 (measured 7e-7), far
+    inside the 2 % statistical bound meant for chaotic runs."""
+    import os
+    torch.set_num_threads(min(16, os.cpu_count() or 1))
+    cfg, sh = config1(lb, outflow=False)
+    rv, rl = coex(lb, cfg)
+    rho0 = inputs.pool_density(cfg.Lx, cfg.Ly, rl, rv, cfg.pool_height, noise_amp=cfg.noise_amp, seed=cfg.seed)
+    P = oracle_params(cfg, rho0, superheat=sh)
+    f0, th0 = oracle_initial_fp32(rho0, P)
+    sim = lb.Simulation(cfg, superheat=sh, rho0=rho0)
+    sim.set_state(f0, th0)
+    sim.step(1000)
+    sim.heat_flux(reset=True)
+    sim.step(1000)
+    h = sim.heat_flux()
+    fg, tg = sim.get_state()
+    sim.close()
+    fr, tr, qs = run_oracle(f0, th0, P, 2000)
+    q_ref = float(np.mean(qs[1000:]))
+    ef, et = norm_err(fg, fr.numpy()), theta_err(tg, tr.numpy(), sh)
+    print(f"2000 steps: q rel {abs(h['q_mean'] / q_ref - 1):.2e}, f {ef:.2e}, theta {et:.2e}")
+    assert abs(h["q_mean"] / q_ref - 1) < 1e-4
+    assert ef < TOL_200 and et < TOL_200
+
+
 SHAPES = {0: ((0, 0), (64, 1), (96, 7), (256, 57), (512, 3), (128, 1000)),
           1: ((0, 0), (128, 2), (256, 6), (128, 1000), (256, 58), (128, 14)),
           2: ((0, 0), (64, 1), (128, 5), (256, 57), (64, 1000), (128, 13)),
