@@ -59,6 +59,18 @@ def test_critical_heat_flux_and_hc(curve):
     assert c0["hc_max_superheat"] < c0["chf_superheat"]
 
 
+def test_transition_heat_flux_fluctuates_most(curve):
+    """Sec. 3.2, Fig. 6: the transient heat flux of the transition case
+    (0.032) fluctuates far more than that of the nucleate (0.0165) and film
+    (0.035) cases: its standard deviation over the window is more than
+    1.5x and 5x theirs."""
+    _, g = golden()
+    t, n, f = g["q_fluct"]
+    c0 = {c["superheat"]: c for c in curve[0]["cases"]}
+    assert c0[t]["q_std"] > 1.5 * c0[n]["q_std"]
+    assert c0[t]["q_std"] > 5.0 * c0[f]["q_std"]
+
+
 def test_wettability_effects(curve):
     """Sec. 3.3, Fig. 13: a larger contact angle lowers the critical heat
     flux, and boiling starts at a lower superheat (G_w = 0.105 boils at
