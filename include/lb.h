@@ -42,6 +42,8 @@ extern "C" {
 #define LB_E_EOS_DOMAIN (-3)  /* psi argument 2(p - rho/3)/G < 0 somewhere  */
 #define LB_E_NONFINITE (-4)   /* NaN or Inf in rho or T                     */
 #define LB_E_TIMEOUT (-5)     /* a bounded device wait gave up              */
+#define LB_E_BOUNDS (-6)      /* checked build only: a device index left its
+                                 buffer (the access was skipped)            */
 
 /* Boundary condition in y (Sec. 3.1: periodic in x, solid walls at y = 0
  * and y = Ly). */

@@ -16,7 +16,7 @@ constexpr int TRING = 8;   // rows kept of theta^t
 constexpr int SM_ROWS = 7 * RING + TRING;  // psi rho vx vy u2 u3 u4 + theta
 
 enum { BC_WALLS = 0, BC_TOP_OUTFLOW = 1, BC_PERIODIC = 2 };
-enum : unsigned { ERR_EOS = 1u, ERR_NONFINITE = 2u };
+enum : unsigned { ERR_EOS = 1u, ERR_NONFINITE = 2u, ERR_BOUNDS = 4u };
 
 // FP64 device accumulators (wall heat flux of Sec. 3.2, mass, fault flags).
 struct Acc {
@@ -59,6 +59,29 @@ __device__ __forceinline__ int wrap(int v, int n) {
 }
 
 __device__ __forceinline__ bool finite_f(float v) { return fabsf(v) <= 3.402823466e38f; }
+
+// Checked build (-DLB_CHECKED, liblbboil_checked.so): every global and
+// shared-memory access of the fused step goes through these; an address
+// outside its buffer sets ERR_BOUNDS and the access is skipped (a load reads
+// 0) instead of faulting. In the normal build they are the plain accesses.
+#ifdef LB_CHECKED
+__device__ __forceinline__ bool lb_inside(const void* p, const void* base, size_t bytes, size_t width, Acc* acc) {
+    const char* c = static_cast<const char*>(p);
+    const char* b = static_cast<const char*>(base);
+    if (base != nullptr && c >= b && c + width <= b + bytes) return true;
+    atomicOr(&acc->err, ERR_BOUNDS);
+    return false;
+}
+__device__ __forceinline__ float lb_ldg(const float* p, const float* base, size_t n, Acc* acc) {
+    return lb_inside(p, base, n * sizeof(float), sizeof(float), acc) ? __ldg(p) : 0.f;
+}
+__device__ __forceinline__ void lb_st(float* p, float v, const float* base, size_t n, Acc* acc) {
+    if (lb_inside(p, base, n * sizeof(float), sizeof(float), acc)) *p = v;
+}
+#else
+__device__ __forceinline__ float lb_ldg(const float* p, const float*, size_t, Acc*) { return __ldg(p); }
+__device__ __forceinline__ void lb_st(float* p, float v, const float*, size_t, Acc*) { *p = v; }
+#endif
 
 // psi(rho, T) = sqrt(2 (p_EOS - rho c_s^2) / G), c = 1 (Sec. 2 and Eq. 21).
 __device__ __forceinline__ float eos_psi(float rho, float T, const StepParams& P, bool& bad) {

@@ -332,6 +332,7 @@ int check_device_errors(lb_handle* h) {
     if (err) {
         const unsigned z = 0;
         LB_CUDA(cudaMemcpy(&h->acc->err, &z, sizeof(unsigned), cudaMemcpyHostToDevice), "clear error flags");
+        if (err & ERR_BOUNDS) return fail(LB_E_BOUNDS, "a device index left its buffer (checked build)");
         if (err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature on the device");
         if (err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument 2(p - rho/3)/G < 0 (EOS domain)");
     }
@@ -1286,6 +1287,7 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
     Acc a;
     LB_CUDA(cudaMemcpyAsync(&a, acc, sizeof(Acc), cudaMemcpyDeviceToHost, st), "read J");
     LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (a.err & ERR_BOUNDS) return fail(LB_E_BOUNDS, "a device index left its buffer in the window (checked build)");
     if (a.err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature in the window");
     if (a.err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument < 0 in the window (EOS domain)");
     const double Jv = a.q_n > 0 ? a.q_sum / a.q_n : 0.0;

@@ -88,6 +88,7 @@ __device__ __forceinline__ void load_row2(const StepParams& P, int y, int xa, in
                                           int xbp, T (&f)[9], T& th) {
     const float* __restrict__ F = P.f_in;
     const int pl = P.plane, pitch = P.pitch;
+    const size_t nF = 9 * (size_t)pl;
     int ym = y - 1, yp = y + 1;
     bool okm = true, okp = true;
     if (P.bc == BC_PERIODIC) {
@@ -103,25 +104,25 @@ __device__ __forceinline__ void load_row2(const StepParams& P, int y, int xa, in
     const float* Rc = F + y * pitch;
     const float* Rm = F + ym * pitch;
     const float* Rp = F + yp * pitch;
-    f[0] = T(__ldg(Rc + xa), __ldg(Rc + xb));
-    f[1] = T(__ldg(Rc + pl + xam), __ldg(Rc + pl + xbm));
-    f[3] = T(__ldg(Rc + 3 * pl + xap), __ldg(Rc + 3 * pl + xbp));
+    f[0] = T(lb_ldg(Rc + xa, F, nF, P.acc), lb_ldg(Rc + xb, F, nF, P.acc));
+    f[1] = T(lb_ldg(Rc + pl + xam, F, nF, P.acc), lb_ldg(Rc + pl + xbm, F, nF, P.acc));
+    f[3] = T(lb_ldg(Rc + 3 * pl + xap, F, nF, P.acc), lb_ldg(Rc + 3 * pl + xbp, F, nF, P.acc));
     if (okm) {
-        f[2] = T(__ldg(Rm + 2 * pl + xa), __ldg(Rm + 2 * pl + xb));
-        f[5] = T(__ldg(Rm + 5 * pl + xam), __ldg(Rm + 5 * pl + xbm));
-        f[6] = T(__ldg(Rm + 6 * pl + xap), __ldg(Rm + 6 * pl + xbp));
+        f[2] = T(lb_ldg(Rm + 2 * pl + xa, F, nF, P.acc), lb_ldg(Rm + 2 * pl + xb, F, nF, P.acc));
+        f[5] = T(lb_ldg(Rm + 5 * pl + xam, F, nF, P.acc), lb_ldg(Rm + 5 * pl + xbm, F, nF, P.acc));
+        f[6] = T(lb_ldg(Rm + 6 * pl + xap, F, nF, P.acc), lb_ldg(Rm + 6 * pl + xbp, F, nF, P.acc));
     } else {
         f[2] = f[5] = f[6] = T::bc(0.f);
     }
     if (okp) {
-        f[4] = T(__ldg(Rp + 4 * pl + xa), __ldg(Rp + 4 * pl + xb));
-        f[7] = T(__ldg(Rp + 7 * pl + xap), __ldg(Rp + 7 * pl + xbp));
-        f[8] = T(__ldg(Rp + 8 * pl + xam), __ldg(Rp + 8 * pl + xbm));
+        f[4] = T(lb_ldg(Rp + 4 * pl + xa, F, nF, P.acc), lb_ldg(Rp + 4 * pl + xb, F, nF, P.acc));
+        f[7] = T(lb_ldg(Rp + 7 * pl + xap, F, nF, P.acc), lb_ldg(Rp + 7 * pl + xbp, F, nF, P.acc));
+        f[8] = T(lb_ldg(Rp + 8 * pl + xam, F, nF, P.acc), lb_ldg(Rp + 8 * pl + xbm, F, nF, P.acc));
     } else {
         f[4] = f[7] = f[8] = T::bc(0.f);
     }
     const float* Tc = P.th_in + y * pitch;
-    th = T(__ldg(Tc + xa), __ldg(Tc + xb));
+    th = T(lb_ldg(Tc + xa, P.th_in, (size_t)pl, P.acc), lb_ldg(Tc + xb, P.th_in, (size_t)pl, P.acc));
 }
 
 // Isotropic central differences (Lee and Lin; Sec. 2 after Eq. 20) at
@@ -266,7 +267,27 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
     float2* const sU4 = sU3 + RING * W;
     float2* const sTH = sU4 + RING * W;   // TRING slots
     float2* const sCO = sTH + TRING * W;  // [4 coefficients][RING slots][BD], own column
-    for (int i = threadIdx.x; i < SM_ROWS * W + 4 * RING * BD; i += BD) sm2[i] = make_float2(0.f, 0.f);
+    constexpr size_t SMN = (size_t)SM_ROWS * W + 4 * RING * BD;  // float2 in the dynamic shared memory
+    for (int i = threadIdx.x; i < (int)SMN; i += BD) sm2[i] = make_float2(0.f, 0.f);
+    // checked build: a ring cell with its two x neighbours (smp), or a
+    // coefficient slot with its three siblings (smc), inside the shared array
+#ifdef LB_CHECKED
+    auto smp = [&](auto* q) {
+        if (q - 1 >= sm2 && q + 1 < sm2 + SMN) return q;
+        atomicOr(&P.acc->err, ERR_BOUNDS);
+        return static_cast<decltype(q)>(sm2 + 1);
+    };
+    auto smc = [&](auto* q) {
+        if (q >= sm2 && q + 3 * RING * BD < sm2 + SMN) return q;
+        atomicOr(&P.acc->err, ERR_BOUNDS);
+        return static_cast<decltype(q)>(sm2);
+    };
+#define LB_SMP(q) smp(q)
+#define LB_SMC(q) smc(q)
+#else
+#define LB_SMP(q) (q)
+#define LB_SMC(q) (q)
+#endif
 
     const int Lx = P.Lx, Ly = P.Ly;
     const int strip = block % P.nstrips;  // a pair of column strips
@@ -302,7 +323,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
     T acc1 = zero, acc2 = zero, acc3 = zero;
     // the RK coefficients of row r live in slot (r & 3) of sCO
     auto coef = [&](int r) {
-        const float2* c = sCO + (r & 3) * BD + lc;
+        const float2* c = LB_SMC(sCO + (r & 3) * BD + lc);
         return Coef2<T>{T(c[0]), T(c[RING * BD]), T(c[2 * RING * BD]), T(c[3 * RING * BD])};
     };
     __syncthreads();
@@ -336,16 +357,16 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             }
             const T rhoN = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
             const T psiN = eos_psi2(rhoN, tc + T::bc(P.Ts), P, eos_bad);
-            sPSI[(L & 3) * W + s] = psiN.f2();
-            sRHO[(L & 3) * W + s] = rhoN.f2();
-            sTH[(L & 7) * W + s] = tc.f2();
+            *LB_SMP(sPSI + (L & 3) * W + s) = psiN.f2();
+            *LB_SMP(sRHO + (L & 3) * W + s) = rhoN.f2();
+            *LB_SMP(sTH + (L & 7) * W + s) = tc.f2();
         }
         __syncthreads();
 
         // ---- bottom-wall heat flux of level t (Sec. 3.2), one sample per step
         if (!periodic && ys == 0 && L == 2) {
             double qv = 0.0;
-            const float2 r0 = sRHO[0 * W + s], t0 = sTH[0 * W + s], t1 = sTH[1 * W + s], t2 = sTH[2 * W + s];
+            const float2 r0 = *LB_SMP(sRHO + 0 * W + s), t0 = *LB_SMP(sTH + 0 * W + s), t1 = *LB_SMP(sTH + 1 * W + s), t2 = *LB_SMP(sTH + 2 * W + s);
             if (outa) qv += -(double)P.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
             if (outb) qv += -(double)P.cvchi * r0.y * (-3.0 * t0.y + 4.0 * t1.y - t2.y) * 0.5;
 #pragma unroll
@@ -380,8 +401,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             if (r >= loB && r < hiB) {
                 const int y = yL == 0 ? Ly - 1 : yL - 1;
                 const bool wall = !periodic && (y == 0 || y == Ly - 1);
-                const T rhoP(sRHO[(r & 3) * W + s]);
-                const T psiP(sPSI[(r & 3) * W + s]);
+                const T rhoP(*LB_SMP(sRHO + (r & 3) * W + s));
+                const T psiP(*LB_SMP(sPSI + (r & 3) * W + s));
                 const T jxP = (fP[1] - fP[3]) + (fP[5] - fP[6]) + (fP[8] - fP[7]);
                 const T jyP = (fP[2] - fP[4]) + (fP[5] + fP[6]) - (fP[7] + fP[8]);
                 T Fmx = zero, Fmy = zero;
@@ -389,7 +410,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                     const float2* pc = sPSI + (r & 3) * W + s;
                     const float2* pn = (wall && y == Ly - 1) ? pc : sPSI + ((r + 1) & 3) * W + s;
                     const float2* ps = (wall && y == 0) ? pc : sPSI + ((r - 1) & 3) * W + s;
-                    const St2<T> g = stencil2<T>(ps, pc, pn, false);  // sum_a w_a psi(x + e_a) e_a, Eq. 7
+                    const St2<T> g = stencil2<T>(LB_SMP(ps), LB_SMP(pc), LB_SMP(pn), false);  // sum_a w_a psi(x + e_a) e_a, Eq. 7
                     Fmx = (-P.G) * (psiP * g.dx);
                     Fmy = (-P.G) * (psiP * g.dy);
                 }
@@ -402,8 +423,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 const T irho = rcp2(rhoP);
                 const T vx = fma2(T::bc(0.5f), Fx, jxP) * irho;  // Eq. 6
                 const T vy = fma2(T::bc(0.5f), Fy, jyP) * irho;
-                sVX[(r & 3) * W + s] = vx.f2();
-                sVY[(r & 3) * W + s] = vy.f2();
+                *LB_SMP(sVX + (r & 3) * W + s) = vx.f2();
+                *LB_SMP(sVY + (r & 3) * W + s) = vy.f2();
                 const bool st = r >= ys && r < ye;
                 if (st && (outa || outb)) {
                     T o[9];
@@ -413,12 +434,12 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                     if (outa) {
                         if (!finite_f(rhoP.x())) nonfinite = true;
 #pragma unroll
-                        for (int a = 0; a < 9; ++a) out[a * pl + xa] = o[a].x();
+                        for (int a = 0; a < 9; ++a) lb_st(out + (a * pl + xa), o[a].x(), P.f_out, 9 * (size_t)pl, P.acc);
                     }
                     if (outb) {
                         if (!finite_f(rhoP.y())) nonfinite = true;
 #pragma unroll
-                        for (int a = 0; a < 9; ++a) out[a * pl + xb] = o[a].y();
+                        for (int a = 0; a < 9; ++a) lb_st(out + (a * pl + xb), o[a].y(), P.f_out, 9 * (size_t)pl, P.acc);
                     }
                 }
             }
@@ -434,13 +455,13 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 const int r = L - 2;
                 if (r >= loC && r < hiC) {
                     const int y = wrap_row(yL - 2, Ly);
-                    const T thr(sTH[(r & 7) * W + s]);
+                    const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                     T u2 = thr;
                     if (periodic || (y != 0 && y != Ly - 1)) {
                         const int om = ((r - 1) & 3) * W + s, oc = (r & 3) * W + s, op = ((r + 1) & 3) * W + s;
-                        const St2<T> gr = stencil2<T>(sRHO + om, sRHO + oc, sRHO + op, false);
-                        const St2<T> gvx = stencil2<T>(sVX + om, sVX + oc, sVX + op, false);
-                        const St2<T> gvy = stencil2<T>(sVY + om, sVY + oc, sVY + op, false);
+                        const St2<T> gr = stencil2<T>(LB_SMP(sRHO + om), LB_SMP(sRHO + oc), LB_SMP(sRHO + op), false);
+                        const St2<T> gvx = stencil2<T>(LB_SMP(sVX + om), LB_SMP(sVX + oc), LB_SMP(sVX + op), false);
+                        const St2<T> gvy = stencil2<T>(LB_SMP(sVY + om), LB_SMP(sVY + oc), LB_SMP(sVY + op), false);
                         const T rho = gr.c;
                         const T irho = rcp2(rho);
                         const T divv = gvx.dx + gvy.dy;
@@ -450,17 +471,16 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                         kC.ay = fma2(T::bc(P.chi), gr.dy * irho, -gvy.c);
                         kC.cA = (P.R * P.inv_cv) * divv * rcp2(T::bc(1.f) - br);
                         kC.cB = (P.a * P.inv_cv) * (divv * rho) * rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));
-                        float2* c = sCO + (r & 3) * BD + lc;
+                        float2* c = LB_SMC(sCO + (r & 3) * BD + lc);
                         c[0] = kC.ax.f2();
                         c[RING * BD] = kC.ay.f2();
                         c[2 * RING * BD] = kC.cA.f2();
                         c[3 * RING * BD] = kC.cB.f2();
-                        const St2<T> ut = stencil2<T>(sTH + ((r - 1) & 7) * W + s, sTH + (r & 7) * W + s,
-                                                      sTH + ((r + 1) & 7) * W + s, true);
+                        const St2<T> ut = stencil2<T>(LB_SMP(sTH + ((r - 1) & 7) * W + s), LB_SMP(sTH + (r & 7) * W + s), LB_SMP(sTH + ((r + 1) & 7) * W + s), true);
                         accC = rhs_K2(ut, kC, P);
                         u2 = fma2(T::bc(0.5f), accC, thr);
                     }
-                    sU2[(r & 3) * W + s] = u2.f2();
+                    *LB_SMP(sU2 + (r & 3) * W + s) = u2.f2();
                 }
             }
             __syncthreads();
@@ -469,16 +489,15 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 const int r = L - 3;
                 if (r >= loD && r < hiD) {
                     const int y = wrap_row(yL - 3, Ly);
-                    const T thr(sTH[(r & 7) * W + s]);
+                    const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                     T u3 = thr;
                     if (periodic || (y != 0 && y != Ly - 1)) {
-                        const St2<T> u = stencil2<T>(sU2 + ((r - 1) & 3) * W + s, sU2 + (r & 3) * W + s,
-                                                     sU2 + ((r + 1) & 3) * W + s, true);
+                        const St2<T> u = stencil2<T>(LB_SMP(sU2 + ((r - 1) & 3) * W + s), LB_SMP(sU2 + (r & 3) * W + s), LB_SMP(sU2 + ((r + 1) & 3) * W + s), true);
                         const T h2 = rhs_K2(u, coef(r), P);
                         u3 = fma2(T::bc(0.5f), h2, thr);
                         acc1 = fma2(T::bc(2.f), h2, acc1);
                     }
-                    sU3[(r & 3) * W + s] = u3.f2();
+                    *LB_SMP(sU3 + (r & 3) * W + s) = u3.f2();
                 }
             }
             __syncthreads();
@@ -487,16 +506,15 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 const int r = L - 4;
                 if (r >= loE && r < hiE) {
                     const int y = wrap_row(yL - 4, Ly);
-                    const T thr(sTH[(r & 7) * W + s]);
+                    const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                     T u4 = thr;
                     if (periodic || (y != 0 && y != Ly - 1)) {
-                        const St2<T> u = stencil2<T>(sU3 + ((r - 1) & 3) * W + s, sU3 + (r & 3) * W + s,
-                                                     sU3 + ((r + 1) & 3) * W + s, true);
+                        const St2<T> u = stencil2<T>(LB_SMP(sU3 + ((r - 1) & 3) * W + s), LB_SMP(sU3 + (r & 3) * W + s), LB_SMP(sU3 + ((r + 1) & 3) * W + s), true);
                         const T h3 = rhs_K2(u, coef(r), P);
                         u4 = thr + h3;
                         acc2 = fma2(T::bc(2.f), h3, acc2);
                     }
-                    sU4[(r & 3) * W + s] = u4.f2();
+                    *LB_SMP(sU4 + (r & 3) * W + s) = u4.f2();
                 }
             }
             __syncthreads();
@@ -506,16 +524,15 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             const int r = L - 5;
             if (r >= ys && r < ye && (outa || outb)) {
                 const int y = wrap_row(yL - 5, Ly);
-                const T thr(sTH[(r & 7) * W + s]);
+                const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                 T tnew = thr;
                 if (thermal) {
                     if (!periodic && y == 0) {
-                        tnew = T(__ldg(P.thb + xa), __ldg(P.thb + xb));
+                        tnew = T(lb_ldg(P.thb + xa, P.thb, P.pitch, P.acc), lb_ldg(P.thb + xb, P.thb, P.pitch, P.acc));
                     } else if (!periodic && y == Ly - 1) {
                         tnew = zero;
                     } else {
-                        const St2<T> u = stencil2<T>(sU4 + ((r - 1) & 3) * W + s, sU4 + (r & 3) * W + s,
-                                                     sU4 + ((r + 1) & 3) * W + s, true);
+                        const St2<T> u = stencil2<T>(LB_SMP(sU4 + ((r - 1) & 3) * W + s), LB_SMP(sU4 + (r & 3) * W + s), LB_SMP(sU4 + ((r + 1) & 3) * W + s), true);
                         const T h4 = rhs_K2(u, coef(r), P);
                         tnew = fma2(acc3 + h4, T::bc(1.f / 6.f), thr);
                     }
@@ -523,11 +540,11 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 float* out = P.th_out + y * P.pitch;
                 if (outa) {
                     if (!finite_f(tnew.x())) nonfinite = true;
-                    out[xa] = tnew.x();
+                    lb_st(out + xa, tnew.x(), P.th_out, (size_t)P.plane, P.acc);
                 }
                 if (outb) {
                     if (!finite_f(tnew.y())) nonfinite = true;
-                    out[xb] = tnew.y();
+                    lb_st(out + xb, tnew.y(), P.th_out, (size_t)P.plane, P.acc);
                 }
             }
         }
@@ -546,6 +563,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
     if (eos_bad) atomicOr(&P.acc->err, ERR_EOS);
     if (nonfinite) atomicOr(&P.acc->err, ERR_NONFINITE);
 }
+#undef LB_SMP
+#undef LB_SMC
 
 template <int BD, int MINB, class T>
 __global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {

@@ -15,10 +15,12 @@ from typing import Optional
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblbboil.so")
+# LBBOIL_LIB selects another build of the library, e.g. _lib/liblbboil_checked.so
+LIB_PATH = os.environ.get("LBBOIL_LIB") or os.path.join(_PKG, "_lib", "liblbboil.so")
 
 LB_OK = 0
-ERRORS = {-1: "LB_E_INVAL", -2: "LB_E_CUDA", -3: "LB_E_EOS_DOMAIN", -4: "LB_E_NONFINITE", -5: "LB_E_TIMEOUT"}
+ERRORS = {-1: "LB_E_INVAL", -2: "LB_E_CUDA", -3: "LB_E_EOS_DOMAIN", -4: "LB_E_NONFINITE", -5: "LB_E_TIMEOUT",
+          -6: "LB_E_BOUNDS"}
 BC_WALLS, BC_TOP_OUTFLOW, BC_PERIODIC = 0, 1, 2
 
 

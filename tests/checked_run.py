@@ -1,0 +1,49 @@
+"""Helper of test_gpu_checked.py (not a test module): steps the cases given
+on the command line with whichever library LBBOIL_LIB selects and saves the
+resulting states to an .npz file. Every run ends with a synchronising call,
+which raises if the checked build flagged an address outside its buffer."""
+
+import json
+import sys
+
+import numpy as np
+
+from paper_1501_03857_gb300 import inputs, lb
+
+
+def run(case):
+    Lx, Ly, bc, ghost, gw, iso, steps, bx, seg = case
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, ghost_layer=bool(ghost), isothermal=bool(iso))
+    rv, rl = lb.coexistence(cfg)
+    rho0, f0, th0 = inputs.random_state(Lx, Ly, rl, rv, Ly * 0.45, seed=Lx * 1000 + Ly)
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=gw, rho0=rho0)
+    sim.set_launch(bx, seg)
+    sim.set_state(f0, th0)
+    sim.step(steps)
+    sim.sync()
+    f, th = sim.get_state()
+    sim.close()
+    return f, th
+
+
+def run_batch():
+    insts = []
+    for i, (Lx, Ly, bc) in enumerate(((40, 30, 0), (57, 23, 1), (33, 48, 2))):
+        cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.4 * Ly, seed=20 + i)
+        insts.append({"cfg": cfg, "superheat": 0.01, "Gw": 0.05 * i})
+    b = lb.Batch(insts)
+    b.step(37)
+    b.sync()
+    out = [b.get_state(i) for i in range(b.n)]
+    b.close()
+    return out
+
+
+if __name__ == "__main__":
+    cases = json.loads(sys.argv[1])
+    res = {}
+    for k, c in enumerate(cases):
+        res[f"f{k}"], res[f"t{k}"] = run(c)
+    for k, (f, t) in enumerate(run_batch()):
+        res[f"bf{k}"], res[f"bt{k}"] = f, t
+    np.savez(sys.argv[2], **res)

@@ -37,6 +37,16 @@ def test_library_exports_every_declared_symbol(lb):
         assert hasattr(lb.lib, n), n
 
 
+def test_checked_build_exports_every_declared_symbol(lb):
+    """The bounds-checked build (-DLB_CHECKED) exposes the same C ABI."""
+    import ctypes
+    from paper_1501_03857_gb300 import build
+    assert os.path.exists(build.LIB_CHECKED), "build() makes liblbboil_checked.so beside liblbboil.so"
+    lib = ctypes.CDLL(build.LIB_CHECKED)
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
+
+
 def test_critical_temperature_matches_oracle(lb):
     for a in (3 / 49, 2 / 49):
         cfg = lb.Config(a=a)

@@ -1,0 +1,42 @@
+"""The checked build (liblbboil_checked.so, compiled with -DLB_CHECKED): its
+fused step checks every global and shared-memory address against its buffer
+and flags a miss as LB_E_BOUNDS instead of faulting. On grids with odd
+sizes, every boundary treatment, several launch shapes and a batch of uneven
+instances it flags nothing and produces exactly the states of the normal
+build."""
+
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+# (Lx, Ly, bc, ghost, Gw, isothermal, steps, block_x, seg_rows)
+CASES = [(8, 6, 0, 0, 0.0, 0, 5, 64, 0), (33, 17, 0, 0, 0.08, 0, 40, 64, 6), (33, 17, 1, 0, 0.0, 0, 40, 128, 5),
+         (33, 17, 2, 0, 0.0, 0, 40, 64, 3), (40, 12, 0, 1, 0.0, 0, 20, 128, 0), (21, 9, 0, 0, 0.0, 1, 20, 64, 2),
+         (517, 41, 1, 0, 0.065, 0, 10, 256, 7), (300, 70, 0, 0, 0.105, 0, 10, 128, 0)]
+
+
+def states(tmp_path, lib):
+    out = os.path.join(tmp_path, os.path.basename(lib) + ".npz")
+    env = dict(os.environ, LBBOIL_LIB=lib, PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "tests", "checked_run.py"), json.dumps(CASES), out],
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return np.load(out)
+
+
+def test_checked_build_flags_nothing_and_matches(tmp_path):
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    lib_dir = os.path.join(ROOT, "paper_1501_03857_gb300", "_lib")
+    checked = states(str(tmp_path), os.path.join(lib_dir, "liblbboil_checked.so"))
+    normal = states(str(tmp_path), os.path.join(lib_dir, "liblbboil.so"))
+    assert sorted(checked.files) == sorted(normal.files)
+    for k in normal.files:
+        assert np.array_equal(checked[k], normal[k]), k
