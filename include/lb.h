@@ -254,6 +254,8 @@ int lb_batch_heat_flux(lb_batch* b, double* q_inst, double* q_mean, double* q_st
  * calls of the same name). */
 int lb_batch_get_state(lb_batch* b, int i, float* fpost, float* theta, int on_device);
 int lb_batch_set_state(lb_batch* b, int i, const float* fpost, const float* theta, int on_device);
+/* Macroscopic fields of instance i, as lb_fields (its outputs are [Ly_i*Lx_i]). */
+int lb_batch_fields(lb_batch* b, int i, float* rho, float* ux, float* uy, float* T, int on_device);
 int lb_batch_set_wall_temperature(lb_batch* b, int i, const double* Tb_profile, double superheat);
 int lb_batch_set_wettability(lb_batch* b, int i, double Gw);
 

@@ -1159,6 +1159,11 @@ int lb_batch_get_state(lb_batch* b, int i, float* fpost, float* theta, int on_de
     return lb_get_state(b->inst[i], fpost, theta, on_device);
 }
 
+int lb_batch_fields(lb_batch* b, int i, float* rho, float* ux, float* uy, float* T, int on_device) {
+    if (!b || i < 0 || i >= (int)b->inst.size()) return fail(LB_E_INVAL, "bad batch or instance index");
+    return lb_fields(b->inst[i], rho, ux, uy, T, on_device);
+}
+
 int lb_batch_set_state(lb_batch* b, int i, const float* fpost, const float* theta, int on_device) {
     if (!b || i < 0 || i >= (int)b->inst.size()) return fail(LB_E_INVAL, "bad batch or instance index");
     return lb_set_state(b->inst[i], fpost, theta, on_device);

@@ -121,8 +121,7 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
             batch.step(n)
             done += n
             for i in range(len(cases)):
-                f, _ = batch.get_state(i)
-                rho = f.sum(axis=0)
+                rho = batch.fields(i, ("rho",))["rho"]
                 cov[i].append(wall_coverage(rho, rl, rv))
                 nbub[i].append(len(diagnostics.bubbles(rho, rl, rv)))
         hf = batch.heat_flux()

@@ -84,6 +84,7 @@ def _load():
         "lb_batch_heat_flux": [P, P, P, P, P, I],
         "lb_batch_get_state": [P, I, FP, FP, I],
         "lb_batch_set_state": [P, I, FP, FP, I],
+        "lb_batch_fields": [P, I, FP, FP, FP, FP, I],
         "lb_batch_set_wall_temperature": [P, I, P, D],
         "lb_batch_set_wettability": [P, I, D],
         "lb_batch_info": [P, I64P, C.POINTER(I), C.POINTER(I)],
@@ -443,6 +444,15 @@ class Batch:
         f, fp = _host_ptr(fpost, np.float32)
         t, tp = _host_ptr(theta, np.float32)
         check(lib.lb_batch_set_state(self.h, int(i), fp, tp, 0))
+
+    def fields(self, i: int, which=("rho", "ux", "uy", "T")):
+        """Macroscopic fields of instance i (lb_batch_fields) as host arrays
+        [Ly, Lx]; only the names in `which` are computed and copied."""
+        c = self.cfgs[i]
+        out = {k: np.empty((c.Ly, c.Lx), dtype=np.float32) for k in which}
+        ptr = lambda k: out[k].ctypes.data if k in out else None
+        check(lib.lb_batch_fields(self.h, int(i), ptr("rho"), ptr("ux"), ptr("uy"), ptr("T"), 0))
+        return out
 
     def set_wall_temperature(self, i: int, superheat: float, profile=None):
         prof, pp = _host_ptr(profile, np.float64)

@@ -112,8 +112,8 @@ def run_droplets(gw_values, cfg: lb.Config | None = None, radius: float = 40.0, 
                 done = m
             angles = []
             for i in range(len(gw_values)):
-                f, _ = batch.get_state(i)
-                angles.append(contact_angle(f.sum(axis=0), rl, rv)["angle_deg"])
+                rho = batch.fields(i, ("rho",))["rho"]
+                angles.append(contact_angle(rho, rl, rv)["angle_deg"])
             history[m] = angles
     finally:
         batch.close()

@@ -49,6 +49,14 @@ def test_batch_equals_single_instances(lb, shape):
         hs = sim.heat_flux()
         assert q["n"][i] == hs["n"] == 80
         assert abs(q["q_mean"][i] - hs["q_mean"]) <= 1e-12 * abs(hs["q_mean"])
+        # macroscopic fields of the instance (lb_batch_fields) equal the
+        # single run's (lb_fields); a subset is computed when asked
+        fb_all = batch.fields(i)
+        fs_all = sim.fields()
+        for k in ("rho", "ux", "uy", "T"):
+            assert np.array_equal(fb_all[k], fs_all[k]), (i, k)
+        assert set(batch.fields(i, ("rho",))) == {"rho"}
+        sim.close()
 
 
 def test_batch_parameter_changes_follow_instances(lb):
