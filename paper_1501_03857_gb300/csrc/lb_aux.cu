@@ -1,4 +1,5 @@
-// Off-hot-path kernels: initial state, macroscopic fields, FP64 mass sum.
+// Off-hot-path kernels: initial state, macroscopic fields, FP64 mass sum,
+// and the pressure probe run after a step when probes are set (Fig. 3).
 #include "lb_internal.h"
 
 namespace lbgpu {

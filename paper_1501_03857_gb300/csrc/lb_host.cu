@@ -1,6 +1,9 @@
 // C-ABI implementation (include/lb.h): parameter validation, FP64 host
-// thermodynamics (critical point, Maxwell coexistence), the initial pool,
-// workspace layout, launches and read-back.
+// thermodynamics (critical point, Maxwell coexistence, the EOS pressure),
+// the initial pool, workspace layout, launches (plain steps replayed from
+// captured graphs), read-back, pressure probes, batches of independent
+// instances, and the adjoint driver (checkpoints, segment recomputation
+// overlapped with the reverse sweep).
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
