@@ -24,7 +24,8 @@
  *  - Device-detected faults (EOS domain, non-finite values) latch a flag
  *    that the next synchronising call (lb_sync, lb_heat_flux, lb_fields,
  *    lb_get_state, lb_mass) reports as LB_E_EOS_DOMAIN / LB_E_NONFINITE and
- *    then clears.
+ *    then clears; in the bounds-checked build (liblbboil_checked.so) an
+ *    address outside its buffer is reported the same way as LB_E_BOUNDS.
  */
 #ifndef LB_H
 #define LB_H
@@ -56,8 +57,11 @@ typedef struct lb_grid {
     int32_t Lx, Ly;
     int32_t bc_y;         /* LB_BC_*                                         */
     int32_t ghost_layer;  /* 1: apply F_m on wall rows with a ghost row that
-                             copies the wall row's psi (the ~90 degree
-                             variant of Sec. 3.2); 0: no F on wall rows      */
+                             copies the wall row's psi (Sec. 3.2's ghost-
+                             layer variant, for which the paper reports
+                             about 90 degrees; with this reading a droplet
+                             at G_w = 0 settles near 138 degrees);
+                             0: no F on wall rows (about 44.5 degrees)       */
     int32_t isothermal;   /* 1: skip the temperature equation (T frozen)     */
     int32_t reserved;
 } lb_grid;
@@ -168,13 +172,17 @@ int lb_sync(lb_handle* h);
 int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblocks);
 
 /* Override the launch shape of the current kernel (seg_rows >= 1; 0 keeps
- * the automatic choice). The paired kernel takes block_x 128 or 256, the
- * row-wise kernel any multiple of 32 in [64, 512]. Used by the autotuner. */
+ * the automatic choice; block_x 0 picks the kernel's default). The
+ * dual-strip kernels (2, 3) take block_x 64, 128 or 256, the two-row kernel
+ * (1) 128 or 256, the row-wise kernel (0) any multiple of 32 in [64, 1024].
+ * Results do not depend on the launch shape. Used by the autotuner. */
 int lb_set_launch(lb_handle* h, int block_x, int seg_rows);
 
-/* Select the step kernel: 1 (default) advances two rows per iteration with
- * paired FP32 arithmetic; 0 is the row-wise scalar kernel. Both compute the
- * same update; the launch shape returns to its automatic choice. */
+/* Select the step kernel: 2 (default) marches one row per iteration over
+ * two column strips per block with paired FP32 arithmetic; 3 is the same
+ * with scalar FP32; 1 advances two rows per iteration with paired FP32; 0
+ * is the row-wise scalar kernel. All compute the same update (to FP32
+ * rounding); the launch shape returns to its automatic choice. */
 int lb_set_kernel(lb_handle* h, int kernel);
 
 /* Checkpoint: lb_save_bytes gives the blob size; lb_save writes the state,
@@ -288,6 +296,8 @@ int lb_batch_destroy(lb_batch* b);
  * header's first 8 bytes are the count of probed steps (uint64). */
 #define LB_PROBE_MAX 8
 
+/* Ring bytes for n probes (1 <= n <= LB_PROBE_MAX) keeping `capacity`
+ * steps (1 <= capacity <= 2^26): 256 + 16 n capacity. LB_E_INVAL outside. */
 int lb_probe_ring_bytes(int n, int capacity, size_t* bytes);
 
 /* Probe cells (x[k], y[k]), k < n <= LB_PROBE_MAX, 0 <= x < Lx, 0 <= y < Ly;
