@@ -476,7 +476,8 @@ def collide(ff: FlowFields, P: Params):
 # ---------------------------------------------------------------------------
 
 def neighbours(phi):
-    """phi(x + e_a) for a = 0..8, periodic wrap in both directions. Rows that
+    """phi(x + e_a) for a = 0..8, the neighbourhood the isotropic stencils of
+    Sec. 2 (after Eq. 20) read; periodic wrap in both directions. Rows that
     wrap through a wall are only read by stencils centred on wall rows, whose
     results are discarded (wall rows are Dirichlet)."""
     return torch.stack([torch.roll(phi, shifts=(-EY[a], -EX[a]), dims=(0, 1))
@@ -521,6 +522,9 @@ class FrozenFlow:
 
 
 def frozen_flow(rho, vx, vy) -> FrozenFlow:
+    """The parts of K(T) (Eq. 18) that depend on rho and v only: grad rho and
+    div v with the isotropic stencils, computed once per step because rho
+    and v stay at level t through the four RK stages (Sec. 2, after Eq. 20)."""
     drx, dry = grad_iso(rho)
     dvx, _ = grad_iso(vx)
     _, dvy = grad_iso(vy)
@@ -613,12 +617,14 @@ def initial_state(rho0, P: Params, vx0=None, vy0=None):
 
 
 def total_mass(fpost):
-    """sum over cells of rho = sum_a f*_a (collision conserves mass)."""
+    """sum over cells of rho = sum_a f*_a (collision conserves mass); the
+    mean over cells at t = 0 is rho_ave of Eq. 9."""
     return float(fpost.sum())
 
 
 def run(fpost, theta, P: Params, nsteps: int):
-    """nsteps steps; returns the final state and the per-step q(t) series."""
+    """nsteps steps of the step above; returns the final state and the
+    per-step q(t) series (Sec. 3.2)."""
     qs = []
     for _ in range(nsteps):
         fpost, theta, info = step(fpost, theta, P)

@@ -28,8 +28,9 @@ def _crossing(v0: float, v1: float, level: float) -> float:
 
 
 def contact_angle_cap(rho, rho_l: float, rho_v: float, wall_y: float = 0.0, chord_row: int = 3) -> float:
-    """Contact angle in degrees of the one droplet on the bottom wall of
-    rho[y, x] (periodic in x), by the apex-and-chord cap construction."""
+    """Contact angle in degrees, through the liquid as Sec. 3.3 defines it,
+    of the one droplet on the bottom wall of rho[y, x] (periodic in x), by
+    the apex-and-chord cap construction."""
     rho = np.asarray(rho, dtype=np.float64)
     Ly, Lx = rho.shape
     level = 0.5 * (rho_l + rho_v)
@@ -75,7 +76,9 @@ def cap_density(Lx: int, Ly: int, rho_l: float, rho_v: float, R: float, angle_de
                 width: float = 5.0) -> np.ndarray:
     """A droplet whose mid-density contour is exactly the circle of radius R
     meeting the wall line at the given angle (through the liquid): centre at
-    (Lx/2, wall_y - R cos(angle)), tanh profile of the distance to it."""
+    (Lx/2, wall_y - R cos(angle)), tanh profile of the distance to it. The
+    known-answer input of the angle pins (geometry only, no method
+    arithmetic)."""
     yc = wall_y - R * math.cos(math.radians(angle_deg))
     y, x = np.mgrid[0:Ly, 0:Lx].astype(np.float64)
     r = np.hypot(x - 0.5 * Lx, y - yc)
