@@ -116,3 +116,38 @@ def test_autograd_function(lb):
     _, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, 10, 4)
     assert np.allclose(Tb.grad.numpy(), dTb, rtol=1e-12, atol=0)
     assert abs(float(Gw.grad) - dGw) <= 1e-12 * abs(dGw)
+
+
+def test_gradient_direction_at_bench_scale(lb):
+    """The whole dJ/dT_b(x) vector on the 256 x 256 boiling domain of the
+    benchmark (500-step window after a 200-step transient, checkpoint every
+    100): the FP32 forward's central difference along the normalised
+    gradient g/|g| equals |g| within the 1e-3 bound, and along a direction
+    orthogonal to g it is small against |g|."""
+    L, n = 256, 500
+    cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
+    sh, gw = 0.1 * lb.critical_temperature(cfg), 0.065
+    sim = lb.Simulation(cfg, superheat=sh, Gw=gw)
+    sim.step(200)
+    blob = sim.save()
+    J, g, _ = sim.adjoint(n, 100)
+    norm = float(np.linalg.norm(g))
+    d = g / norm
+
+    def J_of(profile):
+        sim.load(blob)
+        sim.set_wall_temperature(sh, profile)
+        sim.heat_flux(reset=True)
+        sim.step(n)
+        return sim.heat_flux()["q_mean"]
+
+    h = 1e-4
+    along = (J_of(h * d) - J_of(-h * d)) / (2 * h)
+    assert abs(along / norm - 1) < 1e-3, (along, norm)
+    rng = np.random.default_rng(0)
+    o = rng.standard_normal(L)
+    o -= (o @ d) * d
+    o /= np.linalg.norm(o)
+    across = (J_of(h * o) - J_of(-h * o)) / (2 * h)
+    assert abs(across - float(g @ o)) < 1e-3 * norm, (across, float(g @ o), norm)
+    sim.close()
