@@ -20,7 +20,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # (Lx, Ly, bc, ghost, Gw, isothermal, steps, block_x, seg_rows)
 CASES = [(8, 6, 0, 0, 0.0, 0, 5, 64, 0), (33, 17, 0, 0, 0.08, 0, 40, 64, 6), (33, 17, 1, 0, 0.0, 0, 40, 128, 5),
          (33, 17, 2, 0, 0.0, 0, 40, 64, 3), (40, 12, 0, 1, 0.0, 0, 20, 128, 0), (21, 9, 0, 0, 0.0, 1, 20, 64, 2),
-         (517, 41, 1, 0, 0.065, 0, 10, 256, 7), (300, 70, 0, 0, 0.105, 0, 10, 128, 0)]
+         (517, 41, 1, 0, 0.065, 0, 10, 256, 7), (300, 70, 0, 0, 0.105, 0, 10, 128, 0),
+         # the smallest grids the library accepts: one column, three rows
+         (1, 3, 0, 0, 0.0, 0, 6, 64, 0), (1, 9, 2, 0, 0.0, 0, 6, 64, 2), (2, 3, 1, 0, 0.05, 0, 6, 128, 1),
+         (5, 4, 0, 1, 0.0, 0, 6, 64, 1), (3, 5, 2, 0, 0.0, 1, 6, 256, 0)]
 
 
 def states(tmp_path, lib):

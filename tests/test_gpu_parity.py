@@ -70,6 +70,31 @@ def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
         assert abs(h["q_inst"] - qs[0]) <= 1e-5 * abs(qs[0]) + 1e-12
 
 
+MINIMAL = [(1, 3, 0, False, 0.0, False), (1, 9, 2, False, 0.0, False), (2, 3, 1, False, 0.05, False),
+           (5, 4, 0, True, 0.0, False), (3, 5, 2, False, 0.0, True)]
+
+
+@pytest.mark.parametrize("kernel", [2, 3])
+@pytest.mark.parametrize("Lx,Ly,bc,ghost,Gw,iso", MINIMAL)
+def test_one_step_minimal_grids(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
+    """The smallest grids the library accepts (one column, three rows, every
+    boundary treatment) against the oracle, after the bounds-checked build
+    ran them without a flag (test_gpu_checked.py)."""
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, ghost_layer=ghost, isothermal=iso)
+    rv, rl = coex(lb, cfg)
+    rho0, f0, th0 = inputs.random_state(Lx, Ly, rl, rv, Ly * 0.45, seed=Lx * 1000 + Ly)
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=Gw, rho0=rho0)
+    sim.set_kernel(kernel)
+    sim.set_state(f0, th0)
+    sim.step(1)
+    fg, tg = sim.get_state()
+    sim.close()
+    P = oracle_params(cfg, rho0, superheat=0.012, Gw=Gw)
+    fr, tr, _ = run_oracle(f0, th0, P, 1)
+    assert norm_err(fg, fr.numpy()) < TOL_ONE_STEP
+    assert theta_err(tg, tr.numpy(), 0.012) < TOL_ONE_STEP
+
+
 def config1(lb, outflow=True):
     """100 x 100 pool, a = 2/49, superheat 0.1 Tc, pool to y = 40, noise 1e-4,
     seed 1, g = 3e-5 (the small FP64 configuration)."""
