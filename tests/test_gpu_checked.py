@@ -26,6 +26,27 @@ CASES = [(8, 6, 0, 0, 0.0, 0, 5, 64, 0), (33, 17, 0, 0, 0.08, 0, 40, 64, 6), (33
          (5, 4, 0, 1, 0.0, 0, 6, 64, 1), (3, 5, 2, 0, 0.0, 1, 6, 256, 0)]
 
 
+def random_cases(n=40, seed=7):
+    """A seeded sweep of shapes and launch configurations for the index
+    checks: Lx 1-300, Ly 3-120, every boundary treatment, the ghost layer,
+    the thermal step on and off, block_x 64/128/256, segment rows from 1 to
+    past Ly."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        Lx, Ly = int(rng.integers(1, 301)), int(rng.integers(3, 121))
+        bc = int(rng.integers(0, 3))
+        ghost = int(bc != 2 and rng.random() < 0.25)
+        iso = int(rng.random() < 0.2)
+        bx = int(rng.choice([64, 128, 256]))
+        seg = int(rng.choice([0, int(rng.integers(1, Ly + 20))]))
+        out.append((Lx, Ly, bc, ghost, round(float(rng.uniform(0, 0.1)), 3), iso, 3, bx, seg))
+    return out
+
+
+CASES = CASES + random_cases()
+
+
 def states(tmp_path, lib):
     out = os.path.join(tmp_path, os.path.basename(lib) + ".npz")
     env = dict(os.environ, LBBOIL_LIB=lib, PYTHONPATH=ROOT)
