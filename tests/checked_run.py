@@ -26,12 +26,13 @@ def run(case):
     return f, th
 
 
-def run_batch():
+def run_batch(shapes, block_x=64, seg=0):
     insts = []
-    for i, (Lx, Ly, bc) in enumerate(((40, 30, 0), (57, 23, 1), (33, 48, 2))):
+    for i, (Lx, Ly, bc) in enumerate(shapes):
         cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.4 * Ly, seed=20 + i)
-        insts.append({"cfg": cfg, "superheat": 0.01, "Gw": 0.05 * i})
+        insts.append({"cfg": cfg, "superheat": 0.01, "Gw": 0.05 * (i % 3)})
     b = lb.Batch(insts)
+    b.set_launch(block_x, seg)
     b.step(37)
     b.sync()
     out = [b.get_state(i) for i in range(b.n)]
@@ -39,11 +40,19 @@ def run_batch():
     return out
 
 
+def random_batch(seed=11, n=12):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(1, 200)), int(rng.integers(3, 90)), int(rng.integers(0, 3))) for _ in range(n)]
+
+
 if __name__ == "__main__":
     cases = json.loads(sys.argv[1])
     res = {}
     for k, c in enumerate(cases):
         res[f"f{k}"], res[f"t{k}"] = run(c)
-    for k, (f, t) in enumerate(run_batch()):
-        res[f"bf{k}"], res[f"bt{k}"] = f, t
+    batches = [(((40, 30, 0), (57, 23, 1), (33, 48, 2)), 64, 0), (random_batch(), 128, 0),
+               (random_batch(12, 9), 64, 5)]
+    for j, (shapes, bx, seg) in enumerate(batches):
+        for k, (f, t) in enumerate(run_batch(shapes, bx, seg)):
+            res[f"b{j}f{k}"], res[f"b{j}t{k}"] = f, t
     np.savez(sys.argv[2], **res)
