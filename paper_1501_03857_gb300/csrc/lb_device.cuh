@@ -51,7 +51,30 @@ struct StepParams {
     float g, rho_ave, gw6;
     // temperature (Eq. 18): chi = c_v chi / c_v, cvchi = c_v chi
     float chi, cvchi, inv_cv;
+    // the constants of the paired FP32 arithmetic, each duplicated into a
+    // float2 so that a paired instruction can take it from the parameter
+    // bank as it is (set_pairs)
+    float2 kp[27];
 };
+
+enum {
+    KP_TS, KP_K1N, KP_K0, KP_B, KP_R, KP_A, KP_2G, KP_K0K1N, KP_K1K1, KP_CHI6,
+    KP_SE36N, KP_KE6, KP_KESIG, KP_SZ12N, KP_KZ6N, KP_KZSIGN, KP_SQ6, KP_SQ12N, KP_DTAU4, KP_TAUV4,
+    KP_GN12, KP_GW6, KP_GN, KP_RHOAVE, KP_CHI144, KP_RCV12, KP_ACV12, KP_COUNT
+};
+
+// Fill kp from the scalar fields (after any of them changes).
+inline void set_pairs(StepParams& P) {
+    static_assert(KP_COUNT == sizeof(P.kp) / sizeof(P.kp[0]), "kp size");
+    const float G2 = P.G * P.G * (1.f / 144.f);
+    const float ke = (1.f - 0.5f * P.s_e) * (1.f / 36.f), kz = (1.f - 0.5f * P.s_z) * (1.f / 36.f);
+    const float v[KP_COUNT] = {P.Ts, -P.k1, P.k0, P.b, P.R, P.a, P.two_over_G, -P.k0k1, P.k1k1, P.chi * (1.f / 6.f),
+                               -P.s_e * (1.f / 36.f), 6.f * ke, ke * P.sig_e * G2, -P.s_z * (1.f / 12.f), -6.f * kz,
+                               -kz * P.sig_z * G2, P.s_q * (1.f / 6.f), -P.s_q * (1.f / 12.f), 4.f * P.dtau,
+                               4.f * P.tau_v, -P.G * (1.f / 12.f), P.gw6, -P.g, P.rho_ave, P.chi * (1.f / 144.f),
+                               P.R * P.inv_cv * (1.f / 12.f), P.a * P.inv_cv * (1.f / 12.f)};
+    for (int i = 0; i < KP_COUNT; ++i) P.kp[i] = make_float2(v[i], v[i]);
+}
 
 __device__ __forceinline__ int wrap(int v, int n) {
     int r = v % n;

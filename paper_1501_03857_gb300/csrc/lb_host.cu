@@ -282,6 +282,7 @@ void fill_params(lb_handle* h) {
     P.chi = (float)(t.cv_chi / t.cv);
     P.cvchi = (float)t.cv_chi;
     P.inv_cv = (float)(1.0 / t.cv);
+    set_pairs(P);
 }
 
 int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
@@ -619,6 +620,7 @@ int lb_set_wettability(lb_handle* h, double Gw) {
     if (!std::isfinite(Gw)) return fail(LB_E_INVAL, "non-finite Gw");
     h->Gw = Gw;
     h->base.gw6 = (float)(Gw / 6.0);
+    set_pairs(h->base);
     return LB_OK;
 }
 
@@ -798,6 +800,7 @@ int lb_load(lb_handle* h, const void* host_buf, size_t bytes) {
     h->steps = hd.steps;
     h->Gw = hd.Gw;
     h->base.gw6 = (float)(hd.Gw / 6.0);
+    set_pairs(h->base);
     h->superheat = hd.superheat;
     if (hd.has_profile) h->profile.assign((const double*)p, (const double*)p + h->grid.Lx);
     else h->profile.clear();

@@ -24,6 +24,8 @@
 //   F  row L-5  : RK stage 4, store theta^{t+1}
 #include "lb_internal.h"
 
+#include <type_traits>
+
 namespace lbgpu {
 
 namespace {
@@ -126,9 +128,11 @@ __device__ __forceinline__ void load_row2(const StepParams& P, int y, int xa, in
 }
 
 // Isotropic central differences (Lee and Lin; Sec. 2 after Eq. 20) at
-// column s, rows m (below), c, p (above) of float2 ring rows. The first
-// derivatives use the weights 1/3 (axis) and 1/12 (diagonal), the same as
-// sum_a w_a phi(x + e_a) e_a of Eq. 7.
+// column s, rows m (below), c, p (above) of float2 ring rows, without their
+// common factors: dx, dy are 12 x the first derivatives (weights 1/3 axis,
+// 1/12 diagonal: the same as sum_a w_a phi(x + e_a) e_a of Eq. 7) and lap is
+// 6 x the laplacian. The factors are folded into the per-row coefficients
+// that multiply them.
 template <class T>
 struct St2 {
     T dx, dy, lap, c;
@@ -142,12 +146,12 @@ __device__ __forceinline__ St2<T> stencil2(const float2* __restrict__ m, const f
     const T NW(p[-1]), N(p[0]), NE(p[1]);
     const T d1 = NE - SW, d2 = SE - NW;
     St2<T> o;
-    o.dx = fma2(E - W, T::bc(1.f / 3.f), (d1 + d2) * T::bc(1.f / 12.f));
-    o.dy = fma2(N - S, T::bc(1.f / 3.f), (d1 - d2) * T::bc(1.f / 12.f));
+    o.dx = fma2(T::bc(4.f), E - W, d1 + d2);
+    o.dy = fma2(T::bc(4.f), N - S, d1 - d2);
     if (want_lap) {
         const T ax4 = (E + W) + (N + S);
         const T dg = (NE + SW) + (NW + SE);
-        o.lap = fma2(T::bc(-20.f), C, fma2(T::bc(4.f), ax4, dg)) * T::bc(1.f / 6.f);
+        o.lap = fma2(T::bc(-20.f), C, fma2(T::bc(4.f), ax4, dg));
     } else {
         o.lap = T::bc(0.f);
     }
@@ -159,7 +163,8 @@ __device__ __forceinline__ St2<T> stencil2(const float2* __restrict__ m, const f
 // K = ax dT/dx + ay dT/dy + chi lap T - T (cA - cB phi'(T)), where
 // ax = -v_x + chi d_x rho / rho (div(lambda grad T)/(rho c_v) with
 // lambda = c_v chi rho), cA - cB phi' = (dp/dT)_rho div v / (rho c_v) and
-// phi'(T) = k1^2 - k0 k1 / sqrt(T) (derivative of Eq. 21's phi).
+// phi'(T) = k1^2 - k0 k1 / sqrt(T) (derivative of Eq. 21's phi). ax and ay
+// are stored divided by 12 (they multiply the unweighted stencil sums).
 template <class T>
 struct Coef2 {
     T ax, ay, cA, cB;
@@ -167,23 +172,24 @@ struct Coef2 {
 
 template <class T>
 __device__ __forceinline__ T rhs_K2(const St2<T>& u, const Coef2<T>& k, const StepParams& P) {
-    const T Tt = u.c + T::bc(P.Ts);
-    const T dphi = fma2(T::bc(-P.k0k1), rsqrt2(Tt), T::bc(P.k1k1));
+    const T Tt = u.c + T(P.kp[KP_TS]);
+    const T dphi = fma2(T(P.kp[KP_K0K1N]), rsqrt2(Tt), T(P.kp[KP_K1K1]));
     const T src = Tt * fma2(-k.cB, dphi, k.cA);
-    return fma2(k.ax, u.dx, fma2(k.ay, u.dy, fma2(T::bc(P.chi), u.lap, -src)));
+    return fma2(k.ax, u.dx, fma2(k.ay, u.dy, fma2(T(P.kp[KP_CHI6]), u.lap, -src)));
 }
 
 // psi of Sec. 2 with the Peng-Robinson EOS of Eq. 21 for two cells.
 template <class T>
 __device__ __forceinline__ T eos_psi2(T rho, T Tt, const StepParams& P, bool& bad) {
     const T sT = Tt * rsqrt2(Tt);
-    T ph = fma2(T::bc(-P.k1), sT, T::bc(P.k0));
+    T ph = fma2(T(P.kp[KP_K1N]), sT, T(P.kp[KP_K0]));
     ph = ph * ph;
-    const T br = P.b * rho;
-    const T i1 = rcp2(T::bc(1.f) - br);
-    const T i2 = rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));  // 1 + 2 b rho - b^2 rho^2
-    const T p = (P.R * rho) * Tt * i1 - (P.a * ph) * (rho * rho) * i2;
-    const T arg = P.two_over_G * fma2(rho, T::bc(-1.f / 3.f), p);
+    // p = R rho T / d1 - a phi rho^2 / d2 over the common denominator d1 d2
+    const T br = T(P.kp[KP_B]) * rho;
+    const T d1 = T::bc(1.f) - br;
+    const T d2 = fma2(br, T::bc(2.f) - br, T::bc(1.f));  // 1 + 2 b rho - b^2 rho^2
+    const T p = fma2((T(P.kp[KP_R]) * rho) * Tt, d2, -(((T(P.kp[KP_A]) * ph) * (rho * rho)) * d1)) * rcp2(d1 * d2);
+    const T arg = T(P.kp[KP_2G]) * fma2(rho, T::bc(-1.f / 3.f), p);
     const float ax = arg.x(), ay = arg.y();
     bad |= (ax < 0.f) | (ay < 0.f);
     // correctly rounded: psi multiplies the neighbour sums of Eq. 7, so its
@@ -196,8 +202,10 @@ __device__ __forceinline__ T eos_psi2(T rho, T Tt, const StepParams& P, bool& ba
 // (I - Lambda/2) S, for two cells. dm is small (non-equilibrium moments and
 // forces), so FP32 rounding stays at ~1 ulp of f and dm_rho = 0 conserves
 // mass exactly; the non-equilibrium moments use rho v = j + F/2 (Eq. 6).
+// g2 = 144 |sum_a w_a psi(x + e_a) e_a|^2: with F_m = -G psi sum_a ... of
+// Eq. 7, the |F_m|^2 / psi^2 of the sigma term of Eq. 8 is G^2 g2 / 144.
 template <class T>
-__device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T Fx, T Fy, T Fmx, T Fmy, T psi,
+__device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T Fx, T Fy, T g2,
                                          const StepParams& P, T (&o)[9]) {
     const T sa = (f[1] + f[3]) + (f[2] + f[4]);
     const T sd = (f[5] + f[7]) + (f[6] + f[8]);
@@ -205,40 +213,37 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
     const T dyd = (f[5] - f[7]) + (f[6] - f[8]);
     const T rv2 = rho * fma2(vx, vx, vy * vy);
     const T ne1 = fma2(T::bc(-2.f), f[0], fma2(T::bc(4.f), sd, sa)) - 3.f * rv2;
-    const T ne2 = 3.f * ((f[0] - sa) + rv2);
-    const T ne4 = fma2(T::bc(2.f), dxd, fma2(T::bc(0.5f), Fx, f[3] - f[1]));
-    const T ne6 = fma2(T::bc(2.f), dyd, fma2(T::bc(0.5f), Fy, f[4] - f[2]));
+    const T ne2t = (f[0] - sa) + rv2;  // (epsilon - epsilon^eq) / 3
     const T ne7 = ((f[1] + f[3]) - (f[2] + f[4])) - rho * fma2(vx, vx, -(vy * vy));
     const T ne8 = ((f[5] + f[7]) - (f[6] + f[8])) - rho * (vx * vy);
     const T vF = fma2(vx, Fx, vy * Fy);
-    const T psi2 = psi * psi;
-    const T fm2 = fma2(Fmx, Fmx, Fmy * Fmy);
-    const T ratio(psi2.x() > 0.f ? __fdividef(fm2.x(), psi2.x()) : 0.f,
-                  psi2.y() > 0.f ? __fdividef(fm2.y(), psi2.y()) : 0.f);
-    const T S1 = fma2(T::bc(6.f), vF, P.sig_e * ratio);
-    const T S2 = -fma2(T::bc(6.f), vF, P.sig_z * ratio);
     const T S7 = 2.f * fma2(vx, Fx, -(vy * Fy));
     const T S8 = fma2(vx, Fy, vy * Fx);
-    // tau_nu(rho): linear between the coexistence densities, clamped
-    const T sr = (rho - T::bc(P.rho_v)) * T::bc(P.inv_drho);
-    const T sfr(fminf(fmaxf(sr.x(), 0.f), 1.f), fminf(fmaxf(sr.y(), 0.f), 1.f));
-    const T snu = rcp2(fma2(T::bc(P.dtau), sfr, T::bc(P.tau_v)));
-    const T dm1 = fma2(T::bc(-P.s_e), ne1, (1.f - 0.5f * P.s_e) * S1);
-    const T dm2 = fma2(T::bc(-P.s_z), ne2, (1.f - 0.5f * P.s_z) * S2);
-    const T dm4 = fma2(T::bc(-P.s_q), ne4, (0.5f * P.s_q - 1.f) * Fx);
-    const T dm6 = fma2(T::bc(-P.s_q), ne6, (0.5f * P.s_q - 1.f) * Fy);
-    const T hnu = fma2(T::bc(-0.5f), snu, T::bc(1.f));
-    const T dm7 = fma2(-snu, ne7, hnu * S7);
-    const T dm8 = fma2(-snu, ne8, hnu * S8);
-    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4); dm_j = F
-    const T n1 = dm1 * T::bc(1.f / 36.f), n2 = dm2 * T::bc(1.f / 36.f);
-    const T n3 = Fx * T::bc(1.f / 6.f), n4 = dm4 * T::bc(1.f / 12.f);
-    const T n5 = Fy * T::bc(1.f / 6.f), n6 = dm6 * T::bc(1.f / 12.f);
-    const T n7 = dm7 * T::bc(0.25f), n8 = dm8 * T::bc(0.25f);
+    // tau_nu(rho): linear between the coexistence densities, clamped to [0, 1]
+    const float sr0 = -P.rho_v * P.inv_drho;
+    const T sfr(__saturatef(fmaf(rho.x(), P.inv_drho, sr0)), __saturatef(fmaf(rho.y(), P.inv_drho, sr0)));
+    // M^-1 = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) applied
+    // to dm (dm_j = F): n_k = dm_k times its diagonal entry, the entry folded
+    // into the relaxation constants. dm_e, dm_eps: rates s_e, s_z with the
+    // sigma source S = +-(6 v.F + sigma' |F_m|^2 / psi^2) (Eq. 8).
+    const T n1 = fma2(T(P.kp[KP_SE36N]), ne1, fma2(T(P.kp[KP_KE6]), vF, T(P.kp[KP_KESIG]) * g2));
+    const T n2 = fma2(T(P.kp[KP_SZ12N]), ne2t, fma2(T(P.kp[KP_KZ6N]), vF, T(P.kp[KP_KZSIGN]) * g2));
+    // dm_q = -s_q (q - q^eq) + (s_q/2 - 1) F with q - q^eq = qh + F/2, so
+    // dm_q = -s_q qh - F; with n3 = F_x/6, n4 = dm_qx/12: n3 - 2 n4 =
+    // F_x/3 + (s_q/6) qh_x and n3 + n4 = F_x/12 - (s_q/12) qh_x
+    const T qhx = fma2(T::bc(2.f), dxd, f[3] - f[1]);
+    const T qhy = fma2(T::bc(2.f), dyd, f[4] - f[2]);
+    const T cx = fma2(T(P.kp[KP_SQ6]), qhx, T::bc(1.f / 3.f) * Fx);
+    const T cy = fma2(T(P.kp[KP_SQ6]), qhy, T::bc(1.f / 3.f) * Fy);
+    const T dxx = fma2(T(P.kp[KP_SQ12N]), qhx, T::bc(1.f / 12.f) * Fx);
+    const T dyy = fma2(T(P.kp[KP_SQ12N]), qhy, T::bc(1.f / 12.f) * Fy);
+    // p_xx, p_xy: rate s_nu(rho), quartered: snu4 = s_nu / 4, hnu4 = (1 - s_nu/2) / 4
+    const T snu4 = rcp2(fma2(T(P.kp[KP_DTAU4]), sfr, T(P.kp[KP_TAUV4])));
+    const T hnu4 = fma2(T::bc(-0.5f), snu4, T::bc(0.25f));
+    const T n7 = fma2(-snu4, ne7, hnu4 * S7);
+    const T n8 = fma2(-snu4, ne8, hnu4 * S8);
     const T ax_ = fma2(T::bc(-2.f), n2, -n1);
     const T dg = fma2(T::bc(2.f), n1, n2);
-    const T cx = fma2(T::bc(-2.f), n4, n3), cy = fma2(T::bc(-2.f), n6, n5);
-    const T dxx = n3 + n4, dyy = n5 + n6;
     o[0] = fma2(T::bc(4.f), n2 - n1, f[0]);
     o[1] = f[1] + ((ax_ + cx) + n7);
     o[2] = f[2] + ((ax_ + cy) - n7);
@@ -308,6 +313,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
     const int ys = seg * P.seg_h;
     const int ye = min(ys + P.seg_h, Ly);
     auto lo = [&](int d) { return periodic ? ys - d : max(ys - d, 0); };
+    // with walls every pipeline row is in [0, Ly) and is its own physical row
+    auto interior = [&](int r) { return periodic || (r != 0 && r != Ly - 1); };
     auto hi = [&](int d) { return periodic ? ye + d : min(ye + d, Ly); };
     const int loP = lo(5), hiP = hi(5), loB = lo(4), hiB = hi(4), loC = lo(3), hiC = hi(3);
     const int loD = lo(2), hiD = hi(2), loE = lo(1), hiE = hi(1);
@@ -329,10 +336,18 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
     __syncthreads();
 
     int yL = wrap_row(loP, Ly);  // physical row of pipeline row L
-    for (int L = loP; L <= ye + 4; ++L) {
+    // One iteration of the pipeline. In the steady part (S) every stage's row
+    // lies in the block's own rows and off the walls, so the range and wall
+    // tests are compiled out; the first and last iterations keep them.
+    auto iter = [&](const int L, auto steady) {
+        constexpr bool S = decltype(steady)::value;
         // ---- prefetch the pulled populations of row L+1
         T fn[9], tn = zero;
         const int yN = yL + 1 == Ly ? 0 : yL + 1;
+        // (the range test stays in the steady part too: without it the
+        // loads are no longer issued a whole iteration ahead of their use,
+        // and their latency shows up as long-scoreboard stalls, 1.3 cycles
+        // per issued instruction instead of 0.2)
         if (L + 1 < hiP) {
             load_row2(P, yN, xa, xam, xap, xb, xbm, xbp, fn, tn);
         } else {
@@ -341,22 +356,22 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
         }
 
         // ---- P: wall fill, rho, psi of row L
-        if (L < hiP) {
+        if (S || L < hiP) {
             const int y = yL;
-            if (!periodic && y == 0) {  // Zou-He bottom wall, u = 0
+            if (!S && !periodic && y == 0) {  // Zou-He bottom wall, u = 0
                 const T d = 0.5f * (fc[1] - fc[3]);
                 fc[2] = fc[4];
                 fc[5] = fc[7] - d;
                 fc[6] = fc[8] + d;
             }
-            if (P.bc == BC_WALLS && y == Ly - 1) {  // Zou-He top wall, u = 0
+            if (!S && P.bc == BC_WALLS && y == Ly - 1) {  // Zou-He top wall, u = 0
                 const T d = 0.5f * (fc[1] - fc[3]);
                 fc[4] = fc[2];
                 fc[7] = fc[5] + d;
                 fc[8] = fc[6] - d;
             }
             const T rhoN = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
-            const T psiN = eos_psi2(rhoN, tc + T::bc(P.Ts), P, eos_bad);
+            const T psiN = eos_psi2(rhoN, tc + T(P.kp[KP_TS]), P, eos_bad);
             *LB_SMP(sPSI + (L & 3) * W + s) = psiN.f2();
             *LB_SMP(sRHO + (L & 3) * W + s) = rhoN.f2();
             *LB_SMP(sTH + (L & 7) * W + s) = tc.f2();
@@ -364,7 +379,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
         __syncthreads();
 
         // ---- bottom-wall heat flux of level t (Sec. 3.2), one sample per step
-        if (!periodic && ys == 0 && L == 2) {
+        if (!S && !periodic && ys == 0 && L == 2) {
             double qv = 0.0;
             const float2 r0 = *LB_SMP(sRHO + 0 * W + s), t0 = *LB_SMP(sTH + 0 * W + s), t1 = *LB_SMP(sTH + 1 * W + s), t2 = *LB_SMP(sTH + 2 * W + s);
             if (outa) qv += -(double)P.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
@@ -398,26 +413,28 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
         // ---- B: forces, velocity, collision of row L-1
         {
             const int r = L - 1;
-            if (r >= loB && r < hiB) {
+            if (S || (r >= loB && r < hiB)) {
                 const int y = yL == 0 ? Ly - 1 : yL - 1;
-                const bool wall = !periodic && (y == 0 || y == Ly - 1);
+                const bool wall = !S && !periodic && (y == 0 || y == Ly - 1);
                 const T rhoP(*LB_SMP(sRHO + (r & 3) * W + s));
                 const T psiP(*LB_SMP(sPSI + (r & 3) * W + s));
                 const T jxP = (fP[1] - fP[3]) + (fP[5] - fP[6]) + (fP[8] - fP[7]);
                 const T jyP = (fP[2] - fP[4]) + (fP[5] + fP[6]) - (fP[7] + fP[8]);
-                T Fmx = zero, Fmy = zero;
+                T Fmx = zero, Fmy = zero, g2 = zero;
                 if (!wall || P.ghost) {
                     const float2* pc = sPSI + (r & 3) * W + s;
                     const float2* pn = (wall && y == Ly - 1) ? pc : sPSI + ((r + 1) & 3) * W + s;
                     const float2* ps = (wall && y == 0) ? pc : sPSI + ((r - 1) & 3) * W + s;
-                    const St2<T> g = stencil2<T>(LB_SMP(ps), LB_SMP(pc), LB_SMP(pn), false);  // sum_a w_a psi(x + e_a) e_a, Eq. 7
-                    Fmx = (-P.G) * (psiP * g.dx);
-                    Fmy = (-P.G) * (psiP * g.dy);
+                    const St2<T> g = stencil2<T>(LB_SMP(ps), LB_SMP(pc), LB_SMP(pn), false);  // 12 sum_a w_a psi(x + e_a) e_a, Eq. 7
+                    const T mG = T(P.kp[KP_GN12]) * psiP;
+                    Fmx = mG * g.dx;
+                    Fmy = mG * g.dy;
+                    g2 = fma2(g.dx, g.dx, g.dy * g.dy);
                 }
                 T Fy = Fmy;
                 if (!wall) {
-                    if (!periodic && y == 1) Fy = fma2(T::bc(P.gw6), psiP * psiP, Fy);  // Eq. 22
-                    Fy = fma2(T::bc(-P.g), rhoP - T::bc(P.rho_ave), Fy);                // Eq. 9
+                    if (!S && !periodic && y == 1) Fy = fma2(T(P.kp[KP_GW6]), psiP * psiP, Fy);  // Eq. 22
+                    Fy = fma2(T(P.kp[KP_GN]), rhoP - T(P.kp[KP_RHOAVE]), Fy);                // Eq. 9
                 }
                 const T Fx = Fmx;
                 const T irho = rcp2(rhoP);
@@ -425,10 +442,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 const T vy = fma2(T::bc(0.5f), Fy, jyP) * irho;
                 *LB_SMP(sVX + (r & 3) * W + s) = vx.f2();
                 *LB_SMP(sVY + (r & 3) * W + s) = vy.f2();
-                const bool st = r >= ys && r < ye;
+                const bool st = S || (r >= ys && r < ye);
                 if (st && (outa || outb)) {
                     T o[9];
-                    collide2(fP, rhoP, vx, vy, Fx, Fy, Fmx, Fmy, psiP, P, o);
+                    collide2(fP, rhoP, vx, vy, Fx, Fy, g2, P, o);
                     const int pl = P.plane;
                     float* out = P.f_out + y * P.pitch;
                     if (outa) {
@@ -453,24 +470,23 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             // ---- C: frozen-flow coefficients and RK stage 1 of row L-2
             {
                 const int r = L - 2;
-                if (r >= loC && r < hiC) {
-                    const int y = wrap_row(yL - 2, Ly);
+                if (S || (r >= loC && r < hiC)) {
                     const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                     T u2 = thr;
-                    if (periodic || (y != 0 && y != Ly - 1)) {
+                    if (S || interior(r)) {
                         const int om = ((r - 1) & 3) * W + s, oc = (r & 3) * W + s, op = ((r + 1) & 3) * W + s;
                         const St2<T> gr = stencil2<T>(LB_SMP(sRHO + om), LB_SMP(sRHO + oc), LB_SMP(sRHO + op), false);
                         const St2<T> gvx = stencil2<T>(LB_SMP(sVX + om), LB_SMP(sVX + oc), LB_SMP(sVX + op), false);
                         const St2<T> gvy = stencil2<T>(LB_SMP(sVY + om), LB_SMP(sVY + oc), LB_SMP(sVY + op), false);
                         const T rho = gr.c;
-                        const T irho = rcp2(rho);
-                        const T divv = gvx.dx + gvy.dy;
-                        const T br = P.b * rho;
-                        Coef2<T> kC;
-                        kC.ax = fma2(T::bc(P.chi), gr.dx * irho, -gvx.c);
-                        kC.ay = fma2(T::bc(P.chi), gr.dy * irho, -gvy.c);
-                        kC.cA = (P.R * P.inv_cv) * divv * rcp2(T::bc(1.f) - br);
-                        kC.cB = (P.a * P.inv_cv) * (divv * rho) * rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));
+                        const T q = T(P.kp[KP_CHI144]) * rcp2(rho);
+                        const T divv = gvx.dx + gvy.dy;  // 12 div v
+                        const T br = T(P.kp[KP_B]) * rho;
+                        Coef2<T> kC;  // ax, ay divided by 12
+                        kC.ax = fma2(q, gr.dx, T::bc(-1.f / 12.f) * gvx.c);
+                        kC.ay = fma2(q, gr.dy, T::bc(-1.f / 12.f) * gvy.c);
+                        kC.cA = T(P.kp[KP_RCV12]) * divv * rcp2(T::bc(1.f) - br);
+                        kC.cB = T(P.kp[KP_ACV12]) * (divv * rho) * rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));
                         float2* c = LB_SMC(sCO + (r & 3) * BD + lc);
                         c[0] = kC.ax.f2();
                         c[RING * BD] = kC.ay.f2();
@@ -487,11 +503,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             // ---- D: RK stage 2 of row L-3
             {
                 const int r = L - 3;
-                if (r >= loD && r < hiD) {
-                    const int y = wrap_row(yL - 3, Ly);
+                if (S || (r >= loD && r < hiD)) {
                     const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                     T u3 = thr;
-                    if (periodic || (y != 0 && y != Ly - 1)) {
+                    if (S || interior(r)) {
                         const St2<T> u = stencil2<T>(LB_SMP(sU2 + ((r - 1) & 3) * W + s), LB_SMP(sU2 + (r & 3) * W + s), LB_SMP(sU2 + ((r + 1) & 3) * W + s), true);
                         const T h2 = rhs_K2(u, coef(r), P);
                         u3 = fma2(T::bc(0.5f), h2, thr);
@@ -504,11 +519,10 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             // ---- E: RK stage 3 of row L-4
             {
                 const int r = L - 4;
-                if (r >= loE && r < hiE) {
-                    const int y = wrap_row(yL - 4, Ly);
+                if (S || (r >= loE && r < hiE)) {
                     const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                     T u4 = thr;
-                    if (periodic || (y != 0 && y != Ly - 1)) {
+                    if (S || interior(r)) {
                         const St2<T> u = stencil2<T>(LB_SMP(sU3 + ((r - 1) & 3) * W + s), LB_SMP(sU3 + (r & 3) * W + s), LB_SMP(sU3 + ((r + 1) & 3) * W + s), true);
                         const T h3 = rhs_K2(u, coef(r), P);
                         u4 = thr + h3;
@@ -522,14 +536,14 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
         // ---- F: RK stage 4 and theta^{t+1} of row L-5
         {
             const int r = L - 5;
-            if (r >= ys && r < ye && (outa || outb)) {
-                const int y = wrap_row(yL - 5, Ly);
+            if ((S || (r >= ys && r < ye)) && (outa || outb)) {
+                const int y = periodic ? wrap_row(yL - 5, Ly) : r;
                 const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                 T tnew = thr;
                 if (thermal) {
-                    if (!periodic && y == 0) {
+                    if (!S && !periodic && y == 0) {
                         tnew = T(lb_ldg(P.thb + xa, P.thb, P.pitch, P.acc), lb_ldg(P.thb + xb, P.thb, P.pitch, P.acc));
-                    } else if (!periodic && y == Ly - 1) {
+                    } else if (!S && !periodic && y == Ly - 1) {
                         tnew = zero;
                     } else {
                         const St2<T> u = stencil2<T>(LB_SMP(sU4 + ((r - 1) & 3) * W + s), LB_SMP(sU4 + (r & 3) * W + s), LB_SMP(sU4 + ((r + 1) & 3) * W + s), true);
@@ -559,7 +573,16 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
         }
         tc = tn;
         yL = yN;
-    }
+    };
+    // steady iterations: F's row L-5 >= ys (B, C, D, E then also in the
+    // block's rows), B's row L-1 < ye; with walls F's row >= 1 and P's row
+    // L <= Ly - 2, so no stage meets a wall row or the first fluid row
+    const int Ls = ys + 5 + (!periodic && ys == 0 ? 1 : 0);
+    const int Le = max(Ls, periodic ? ye + 1 : min(ye + 1, Ly - 1));
+    int L = loP;
+    for (; L < Ls; ++L) iter(L, std::false_type{});
+    for (; L < Le; ++L) iter(L, std::true_type{});
+    for (; L <= ye + 4; ++L) iter(L, std::false_type{});
     if (eos_bad) atomicOr(&P.acc->err, ERR_EOS);
     if (nonfinite) atomicOr(&P.acc->err, ERR_NONFINITE);
 }

@@ -13,12 +13,23 @@
   deviation, and h_c = q_bar / Delta T. The heated wall's vapour coverage
   (the fraction of the first fluid row below the mid density) and the
   number of vapour bubbles in the pool are sampled every sample_every steps.
+  Boiling is chaotic: near the top of a curve neighbouring superheats differ
+  by less than the run-to-run spread of one window's mean, so the location
+  of the maximum moves with any rounding-level change. With several seeds
+  (the initial density noise of the pool) every case runs once per seed in
+  the same batch and the case statistics are ensemble averages over them.
 * classify_curve: the regime of every case of a curve, after Sec. 3.2: no
   boiling forms no vapour at the heated wall and no bubbles; film boiling
   keeps the whole heating surface under a continuous vapour film; the
-  remaining (boiling) cases are nucleate up to the superheat of the
-  critical (maximum) heat flux of their curve and transition beyond it,
-  where vapour patches insulate the liquid and q falls.
+  remaining (boiling) cases are nucleate up to the largest heat flux
+  attainable in nucleate boiling and transition beyond it, where vapour
+  patches insulate the liquid and q no longer rises with the superheat
+  (Sec. 1 defines transition boiling as lying between the maximum of
+  nucleate boiling and the minimum of film boiling). With seed ensembles
+  that limit is the lowest superheat no higher case exceeds by more than
+  two combined standard errors of the means (nucleate_limit); for single
+  runs it is the superheat of the largest mean flux. An ensemble case is
+  film (no) boiling when most of its runs are.
 
 Superheats are in lattice units (Delta T = T_b - T_s), as in the paper.
 """
@@ -72,45 +83,90 @@ def wall_coverage(rho: np.ndarray, rho_l: float, rho_v: float, row: int = 1) -> 
     return float(np.mean(np.asarray(rho)[row] < 0.5 * (rho_l + rho_v)))
 
 
+def nucleate_limit(cases) -> float:
+    """Superheat of the largest heat flux attainable in nucleate boiling for
+    the boiling cases of one curve (dicts with superheat, q_mean and
+    optionally q_sem): the lowest superheat whose mean flux no higher case
+    exceeds by more than twice the combined standard error (q_sem missing or
+    NaN counts as 0, which gives the superheat of the largest mean)."""
+    cs = sorted(cases, key=lambda c: c["superheat"])
+
+    def sem(c):
+        v = c.get("q_sem", 0.0)
+        return 0.0 if v != v else float(v)
+
+    for i, c in enumerate(cs):
+        if all(d["q_mean"] <= c["q_mean"] + 2.0 * np.hypot(sem(c), sem(d)) for d in cs[i + 1:]):
+            return c["superheat"]
+    raise ValueError("no boiling cases")
+
+
 def classify_curve(cases) -> list:
-    """Regime of each case dict (superheat, Gw, q_mean, coverage_min,
-    coverage_max, bubbles_max) of one or more curves; cases are grouped by
-    G_w and each group's critical heat flux is its largest q_mean among the
-    boiling, non-film cases."""
+    """Regime of each case dict (superheat, Gw, q_mean, optionally q_sem,
+    coverage_min, coverage_max, bubbles_max) of one or more curves; cases
+    are grouped by G_w and the boiling, non-film cases of a group are
+    nucleate up to its nucleate_limit and transition beyond it. A seed
+    ensemble (film_fraction, none_fraction present) is film or no boiling
+    when most of its runs are."""
     labels = []
     for c in cases:
-        if c["coverage_min"] >= FILM_COVERAGE:
-            labels.append("film")
-        elif c["coverage_max"] == 0.0 and c["bubbles_max"] == 0:
-            labels.append("none")
+        if "film_fraction" in c:
+            film, none = c["film_fraction"] > 0.5, c["none_fraction"] > 0.5
         else:
-            labels.append("boiling")
-    chf = {}
-    for c, lab in zip(cases, labels):
-        if lab == "boiling" and (c["Gw"] not in chf or c["q_mean"] > chf[c["Gw"]][1]):
-            chf[c["Gw"]] = (c["superheat"], c["q_mean"])
-    return [("nucleate" if c["superheat"] <= chf[c["Gw"]][0] else "transition") if lab == "boiling" else lab
+            film = c["coverage_min"] >= FILM_COVERAGE
+            none = c["coverage_max"] == 0.0 and c["bubbles_max"] == 0
+        labels.append("film" if film else "none" if none else "boiling")
+    limit = {}
+    for gw in set(c["Gw"] for c, lab in zip(cases, labels) if lab == "boiling"):
+        limit[gw] = nucleate_limit([c for c, lab in zip(cases, labels) if lab == "boiling" and c["Gw"] == gw])
+    return [("nucleate" if c["superheat"] <= limit[c["Gw"]] else "transition") if lab == "boiling" else lab
             for c, lab in zip(cases, labels)]
+
+
+def ensemble(runs: list) -> dict:
+    """One case's statistics over the runs of its seeds (dicts with q_mean,
+    q_std and the sampled coverage and bubble series): mean flux and its
+    standard error over the seeds, mean within-window deviation, coverage
+    mean / min / max and bubble count mean / max over every sample of every
+    run, and the fractions of runs that kept a film on the wall in every
+    sample or formed no vapour at all (film_fraction, none_fraction)."""
+    qm = np.array([r["q_mean"] for r in runs], dtype=np.float64)
+    cov = np.concatenate([np.asarray(r["coverage"], dtype=np.float64) for r in runs])
+    nb = np.concatenate([np.asarray(r["bubbles"]) for r in runs])
+    sem = float(qm.std(ddof=1) / np.sqrt(len(qm))) if len(qm) > 1 else float("nan")
+    film = [min(r["coverage"]) >= FILM_COVERAGE for r in runs]
+    none = [max(r["coverage"]) == 0.0 and max(r["bubbles"]) == 0 for r in runs]
+    return {"q_mean": float(qm.mean()), "q_sem": sem, "q_runs": [float(q) for q in qm],
+            "q_std": float(np.mean([r["q_std"] for r in runs])),
+            "coverage_mean": float(cov.mean()), "coverage_min": float(cov.min()), "coverage_max": float(cov.max()),
+            "bubbles_mean": float(nb.mean()), "bubbles_max": int(nb.max()),
+            "film_fraction": float(np.mean(film)), "none_fraction": float(np.mean(none))}
 
 
 def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, base_superheat: float = 0.0137,
                   t_switch: int = 20000, t_settle: int = 5000, t_avg: int = 15000, sample_every: int = 500,
-                  stream=None) -> dict:
+                  seeds=None, stream=None) -> dict:
     """The boiling curve(s) for every (Delta T, G_w) pair in one batch;
     returns per case q_bar, q_std, h_c, the wall coverage (mean, min, max),
     the bubble count (mean, max) and the regime, and per G_w the superheat
-    and value of the critical heat flux and of the largest h_c."""
+    and value of the largest mean heat flux (chf), the nucleate_limit
+    superheat and the superheat and value of the largest h_c. `seeds`
+    (default: cfg.seed alone) runs every case once per seed of the pool's
+    initial noise; the case statistics are then ensemble averages (see
+    `ensemble`), with q_sem the standard error of q_bar over the seeds."""
     cfg = cfg or paper_config()
+    seeds = [cfg.seed] if seeds is None else [int(s) for s in seeds]
     rv, rl = lb.coexistence(cfg)
     cases = [(float(dT), float(gw)) for gw in Gw_values for dT in superheats]
-    insts = [{"cfg": cfg, "Gw": gw, "superheat": (base_superheat if dT > base_superheat else dT)}
-             for dT, gw in cases]
+    runs = [(c, sd) for c in cases for sd in seeds]
+    insts = [{"cfg": replace(cfg, seed=sd), "Gw": gw, "superheat": (base_superheat if dT > base_superheat else dT)}
+             for (dT, gw), sd in runs]
     batch = lb.Batch(insts, stream=stream)
-    cov = [[] for _ in cases]
-    nbub = [[] for _ in cases]
+    cov = [[] for _ in runs]
+    nbub = [[] for _ in runs]
     try:
         batch.step(t_switch)
-        for i, (dT, gw) in enumerate(cases):
+        for i, ((dT, gw), _) in enumerate(runs):
             if dT > base_superheat:
                 batch.set_wall_temperature(i, dT)
         batch.step(t_settle)
@@ -120,7 +176,7 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
             n = min(sample_every, t_avg - done)
             batch.step(n)
             done += n
-            for i in range(len(cases)):
+            for i in range(len(runs)):
                 rho = batch.fields(i, ("rho",))["rho"]
                 cov[i].append(wall_coverage(rho, rl, rv))
                 nbub[i].append(len(diagnostics.bubbles(rho, rl, rv)))
@@ -128,12 +184,11 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
     finally:
         batch.close()
     out = []
-    for i, (dT, gw) in enumerate(cases):
-        qm, qs = float(hf["q_mean"][i]), float(hf["q_std"][i])
-        out.append({"superheat": dT, "Gw": gw, "q_mean": qm, "q_std": qs, "h_c": qm / dT,
-                    "coverage_mean": float(np.mean(cov[i])), "coverage_min": float(np.min(cov[i])),
-                    "coverage_max": float(np.max(cov[i])), "bubbles_mean": float(np.mean(nbub[i])),
-                    "bubbles_max": int(np.max(nbub[i]))})
+    for k, (dT, gw) in enumerate(cases):
+        idx = [i for i, (c, _) in enumerate(runs) if c == (dT, gw)]
+        st = ensemble([{"q_mean": float(hf["q_mean"][i]), "q_std": float(hf["q_std"][i]), "coverage": cov[i],
+                        "bubbles": nbub[i]} for i in idx])
+        out.append(dict({"superheat": dT, "Gw": gw, "h_c": st["q_mean"] / dT}, **st))
     for c, lab in zip(out, classify_curve(out)):
         c["regime"] = lab
     curves = {}
@@ -141,7 +196,9 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
         grp = [c for c in out if c["Gw"] == gw]
         top = max(grp, key=lambda c: c["q_mean"])
         best = max(grp, key=lambda c: c["h_c"])
-        curves[gw] = {"chf_superheat": top["superheat"], "chf": top["q_mean"],
+        boil = [c for c in grp if c["regime"] in ("nucleate", "transition")]
+        curves[gw] = {"chf_superheat": top["superheat"], "chf": top["q_mean"], "chf_sem": top["q_sem"],
+                      "nucleate_limit_superheat": nucleate_limit(boil) if boil else None,
                       "hc_max_superheat": best["superheat"], "hc_max": best["h_c"]}
     return {"t_switch": t_switch, "t_settle": t_settle, "t_avg": t_avg, "base_superheat": base_superheat,
-            "cases": out, "curves": curves}
+            "seeds": seeds, "cases": out, "curves": curves}
