@@ -173,7 +173,8 @@ int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblo
 
 /* Override the launch shape of the current kernel (seg_rows >= 1; 0 keeps
  * the automatic choice; block_x 0 picks the kernel's default). The
- * dual-strip kernels (2, 3) take block_x 64, 128 or 256, the two-row kernel
+ * dual-strip kernels (2, 3) take block_x 64, 128 or 256 (default: 64 up to
+ * 4096 columns, 128 beyond), the two-row kernel
  * (1) 128 or 256, the row-wise kernel (0) any multiple of 32 in [64, 1024].
  * Results do not depend on the launch shape. Used by the autotuner. */
 int lb_set_launch(lb_handle* h, int block_x, int seg_rows);

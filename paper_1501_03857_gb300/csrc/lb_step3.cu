@@ -650,11 +650,19 @@ struct DualKernel {
     }
 };
 
-// the instantiations a launch can pick: (block size, paired FP32 or scalar)
+// the instantiations a launch can pick: (block size, paired FP32 or scalar).
+// The single-domain step is compiled for 12 warps per SM (6 blocks of 64 or
+// 3 of 128, up to 170 registers a thread; it takes about 148), not 16 (8 x 64
+// or 4 x 128 at 128 registers): within 128 registers the compiler spends ~50
+// more instructions per cell on copies and recomputation, which costs more
+// than the four warps gain (4096^2: 0.385 ms at 6 x 64 and 0.391 ms at 3 x 128
+// against 0.420 ms at 4 x 128). The batched step keeps 128 registers: with
+// its parameters in shared memory it ran 7 % slower with the larger budget.
+
 template <class T>
 cudaError_t dual_prepare_t() {
-    cudaError_t e = DualKernel<64, 8, T>::prepare();
-    if (e == cudaSuccess) e = DualKernel<128, 4, T>::prepare();
+    cudaError_t e = DualKernel<64, 6, T>::prepare();
+    if (e == cudaSuccess) e = DualKernel<128, 3, T>::prepare();
     if (e == cudaSuccess) e = DualKernel<256, 2, T>::prepare();
     return e;
 }
@@ -667,16 +675,16 @@ cudaError_t batch_prepare_t() {
 
 template <class T>
 cudaError_t dual_occupancy_t(int block_x, int* n) {
-    if (block_x == 64) return DualKernel<64, 8, T>::occupancy(n);
-    if (block_x == 128) return DualKernel<128, 4, T>::occupancy(n);
+    if (block_x == 64) return DualKernel<64, 6, T>::occupancy(n);
+    if (block_x == 128) return DualKernel<128, 3, T>::occupancy(n);
     return DualKernel<256, 2, T>::occupancy(n);
 }
 
 template <class T>
 cudaError_t dual_launch_t(const StepParams& P, const Launch& L, cudaStream_t st) {
     const int nb = L.nstrips * L.nseg;
-    if (L.block_x == 64) return DualKernel<64, 8, T>::launch(P, nb, st);
-    if (L.block_x == 128) return DualKernel<128, 4, T>::launch(P, nb, st);
+    if (L.block_x == 64) return DualKernel<64, 6, T>::launch(P, nb, st);
+    if (L.block_x == 128) return DualKernel<128, 3, T>::launch(P, nb, st);
     return DualKernel<256, 2, T>::launch(P, nb, st);
 }
 
