@@ -4,9 +4,10 @@
 // Eq. 22.
 //
 // Forward intermediates of step n are recomputed from the stored state
-// (f*^n, theta^n) by plain field kernels (one thread per cell) that follow
-// the fused step's formulas; the reverse passes then transpose each part of
-// the step in the opposite order:
+// (f*^n, theta^n): on large domains by the fused step itself in its
+// recompute mode (lb_step3.cu, RecomputeOut), on small ones by field kernels
+// (one thread per cell) that follow its formulas. The reverse passes (field
+// kernels) then transpose each part of the step in the opposite order:
 //
 //   RK4 of Eq. 18 (stage 4 .. 1)   -> lambda_theta, lambda of the per-cell
 //                                     coefficients (ax, ay, cA, cB)
@@ -117,7 +118,12 @@ __device__ __forceinline__ Eos eos(float rho, float T, const StepParams& P) {
     return e;
 }
 
-// ---- forward recompute ----------------------------------------------------
+// ---- forward recompute by field kernels ---------------------------------------
+//
+// For small domains, where the fused step's 5-row pipeline halo and its
+// sequential march dominate (a 256 x 256 step takes ~20 us in it), the
+// intermediates are recomputed by these one-thread-per-cell kernels, which
+// follow the fused step's formulas.
 
 __global__ void fwd_pull(const StepParams P, AdjFields A) {
     int x, y, i;
@@ -211,27 +217,12 @@ __global__ void fwd_coef(const StepParams P, AdjFields A) {
     A.cB[i] = divv * P.a * rho * P.inv_cv / (1.f + 2.f * br - br * br);
 }
 
-// lambda-bar (the incoming lambda_theta on fluid rows), mu_4 = lambda-bar / 6,
-// dJ/d theta_b += incoming lambda_theta on the bottom wall row (the Dirichlet
-// value of the new level), and zeroed coefficient adjoints, for cell i.
-__device__ __forceinline__ void rev_init_cell(const StepParams& P, const AdjFields& A, int x, int y, int i,
-                                              bool wall) {
-    const float lin = A.lt_in[i];
-    if (P.bc != BC_PERIODIC && y == 0) A.dTb[x] += (double)lin;
-    const float lbar = wall ? 0.f : lin;
-    A.lth[i] = lbar;  // identity part of theta' = theta + ...
-    A.mu[i] = lbar * (1.f / 6.f);
-    A.lax[i] = A.lay[i] = A.lcA[i] = A.lcB[i] = 0.f;
-}
-
-// u_out = theta + c K(u_in) on fluid rows, theta on wall rows (Eqs. 18-20);
-// with init != 0 also the start of the reverse sweep (rev_init_cell).
-__global__ void fwd_stage(const StepParams P, AdjFields A, const float* u_in, float* u_out, float c, int init) {
+// u_out = theta + c K(u_in) on fluid rows, theta on wall rows (Eqs. 18-20).
+__global__ void fwd_stage(const StepParams P, AdjFields A, const float* u_in, float* u_out, float c) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
     const Grid g = grid_of(P);
     const bool wall = g.wall(y);
-    if (init) rev_init_cell(P, A, x, y, i, wall);
     if (wall) {
         u_out[i] = A.theta[i];
         return;
@@ -278,23 +269,40 @@ __device__ __forceinline__ void rev_coef_cell(const StepParams& P, const AdjFiel
 // Transpose of one RK stage h = mask K(u): from mu (= mask lambda_h) compute
 // lambda_u (transposed stencils + the diagonal source term), accumulate the
 // coefficient adjoints and lambda_theta (u = theta + ...), and form the next
-// stage's mu = mask (a lambda-bar + b lambda_u).
-__global__ void rev_stage(const StepParams P, AdjFields A, const float* u, float a_bar, float b_u, int last) {
+// stage's mu = mask (a lambda-bar + b lambda_u). The first (stage 4) starts
+// the sweep: its mu is lambda-bar / 6 with lambda-bar the incoming
+// lambda_theta on fluid rows, the accumulators start from lambda-bar
+// (identity part of theta' = theta + ...) and 0, and the incoming lambda of
+// the new bottom wall row (its Dirichlet value) goes to dJ/d theta_b.
+__global__ void rev_stage(const StepParams P, AdjFields A, const float* u, float a_bar, float b_u, int first,
+                          int last) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
     const Grid g = grid_of(P);
     const bool wall = g.wall(y);
-    float lu = 0.f;
+    auto mu_at = [&](int j, int yj) {
+        return first ? (g.wall(yj) ? 0.f : A.lt_in[j] * (1.f / 6.f)) : A.mu[j];
+    };
+    // the nine neighbours' mu first (issued together), then their
+    // coefficients only where mu is non-zero: lambda is zero away from the
+    // heated wall early in a reverse sweep, and those cells cost no traffic
+    float mj[9];
+    int jj[9];
+#pragma unroll
     for (int a = 0; a < 9; ++a) {
         // source cell s = y - d with d = e_a contributes c_d(s) mu(s)
-        const int j = g.at(x, y, -EXd[a], -EYd[a]);
-        if (j < 0) continue;
-        const float m = A.mu[j];
-        if (m == 0.f) continue;
-        const int dx = EXd[a], dy = EYd[a];
-        lu += (A.ax[j] * wdx(dx, dy) + A.ay[j] * wdy(dx, dy) + P.chi * wlap(dx, dy)) * m;
+        jj[a] = g.at(x, y, -EXd[a], -EYd[a]);
+        mj[a] = jj[a] < 0 ? 0.f : mu_at(jj[a], y - EYd[a]);
     }
-    const float m = A.mu[i];
+    float lu = 0.f;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        if (mj[a] == 0.f) continue;
+        const int j = jj[a], dx = EXd[a], dy = EYd[a];
+        lu += (A.ax[j] * wdx(dx, dy) + A.ay[j] * wdy(dx, dy) + P.chi * wlap(dx, dy)) * mj[a];
+    }
+    const float m = mj[0];  // own cell (e_0 = 0)
+    float lax = 0.f, lay = 0.f, lcA = 0.f, lcB = 0.f;
     if (!wall && m != 0.f) {
         const float T = P.Ts + u[i];
         const float sT = sqrtf(T);
@@ -302,17 +310,34 @@ __global__ void rev_stage(const StepParams P, AdjFields A, const float* u, float
         const float d2phi = 0.5f * P.k0k1 / (sT * T);
         lu += (-(A.cA[i] - A.cB[i] * dphi) + T * A.cB[i] * d2phi) * m;
         float dx = 0.f, dy = 0.f;
+#pragma unroll
         for (int a = 1; a < 9; ++a) {
             const float un = u[g.at(x, y, EXd[a], EYd[a])];
             dx += wdx(EXd[a], EYd[a]) * un;
             dy += wdy(EXd[a], EYd[a]) * un;
         }
-        A.lax[i] += dx * m;
-        A.lay[i] += dy * m;
-        A.lcA[i] += -T * m;
-        A.lcB[i] += T * dphi * m;
+        lax = dx * m;
+        lay = dy * m;
+        lcA = -T * m;
+        lcB = T * dphi * m;
     }
-    A.lth[i] += lu;
+    if (first) {
+        const float lin = A.lt_in[i];
+        if (P.bc != BC_PERIODIC && y == 0) A.dTb[x] += (double)lin;
+        A.lax[i] = lax;
+        A.lay[i] = lay;
+        A.lcA[i] = lcA;
+        A.lcB[i] = lcB;
+        A.lth[i] = (wall ? 0.f : lin) + lu;
+    } else {
+        if (lax != 0.f || lay != 0.f || lcA != 0.f || lcB != 0.f) {
+            A.lax[i] += lax;
+            A.lay[i] += lay;
+            A.lcA[i] += lcA;
+            A.lcB[i] += lcB;
+        }
+        A.lth[i] += lu;
+    }
     if (!last) {
         const float lin = A.lt_in[i];
         const float lbar = wall ? 0.f : lin;
@@ -468,12 +493,20 @@ __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
         }
         lpsi += -P.G * (sx * A.lFmx[i] + sy * A.lFmy[i]);
     }
-    for (int a = 1; a < 9; ++a) {  // neighbour factor: psi(y) appears in F_m(y - e_a)
-        const int j = g.at(x, y, -EXd[a], -EYd[a]);
-        if (j < 0) continue;
-        const float lfx = A.lFmx[j], lfy = A.lFmy[j];
-        if (lfx == 0.f && lfy == 0.f) continue;
-        lpsi += -P.G * A.psi[j] * (wdx(EXd[a], EYd[a]) * lfx + wdy(EXd[a], EYd[a]) * lfy);
+    // neighbour factor: psi(y) appears in F_m(y - e_a); the eight lambda_F_m
+    // pairs first (issued together), psi only where they are non-zero
+    float lfx[9], lfy[9];
+    int jj[9];
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        jj[a] = g.at(x, y, -EXd[a], -EYd[a]);
+        lfx[a] = jj[a] < 0 ? 0.f : A.lFmx[jj[a]];
+        lfy[a] = jj[a] < 0 ? 0.f : A.lFmy[jj[a]];
+    }
+#pragma unroll
+    for (int a = 1; a < 9; ++a) {
+        if (lfx[a] == 0.f && lfy[a] == 0.f) continue;
+        lpsi += -P.G * A.psi[jj[a]] * (wdx(EXd[a], EYd[a]) * lfx[a] + wdy(EXd[a], EYd[a]) * lfy[a]);
     }
     float lrho = A.lrho[i];
     float lth = A.lth[i];
@@ -533,6 +566,12 @@ __global__ void rev_pull(const StepParams P, AdjFields A) {
         A.lf_out[a * P.plane + i] = j < 0 ? 0.f : A.lf[a * P.plane + j];
     }
 }
+
+// Domains of at least this many cells recompute with the fused step (one
+// launch instead of six; at 2048^2 the reverse step takes 0.83 ms instead of
+// 0.96 ms); smaller ones with the field kernels (at 256^2 the six small
+// launches take ~15 us, the fused step ~20 us).
+constexpr size_t kFusedRecomputeCells = 512 * 512;
 
 // Work-buffer layout: 54 field planes, then dJ/d theta_b [pitch doubles], the
 // per-column dJ/dG_w parts [pitch doubles] and dJ/dG_w.
@@ -639,10 +678,11 @@ cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* l
 }
 
 // One reverse step: state (fstar, theta) of level n, lambda of level n+1 in
-// (lf_in, lt_in), lambda of level n out; lq = dJ/dq(t_n).
-cudaError_t adjoint_reverse_step(const StepParams& P, void* work, const float* fstar, const float* theta,
-                                 const float* lf_in, const float* lt_in, float* lf_out, float* lt_out, float lq,
-                                 cudaStream_t st) {
+// (lf_in, lt_in), lambda of level n out; lq = dJ/dq(t_n). L is a dual-strip
+// launch shape matching P (nout, nstrips, seg_h) for the recompute.
+cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* work, const float* fstar,
+                                 const float* theta, const float* lf_in, const float* lt_in, float* lf_out,
+                                 float* lt_out, float lq, cudaStream_t st) {
     AdjFields A = fields_at(P, work);
     A.fstar = fstar;
     A.theta = theta;
@@ -653,17 +693,31 @@ cudaError_t adjoint_reverse_step(const StepParams& P, void* work, const float* f
     // 32 x 8 tiles: the vertical neighbours of a warp's cells are read by the
     // warps above and below it in the same block, so they stay in L1
     const dim3 blk(32, 8), grid((P.Lx + 31) / 32, (P.Ly + 7) / 8);
-    fwd_pull<<<grid, blk, 0, st>>>(P, A);
-    fwd_force<<<grid, blk, 0, st>>>(P, A);
-    fwd_coef<<<grid, blk, 0, st>>>(P, A);
-    fwd_stage<<<grid, blk, 0, st>>>(P, A, theta, A.u2, 0.5f, 0);
-    fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u2, A.u3, 0.5f, 0);
-    fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u3, A.u4, 1.0f, 1);
+    // the step's intermediates from (f*^n, theta^n): written by the fused step
+    // on large domains, by the field kernels above on small ones
+    StepParams Q = P;
+    Q.f_in = fstar;
+    Q.th_in = theta;
+    Q.f_out = nullptr;
+    Q.th_out = nullptr;
+    const RecomputeOut R{A.f,   A.rho, A.psi,  A.jx, A.jy, A.Fmx, A.Fmy, A.Fx, A.Fy, A.vx, A.vy,
+                         A.drx, A.dry, A.divv, A.ax, A.ay, A.cA,  A.cB,  A.u2, A.u3, A.u4};
+    if ((size_t)P.Lx * P.Ly >= kFusedRecomputeCells) {
+        cudaError_t e = dual_recompute(Q, R, L, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        fwd_pull<<<grid, blk, 0, st>>>(P, A);
+        fwd_force<<<grid, blk, 0, st>>>(P, A);
+        fwd_coef<<<grid, blk, 0, st>>>(P, A);
+        fwd_stage<<<grid, blk, 0, st>>>(P, A, theta, A.u2, 0.5f);
+        fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u2, A.u3, 0.5f);
+        fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u3, A.u4, 1.0f);
+    }
     const float* us[4] = {A.u4, A.u3, A.u2, theta};
     const float abar[4] = {1.f / 3.f, 1.f / 3.f, 1.f / 6.f, 0.f};
     const float bu[4] = {1.f, 0.5f, 0.5f, 0.f};
     for (int k = 0; k < 4; ++k) {
-        rev_stage<<<grid, blk, 0, st>>>(P, A, us[k], abar[k], bu[k], k == 3);
+        rev_stage<<<grid, blk, 0, st>>>(P, A, us[k], abar[k], bu[k], k == 0, k == 3);
         float* t = A.mu;
         A.mu = A.mu_next;
         A.mu_next = t;

@@ -285,7 +285,8 @@ void fill_params(lb_handle* h) {
     set_pairs(P);
 }
 
-int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
+// The launch shape of `kernel` for this grid (block_x, seg_rows 0: automatic).
+int compute_launch(const lb_handle* h, int kernel, int block_x, int seg_rows, Launch* out) {
     int dev = 0, nsm = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
@@ -320,14 +321,39 @@ int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
         seg = std::max(8, (Ly + nseg - 1) / nseg);
     }
     if (kernel == KERNEL_PAIRS) seg += seg & 1;  // segments start on even rows
-    h->launch.kernel = kernel;
-    h->launch.block_x = bx;
-    h->launch.seg_rows = seg;
-    h->launch.nstrips = nstrips;
-    h->launch.nseg = (Ly + seg - 1) / seg;
-    h->base.nout = nout;
-    h->base.nstrips = nstrips;
-    h->base.seg_h = seg;
+    out->kernel = kernel;
+    out->block_x = bx;
+    out->seg_rows = seg;
+    out->nstrips = nstrips;
+    out->nseg = (Ly + seg - 1) / seg;
+    return LB_OK;
+}
+
+// The step parameters that describe launch shape L.
+void apply_launch(StepParams& P, const Launch& L) {
+    P.nout = L.block_x - 2 * HALO;
+    P.nstrips = L.nstrips;
+    P.seg_h = L.seg_rows;
+}
+
+int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
+    Launch L;
+    const int rc = compute_launch(h, kernel, block_x, seg_rows, &L);
+    if (rc) return rc;
+    h->launch = L;
+    apply_launch(h->base, L);
+    return LB_OK;
+}
+
+// Clear the device fault flags err (read after the stream drained) and map
+// them to an error code.
+int report_device_errors(lb_handle* h, unsigned err) {
+    if (!err) return LB_OK;
+    const unsigned z = 0;
+    LB_CUDA(cudaMemcpy(&h->acc->err, &z, sizeof(unsigned), cudaMemcpyHostToDevice), "clear error flags");
+    if (err & ERR_BOUNDS) return fail(LB_E_BOUNDS, "a device index left its buffer (checked build)");
+    if (err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature on the device");
+    if (err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument 2(p - rho/3)/G < 0 (EOS domain)");
     return LB_OK;
 }
 
@@ -335,14 +361,7 @@ int check_device_errors(lb_handle* h) {
     unsigned err = 0;
     LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
     LB_CUDA(cudaMemcpy(&err, &h->acc->err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error flags");
-    if (err) {
-        const unsigned z = 0;
-        LB_CUDA(cudaMemcpy(&h->acc->err, &z, sizeof(unsigned), cudaMemcpyHostToDevice), "clear error flags");
-        if (err & ERR_BOUNDS) return fail(LB_E_BOUNDS, "a device index left its buffer (checked build)");
-        if (err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature on the device");
-        if (err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument 2(p - rho/3)/G < 0 (EOS domain)");
-    }
-    return LB_OK;
+    return report_device_errors(h, err);
 }
 
 int upload_wall(lb_handle* h) {
@@ -629,8 +648,10 @@ int lb_set_wettability(lb_handle* h, double Gw) {
 int lb_heat_flux(lb_handle* h, double* q_inst, double* q_mean, double* q_std, int64_t* nsamples, int reset) {
     if (!h) return fail(LB_E_INVAL, "null handle");
     Acc a;
+    // one read of the accumulator record, fault flags included
     LB_CUDA(cudaMemcpyAsync(&a, h->acc, sizeof(Acc), cudaMemcpyDeviceToHost, h->st), "read accumulators");
-    int rc = check_device_errors(h);
+    LB_CUDA(cudaStreamSynchronize(h->st), "cudaStreamSynchronize");
+    int rc = report_device_errors(h, a.err);
     const double n = a.q_n;
     const double mean = n > 0 ? a.q_sum / n : 0.0;
     const double var = n > 1 ? std::max(0.0, (a.q_sum2 - n * mean * mean) / (n - 1)) : 0.0;
@@ -1338,11 +1359,20 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         }
         return LB_OK;
     };
+    // the reverse step recomputes the step's intermediates with the paired
+    // dual-strip kernel: its launch shape (the current one if that kernel is
+    // in use)
+    Launch RL = h->launch;
+    StepParams RB = base;
+    if (RL.kernel != KERNEL_DUAL && RL.kernel != KERNEL_DUAL_SCALAR) {
+        if ((rc = compute_launch(h, KERNEL_DUAL, 0, 0, &RL))) return rc;
+        apply_launch(RB, RL);
+    }
     auto sweep = [&](int len, int buf, int c0, cudaStream_t q) -> int {
         int c = c0;
         for (int j = len - 1; j >= 0; --j) {
             const float* fs = seg_state(buf, j);
-            LB_CUDA(adjoint_reverse_step(base, work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl, lam[1 - c],
+            LB_CUDA(adjoint_reverse_step(RB, RL, work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl, lam[1 - c],
                                          lam[1 - c] + 9 * pl, lq, q),
                     "adjoint reverse step");
             c ^= 1;

@@ -34,6 +34,21 @@ cudaError_t dual_prepare();
 cudaError_t dual_occupancy(int block_x, bool paired, int* blocks_per_sm);
 cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st);
 
+// The forward intermediates of one step that the adjoint's reverse kernels
+// read (lb_adjoint.cu), written by the dual-strip step in its recompute mode
+// (lb_step3.cu): the pulled and wall-filled populations (9 planes, plane
+// stride StepParams::plane) and the pitched [Ly][pitch] planes below. The
+// gradients drx, dry and div v carry the stencil weights; ax, ay, cA, cB are
+// the coefficients of K(T), Eq. 18 (0 on the wall rows); u2-u4 the RK stage
+// inputs (theta on the wall rows). The step itself (f*, theta of the next
+// level, heat flux) is not written in this mode.
+struct RecomputeOut {
+    float* f;
+    float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *Fx, *Fy, *vx, *vy;
+    float *drx, *dry, *divv, *ax, *ay, *cA, *cB, *u2, *u3, *u4;
+};
+cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Launch& L, cudaStream_t st);
+
 // The same step over a table of independent instances in one launch
 // (paired FP32, block_x 64 or 128); instance i owns blocks
 // [block_off[i], block_off[i+1]).
@@ -57,9 +72,9 @@ cudaError_t launch_macro(const StepParams& P, float* scratch, float* rho, float*
 // (which adds the initial wall row's lambda_theta to dJ/d theta_b).
 size_t adjoint_work_bytes(const StepParams& P);
 cudaError_t adjoint_grads_reset(const StepParams& P, void* work, cudaStream_t st);
-cudaError_t adjoint_reverse_step(const StepParams& P, void* work, const float* fstar, const float* theta,
-                                 const float* lf_in, const float* lt_in, float* lf_out, float* lt_out, float lq,
-                                 cudaStream_t st);
+cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* work, const float* fstar,
+                                 const float* theta, const float* lf_in, const float* lt_in, float* lf_out,
+                                 float* lt_out, float lq, cudaStream_t st);
 cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* lt0, double* dTb_host,
                                  double* dGw_host, cudaStream_t st);
 

@@ -257,9 +257,12 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
 
 }  // namespace
 
-// The whole step for block `block` of the launch described by P.
-template <int BD, class T>
-__device__ __forceinline__ void step_body(const StepParams& P, const int block) {
+// The whole step for block `block` of the launch described by P. With REC
+// (the adjoint's recompute mode) the block writes the forward intermediates
+// of its own cells to R instead of the collided populations, theta^{t+1} and
+// the heat flux (RecomputeOut, lb_internal.h).
+template <int BD, class T, bool REC = false>
+__device__ __forceinline__ void step_body(const StepParams& P, const int block, const RecomputeOut* R = nullptr) {
     constexpr int W = BD + 2;
     extern __shared__ float2 sm2[];
     __shared__ double red[BD / 32];
@@ -320,6 +323,12 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
     const int loD = lo(2), hiD = hi(2), loE = lo(1), hiE = hi(1);
     const bool thermal = !P.isothermal;
     bool eos_bad = false, nonfinite = false;
+    // recompute mode: a value pair into row y of a pitched plane, own columns
+    auto put = [&](float* plane, int y, T v) {
+        float* row = plane + y * P.pitch;
+        if (outa) lb_st(row + xa, v.x(), plane, (size_t)P.plane, P.acc);
+        if (outb) lb_st(row + xb, v.y(), plane, (size_t)P.plane, P.acc);
+    };
     const T zero = T::bc(0.f);
 
     T fc[9], tc = zero;
@@ -375,11 +384,19 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
             *LB_SMP(sPSI + (L & 3) * W + s) = psiN.f2();
             *LB_SMP(sRHO + (L & 3) * W + s) = rhoN.f2();
             *LB_SMP(sTH + (L & 7) * W + s) = tc.f2();
+            if constexpr (REC) {
+                if (L >= ys && L < ye) {
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) put(R->f + (size_t)a * P.plane, y, fc[a]);
+                    put(R->rho, y, rhoN);
+                    put(R->psi, y, psiN);
+                }
+            }
         }
         __syncthreads();
 
         // ---- bottom-wall heat flux of level t (Sec. 3.2), one sample per step
-        if (!S && !periodic && ys == 0 && L == 2) {
+        if (!REC && !S && !periodic && ys == 0 && L == 2) {
             double qv = 0.0;
             const float2 r0 = *LB_SMP(sRHO + 0 * W + s), t0 = *LB_SMP(sTH + 0 * W + s), t1 = *LB_SMP(sTH + 1 * W + s), t2 = *LB_SMP(sTH + 2 * W + s);
             if (outa) qv += -(double)P.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
@@ -443,7 +460,18 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                 *LB_SMP(sVX + (r & 3) * W + s) = vx.f2();
                 *LB_SMP(sVY + (r & 3) * W + s) = vy.f2();
                 const bool st = S || (r >= ys && r < ye);
-                if (st && (outa || outb)) {
+                if constexpr (REC) {
+                    if (st) {
+                        put(R->jx, y, jxP);
+                        put(R->jy, y, jyP);
+                        put(R->Fmx, y, Fmx);
+                        put(R->Fmy, y, Fmy);
+                        put(R->Fx, y, Fx);
+                        put(R->Fy, y, Fy);
+                        put(R->vx, y, vx);
+                        put(R->vy, y, vy);
+                    }
+                } else if (st && (outa || outb)) {
                     T o[9];
                     collide2(fP, rhoP, vx, vy, Fx, Fy, g2, P, o);
                     const int pl = P.plane;
@@ -495,8 +523,35 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                         const St2<T> ut = stencil2<T>(LB_SMP(sTH + ((r - 1) & 7) * W + s), LB_SMP(sTH + (r & 7) * W + s), LB_SMP(sTH + ((r + 1) & 7) * W + s), true);
                         accC = rhs_K2(ut, kC, P);
                         u2 = fma2(T::bc(0.5f), accC, thr);
+                        if constexpr (REC) {
+                            if (S || (r >= ys && r < ye)) {  // weighted gradients, unscaled coefficients
+                                const int y = periodic ? wrap_row(yL - 2, Ly) : r;
+                                const T w12 = T::bc(1.f / 12.f), t12 = T::bc(12.f);
+                                put(R->drx, y, w12 * gr.dx);
+                                put(R->dry, y, w12 * gr.dy);
+                                put(R->divv, y, w12 * divv);
+                                put(R->ax, y, t12 * kC.ax);
+                                put(R->ay, y, t12 * kC.ay);
+                                put(R->cA, y, kC.cA);
+                                put(R->cB, y, kC.cB);
+                            }
+                        }
+                    } else if constexpr (REC) {
+                        if (r >= ys && r < ye) {
+                            const int y = periodic ? wrap_row(yL - 2, Ly) : r;
+                            put(R->drx, y, zero);
+                            put(R->dry, y, zero);
+                            put(R->divv, y, zero);
+                            put(R->ax, y, zero);
+                            put(R->ay, y, zero);
+                            put(R->cA, y, zero);
+                            put(R->cB, y, zero);
+                        }
                     }
                     *LB_SMP(sU2 + (r & 3) * W + s) = u2.f2();
+                    if constexpr (REC) {
+                        if (S || (r >= ys && r < ye)) put(R->u2, periodic ? wrap_row(yL - 2, Ly) : r, u2);
+                    }
                 }
             }
             __syncthreads();
@@ -513,6 +568,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                         acc1 = fma2(T::bc(2.f), h2, acc1);
                     }
                     *LB_SMP(sU3 + (r & 3) * W + s) = u3.f2();
+                    if constexpr (REC) {
+                        if (S || (r >= ys && r < ye)) put(R->u3, periodic ? wrap_row(yL - 3, Ly) : r, u3);
+                    }
                 }
             }
             __syncthreads();
@@ -529,6 +587,9 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
                         acc2 = fma2(T::bc(2.f), h3, acc2);
                     }
                     *LB_SMP(sU4 + (r & 3) * W + s) = u4.f2();
+                    if constexpr (REC) {
+                        if (S || (r >= ys && r < ye)) put(R->u4, periodic ? wrap_row(yL - 4, Ly) : r, u4);
+                    }
                 }
             }
             __syncthreads();
@@ -536,7 +597,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
         // ---- F: RK stage 4 and theta^{t+1} of row L-5
         {
             const int r = L - 5;
-            if ((S || (r >= ys && r < ye)) && (outa || outb)) {
+            if (!REC && (S || (r >= ys && r < ye)) && (outa || outb)) {
                 const int y = periodic ? wrap_row(yL - 5, Ly) : r;
                 const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                 T tnew = thr;
@@ -592,6 +653,12 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block) 
 template <int BD, int MINB, class T>
 __global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
     step_body<BD, T>(P, blockIdx.x);
+}
+
+// The forward intermediates of one step for the adjoint (paired FP32).
+template <int BD, int MINB>
+__global__ void __launch_bounds__(BD, MINB) lb_step_recompute(const StepParams P, const __grid_constant__ RecomputeOut R) {
+    step_body<BD, P2, true>(P, blockIdx.x, &R);
 }
 
 // Many independent simulations in one launch (the boiling-curve batch): the
@@ -692,9 +759,36 @@ cudaError_t dual_launch_t(const StepParams& P, const Launch& L, cudaStream_t st)
 
 bool dual_supported(int block_x) { return block_x == 64 || block_x == 128 || block_x == 256; }
 
+namespace {
+
+template <int BD, int MINB>
+cudaError_t recompute_prepare_t() {
+    return cudaFuncSetAttribute(lb_step_recompute<BD, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)DualKernel<BD, MINB, P2>::smem());
+}
+
+template <int BD, int MINB>
+cudaError_t recompute_t(const StepParams& P, const RecomputeOut& R, int nblocks, cudaStream_t st) {
+    lb_step_recompute<BD, MINB><<<nblocks, BD, DualKernel<BD, MINB, P2>::smem(), st>>>(P, R);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Launch& L, cudaStream_t st) {
+    const int nb = L.nstrips * L.nseg;
+    if (L.block_x == 64) return recompute_t<64, 6>(P, R, nb, st);
+    if (L.block_x == 128) return recompute_t<128, 3>(P, R, nb, st);
+    if (L.block_x == 256) return recompute_t<256, 2>(P, R, nb, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t dual_prepare() {
     cudaError_t e = dual_prepare_t<P2>();
     if (e == cudaSuccess) e = dual_prepare_t<S2>();
+    if (e == cudaSuccess) e = recompute_prepare_t<64, 6>();
+    if (e == cudaSuccess) e = recompute_prepare_t<128, 3>();
+    if (e == cudaSuccess) e = recompute_prepare_t<256, 2>();
     return e;
 }
 

@@ -118,13 +118,16 @@ def test_autograd_function(lb):
     assert abs(float(Gw.grad) - dGw) <= 1e-12 * abs(dGw)
 
 
-def test_gradient_direction_at_bench_scale(lb):
+@pytest.mark.parametrize("L", [256, 512])
+def test_gradient_direction_at_bench_scale(lb, L):
     """The whole dJ/dT_b(x) vector on the 256 x 256 boiling domain of the
     benchmark (500-step window after a 200-step transient, checkpoint every
     100): the FP32 forward's central difference along the normalised
     gradient g/|g| equals |g| within the 1e-3 bound, and along a direction
-    orthogonal to g it is small against |g|."""
-    L, n = 256, 500
+    orthogonal to g it is small against |g|. At 512 x 512 the reverse steps
+    recompute the step's intermediates with the fused step kernel, at
+    256 x 256 (and in the tests above) with the field kernels."""
+    n = 500
     cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
     sh, gw = 0.1 * lb.critical_temperature(cfg), 0.065
     sim = lb.Simulation(cfg, superheat=sh, Gw=gw)
