@@ -943,6 +943,8 @@ struct lb_batch {
     cudaStream_t gs;             // private stream the captured graphs run on
     cudaEvent_t ev_in, ev_out;
     cudaGraphExec_t graph;       // GRAPH_STEPS steps starting at parity 0
+    bool kshared;                // all instances share the model constants
+    StepParams kconst;           // ... which are these (instance 0's parameters)
 };
 
 namespace {
@@ -958,6 +960,24 @@ size_t batch_tail_offset(const lb_batch_desc* d, int n, std::vector<size_t>* off
     return off;
 }
 
+// The model constants the step reads from K (step_body, lb_step3.cu): the
+// float2 pairs except the wettability and rho_ave, inv_drho, rho_v, cvchi.
+bool same_constants(const StepParams& a, const StepParams& b) {
+    for (int k = 0; k < KP_COUNT; ++k)
+        if (k != KP_GW6 && k != KP_RHOAVE && memcmp(&a.kp[k], &b.kp[k], sizeof(float2)) != 0) return false;
+    return a.inv_drho == b.inv_drho && a.rho_v == b.rho_v && a.cvchi == b.cvchi;
+}
+
+// Whether every instance shares instance 0's model constants; if so the step
+// takes them from its parameters (lb_step_batch_k) instead of each block's
+// shared-memory copy.
+void batch_constants(lb_batch* b) {
+    b->kconst = b->inst[0]->base;
+    b->kshared = true;
+    for (lb_handle* h : b->inst)
+        if (!same_constants(h->base, b->kconst)) b->kshared = false;
+}
+
 // Common block size, per-instance segment height and block offsets. With an
 // automatic segment height every instance gets a share of one full wave
 // proportional to its cells.
@@ -966,7 +986,8 @@ int batch_layout(lb_batch* b) {
     int dev = 0, nsm = 0, occ = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-    LB_CUDA(batch_occupancy(b->block_x, &occ), "occupancy");
+    batch_constants(b);
+    LB_CUDA(batch_occupancy(b->block_x, b->kshared, &occ), "occupancy");
     if (occ < 1) return fail(LB_E_INVAL, "batch block_x %d does not fit on an SM", b->block_x);
     const int nout = b->block_x - 2 * HALO;
     long long cells = 0;
@@ -1028,7 +1049,9 @@ int batch_upload(lb_batch* b) {
 
 int batch_launch_one(lb_batch* b, cudaStream_t s, int parity) {
     const int n = (int)b->inst.size();
-    LB_CUDA(batch_launch(b->block_x, b->table + parity * n, b->block_off, n, b->nblocks, s), "batch step launch");
+    LB_CUDA(batch_launch(b->block_x, b->table + parity * n, b->block_off, n, b->nblocks,
+                         b->kshared ? &b->kconst : nullptr, s),
+            "batch step launch");
     return LB_OK;
 }
 

@@ -54,9 +54,11 @@ cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Lau
 // [block_off[i], block_off[i+1]).
 bool batch_supported(int block_x);
 cudaError_t batch_prepare();
-cudaError_t batch_occupancy(int block_x, int* blocks_per_sm);
+cudaError_t batch_occupancy(int block_x, bool shared_k, int* blocks_per_sm);
+// K non-null: every instance shares the model constants in *K (see
+// step_body in lb_step3.cu) and the kernel reads them from its parameters.
 cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,
-                         cudaStream_t st);
+                         const StepParams* K, cudaStream_t st);
 
 // Initial state: f* = w_a rho0 (rest equilibrium), theta = 0 with the wall
 // rows at their Dirichlet values. rho0 is pitched [Ly][pitch].

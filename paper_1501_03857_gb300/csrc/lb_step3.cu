@@ -257,12 +257,17 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
 
 }  // namespace
 
-// The whole step for block `block` of the launch described by P. With REC
-// (the adjoint's recompute mode) the block writes the forward intermediates
-// of its own cells to R instead of the collided populations, theta^{t+1} and
-// the heat flux (RecomputeOut, lb_internal.h).
+// The whole step for block `block` of the launch described by P. K supplies
+// the model constants (kp except the wettability and rho_ave pairs,
+// inv_drho, rho_v, cvchi): the same struct as P for one domain, or the
+// batch's shared constants in the parameter bank while P is an instance's
+// copy in shared memory. With REC (the adjoint's recompute mode) the block
+// writes the forward intermediates of its own cells to R instead of the
+// collided populations, theta^{t+1} and the heat flux (RecomputeOut,
+// lb_internal.h).
 template <int BD, class T, bool REC = false>
-__device__ __forceinline__ void step_body(const StepParams& P, const int block, const RecomputeOut* R = nullptr) {
+__device__ __forceinline__ void step_body(const StepParams& P, const StepParams& K, const int block,
+                                          const RecomputeOut* R = nullptr) {
     constexpr int W = BD + 2;
     extern __shared__ float2 sm2[];
     __shared__ double red[BD / 32];
@@ -380,7 +385,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                 fc[8] = fc[6] - d;
             }
             const T rhoN = ((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7])) + fc[8];
-            const T psiN = eos_psi2(rhoN, tc + T(P.kp[KP_TS]), P, eos_bad);
+            const T psiN = eos_psi2(rhoN, tc + T(K.kp[KP_TS]), K, eos_bad);
             *LB_SMP(sPSI + (L & 3) * W + s) = psiN.f2();
             *LB_SMP(sRHO + (L & 3) * W + s) = rhoN.f2();
             *LB_SMP(sTH + (L & 7) * W + s) = tc.f2();
@@ -399,8 +404,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
         if (!REC && !S && !periodic && ys == 0 && L == 2) {
             double qv = 0.0;
             const float2 r0 = *LB_SMP(sRHO + 0 * W + s), t0 = *LB_SMP(sTH + 0 * W + s), t1 = *LB_SMP(sTH + 1 * W + s), t2 = *LB_SMP(sTH + 2 * W + s);
-            if (outa) qv += -(double)P.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
-            if (outb) qv += -(double)P.cvchi * r0.y * (-3.0 * t0.y + 4.0 * t1.y - t2.y) * 0.5;
+            if (outa) qv += -(double)K.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
+            if (outb) qv += -(double)K.cvchi * r0.y * (-3.0 * t0.y + 4.0 * t1.y - t2.y) * 0.5;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) qv += __shfl_down_sync(0xffffffffu, qv, o);
             if ((lc & 31) == 0) red[lc >> 5] = qv;
@@ -443,7 +448,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                     const float2* pn = (wall && y == Ly - 1) ? pc : sPSI + ((r + 1) & 3) * W + s;
                     const float2* ps = (wall && y == 0) ? pc : sPSI + ((r - 1) & 3) * W + s;
                     const St2<T> g = stencil2<T>(LB_SMP(ps), LB_SMP(pc), LB_SMP(pn), false);  // 12 sum_a w_a psi(x + e_a) e_a, Eq. 7
-                    const T mG = T(P.kp[KP_GN12]) * psiP;
+                    const T mG = T(K.kp[KP_GN12]) * psiP;
                     Fmx = mG * g.dx;
                     Fmy = mG * g.dy;
                     g2 = fma2(g.dx, g.dx, g.dy * g.dy);
@@ -451,7 +456,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                 T Fy = Fmy;
                 if (!wall) {
                     if (!S && !periodic && y == 1) Fy = fma2(T(P.kp[KP_GW6]), psiP * psiP, Fy);  // Eq. 22
-                    Fy = fma2(T(P.kp[KP_GN]), rhoP - T(P.kp[KP_RHOAVE]), Fy);                // Eq. 9
+                    Fy = fma2(T(K.kp[KP_GN]), rhoP - T(P.kp[KP_RHOAVE]), Fy);                // Eq. 9
                 }
                 const T Fx = Fmx;
                 const T irho = rcp2(rhoP);
@@ -473,7 +478,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                     }
                 } else if (st && (outa || outb)) {
                     T o[9];
-                    collide2(fP, rhoP, vx, vy, Fx, Fy, g2, P, o);
+                    collide2(fP, rhoP, vx, vy, Fx, Fy, g2, K, o);
                     const int pl = P.plane;
                     float* out = P.f_out + y * P.pitch;
                     if (outa) {
@@ -507,21 +512,21 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                         const St2<T> gvx = stencil2<T>(LB_SMP(sVX + om), LB_SMP(sVX + oc), LB_SMP(sVX + op), false);
                         const St2<T> gvy = stencil2<T>(LB_SMP(sVY + om), LB_SMP(sVY + oc), LB_SMP(sVY + op), false);
                         const T rho = gr.c;
-                        const T q = T(P.kp[KP_CHI144]) * rcp2(rho);
+                        const T q = T(K.kp[KP_CHI144]) * rcp2(rho);
                         const T divv = gvx.dx + gvy.dy;  // 12 div v
-                        const T br = T(P.kp[KP_B]) * rho;
+                        const T br = T(K.kp[KP_B]) * rho;
                         Coef2<T> kC;  // ax, ay divided by 12
                         kC.ax = fma2(q, gr.dx, T::bc(-1.f / 12.f) * gvx.c);
                         kC.ay = fma2(q, gr.dy, T::bc(-1.f / 12.f) * gvy.c);
-                        kC.cA = T(P.kp[KP_RCV12]) * divv * rcp2(T::bc(1.f) - br);
-                        kC.cB = T(P.kp[KP_ACV12]) * (divv * rho) * rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));
+                        kC.cA = T(K.kp[KP_RCV12]) * divv * rcp2(T::bc(1.f) - br);
+                        kC.cB = T(K.kp[KP_ACV12]) * (divv * rho) * rcp2(fma2(br, T::bc(2.f) - br, T::bc(1.f)));
                         float2* c = LB_SMC(sCO + (r & 3) * BD + lc);
                         c[0] = kC.ax.f2();
                         c[RING * BD] = kC.ay.f2();
                         c[2 * RING * BD] = kC.cA.f2();
                         c[3 * RING * BD] = kC.cB.f2();
                         const St2<T> ut = stencil2<T>(LB_SMP(sTH + ((r - 1) & 7) * W + s), LB_SMP(sTH + (r & 7) * W + s), LB_SMP(sTH + ((r + 1) & 7) * W + s), true);
-                        accC = rhs_K2(ut, kC, P);
+                        accC = rhs_K2(ut, kC, K);
                         u2 = fma2(T::bc(0.5f), accC, thr);
                         if constexpr (REC) {
                             if (S || (r >= ys && r < ye)) {  // weighted gradients, unscaled coefficients
@@ -563,7 +568,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                     T u3 = thr;
                     if (S || interior(r)) {
                         const St2<T> u = stencil2<T>(LB_SMP(sU2 + ((r - 1) & 3) * W + s), LB_SMP(sU2 + (r & 3) * W + s), LB_SMP(sU2 + ((r + 1) & 3) * W + s), true);
-                        const T h2 = rhs_K2(u, coef(r), P);
+                        const T h2 = rhs_K2(u, coef(r), K);
                         u3 = fma2(T::bc(0.5f), h2, thr);
                         acc1 = fma2(T::bc(2.f), h2, acc1);
                     }
@@ -582,7 +587,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                     T u4 = thr;
                     if (S || interior(r)) {
                         const St2<T> u = stencil2<T>(LB_SMP(sU3 + ((r - 1) & 3) * W + s), LB_SMP(sU3 + (r & 3) * W + s), LB_SMP(sU3 + ((r + 1) & 3) * W + s), true);
-                        const T h3 = rhs_K2(u, coef(r), P);
+                        const T h3 = rhs_K2(u, coef(r), K);
                         u4 = thr + h3;
                         acc2 = fma2(T::bc(2.f), h3, acc2);
                     }
@@ -608,7 +613,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
                         tnew = zero;
                     } else {
                         const St2<T> u = stencil2<T>(LB_SMP(sU4 + ((r - 1) & 3) * W + s), LB_SMP(sU4 + (r & 3) * W + s), LB_SMP(sU4 + ((r + 1) & 3) * W + s), true);
-                        const T h4 = rhs_K2(u, coef(r), P);
+                        const T h4 = rhs_K2(u, coef(r), K);
                         tnew = fma2(acc3 + h4, T::bc(1.f / 6.f), thr);
                     }
                 }
@@ -652,13 +657,13 @@ __device__ __forceinline__ void step_body(const StepParams& P, const int block, 
 
 template <int BD, int MINB, class T>
 __global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
-    step_body<BD, T>(P, blockIdx.x);
+    step_body<BD, T>(P, P, blockIdx.x);
 }
 
 // The forward intermediates of one step for the adjoint (paired FP32).
 template <int BD, int MINB>
 __global__ void __launch_bounds__(BD, MINB) lb_step_recompute(const StepParams P, const __grid_constant__ RecomputeOut R) {
-    step_body<BD, P2, true>(P, blockIdx.x, &R);
+    step_body<BD, P2, true>(P, P, blockIdx.x, &R);
 }
 
 // Many independent simulations in one launch (the boiling-curve batch): the
@@ -685,10 +690,39 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_batch(const StepParams* __re
     for (int k = threadIdx.x; k < NW; k += BD)
         reinterpret_cast<int*>(&sP)[k] = __ldg(reinterpret_cast<const int*>(table + inst) + k);
     __syncthreads();
-    step_body<BD, T>(sP, blockIdx.x - block_off[inst]);
+    step_body<BD, T>(sP, sP, blockIdx.x - block_off[inst]);
+}
+
+// The same with the model constants shared by all instances (K, in the
+// parameter bank); the table supplies each instance's buffers, sizes,
+// launch shape, wettability and rho_ave.
+template <int BD, int MINB, class T>
+__global__ void __launch_bounds__(BD, MINB) lb_step_batch_k(const StepParams K, const StepParams* __restrict__ table,
+                                                          const int* __restrict__ block_off, int n) {
+    __shared__ StepParams sP;
+    __shared__ int s_inst;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;  // largest i with block_off[i] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (block_off[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_inst = lo;
+    }
+    __syncthreads();
+    const int inst = s_inst;
+    constexpr int NW = (int)(sizeof(StepParams) / sizeof(int));
+    for (int k = threadIdx.x; k < NW; k += BD)
+        reinterpret_cast<int*>(&sP)[k] = __ldg(reinterpret_cast<const int*>(table + inst) + k);
+    __syncthreads();
+    step_body<BD, T>(sP, K, blockIdx.x - block_off[inst]);
 }
 
 namespace {
+
+// blocks per SM the shared-constant batch kernel is compiled for
+constexpr int BATCH_K_MINB64 = 8, BATCH_K_MINB128 = 4;
 
 template <int BD, int MINB, class T>
 struct DualKernel {
@@ -711,8 +745,20 @@ struct DualKernel {
     static cudaError_t occupancy_batch(int* n) {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lb_step_batch<BD, MINB, T>, BD, smem());
     }
+    static cudaError_t occupancy_batch_k(int* n) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lb_step_batch_k<BD, MINB, T>, BD, smem());
+    }
     static cudaError_t launch_batch(const StepParams* table, const int* off, int n, int nblocks, cudaStream_t st) {
         lb_step_batch<BD, MINB, T><<<nblocks, BD, smem(), st>>>(table, off, n);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare_batch_k() {
+        return cudaFuncSetAttribute(lb_step_batch_k<BD, MINB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem());
+    }
+    static cudaError_t launch_batch_k(const StepParams& K, const StepParams* table, const int* off, int n,
+                                      int nblocks, cudaStream_t st) {
+        lb_step_batch_k<BD, MINB, T><<<nblocks, BD, smem(), st>>>(K, table, off, n);
         return cudaGetLastError();
     }
 };
@@ -737,6 +783,8 @@ cudaError_t dual_prepare_t() {
 cudaError_t batch_prepare_t() {
     cudaError_t e = DualKernel<64, 8, P2>::prepare_batch();
     if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_batch();
+    if (e == cudaSuccess) e = DualKernel<64, BATCH_K_MINB64, P2>::prepare_batch_k();
+    if (e == cudaSuccess) e = DualKernel<128, BATCH_K_MINB128, P2>::prepare_batch_k();
     return e;
 }
 
@@ -804,12 +852,18 @@ bool batch_supported(int block_x) { return block_x == 64 || block_x == 128; }
 
 cudaError_t batch_prepare() { return batch_prepare_t(); }
 
-cudaError_t batch_occupancy(int block_x, int* n) {
+cudaError_t batch_occupancy(int block_x, bool shared_k, int* n) {
+    if (shared_k)
+        return block_x == 64 ? DualKernel<64, BATCH_K_MINB64, P2>::occupancy_batch_k(n)
+                             : DualKernel<128, BATCH_K_MINB128, P2>::occupancy_batch_k(n);
     return block_x == 64 ? DualKernel<64, 8, P2>::occupancy_batch(n) : DualKernel<128, 4, P2>::occupancy_batch(n);
 }
 
 cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,
-                         cudaStream_t st) {
+                         const StepParams* K, cudaStream_t st) {
+    if (K)
+        return block_x == 64 ? DualKernel<64, BATCH_K_MINB64, P2>::launch_batch_k(*K, table, block_off, n, nblocks, st)
+                             : DualKernel<128, BATCH_K_MINB128, P2>::launch_batch_k(*K, table, block_off, n, nblocks, st);
     return block_x == 64 ? DualKernel<64, 8, P2>::launch_batch(table, block_off, n, nblocks, st)
                          : DualKernel<128, 4, P2>::launch_batch(table, block_off, n, nblocks, st);
 }
