@@ -26,10 +26,13 @@ def run(case):
     return f, th
 
 
-def run_batch(shapes, block_x=64, seg=0):
+def run_batch(shapes, block_x=64, seg=0, vary=False):
     insts = []
     for i, (Lx, Ly, bc) in enumerate(shapes):
-        cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.4 * Ly, seed=20 + i)
+        # vary: instances differ in sigma, so the step reads every constant
+        # from its instance's record instead of shared launch parameters
+        cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.4 * Ly, seed=20 + i,
+                        sigma=1.2 + (0.05 * (i % 2) if vary else 0.0))
         insts.append({"cfg": cfg, "superheat": 0.01, "Gw": 0.05 * (i % 3)})
     b = lb.Batch(insts)
     b.set_launch(block_x, seg)
@@ -50,9 +53,10 @@ if __name__ == "__main__":
     res = {}
     for k, c in enumerate(cases):
         res[f"f{k}"], res[f"t{k}"] = run(c)
-    batches = [(((40, 30, 0), (57, 23, 1), (33, 48, 2)), 64, 0), (random_batch(), 128, 0),
-               (random_batch(12, 9), 64, 5)]
-    for j, (shapes, bx, seg) in enumerate(batches):
-        for k, (f, t) in enumerate(run_batch(shapes, bx, seg)):
+    batches = [(((40, 30, 0), (57, 23, 1), (33, 48, 2)), 64, 0, False), (random_batch(), 128, 0, False),
+               (random_batch(12, 9), 64, 5, False), (random_batch(13, 7), 64, 0, True),
+               (random_batch(14, 5), 128, 7, True)]
+    for j, (shapes, bx, seg, vary) in enumerate(batches):
+        for k, (f, t) in enumerate(run_batch(shapes, bx, seg, vary)):
             res[f"b{j}f{k}"], res[f"b{j}t{k}"] = f, t
     np.savez(sys.argv[2], **res)
