@@ -498,7 +498,8 @@ def run_ours(args):
     barrier()
     e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
     e2e = {"value": replicas.job_throughput(world, cells * e2e_steps, e2e_s * 1e3) / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": cfg.Lx * 4, "d2h_bytes_per_step": 76, "steps": e2e_steps,
+           # per step: the wall profile (Lx FP32) up, the 72-byte accumulator record down
+           "h2d_bytes_per_step": cfg.Lx * 4, "d2h_bytes_per_step": 72, "steps": e2e_steps,
            "api": "lb_set_wall_temperature + lb_step(1) + lb_heat_flux per step"}
 
     if rank == 0:
