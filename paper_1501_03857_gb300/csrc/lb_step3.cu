@@ -11,9 +11,10 @@
 // fluid row) holds for both halves, so the whole update runs on Blackwell's
 // paired FP32 instructions (__ffma2_rn / __fadd2_rn / __fmul2_rn: two FP32
 // operations per issue slot) with no repacking. Barriers and ring indexing
-// are shared by the two cells. Reciprocals and 1/sqrt use the MUFU
-// approximations (__fdividef, rsqrtf; <= 2 ulp); psi itself is correctly
-// rounded (__fsqrt_rn).
+// are shared by the two cells. Reciprocals and 1/sqrt are the special-
+// function unit's approximations (PTX rcp.approx, rsqrt.approx: one
+// instruction each, the values __fdividef(1, x) and rsqrtf give here, without
+// their range handling); psi itself is correctly rounded (__fsqrt_rn).
 //
 //   P  row L    : pull f (loads issued one iteration ahead), wall fill,
 //                 rho, psi(rho, T^t)                       (Eqs. 3, 6, 21)
@@ -69,10 +70,22 @@ __device__ __forceinline__ S2 operator*(S2 p, S2 q) { return S2(p.a * q.a, p.b *
 __device__ __forceinline__ S2 operator*(float s, S2 q) { return S2(s * q.a, s * q.b); }
 __device__ __forceinline__ S2 fma2(S2 p, S2 q, S2 r) { return S2(fmaf(p.a, q.a, r.a), fmaf(p.b, q.b, r.b)); }
 
+// the special-function unit's approximate reciprocal and 1/sqrt (PTX
+// rcp.approx / rsqrt.approx, flushing subnormals: none occur in the step)
+__device__ __forceinline__ float rcp_approx(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float a) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 template <class T>
-__device__ __forceinline__ T rcp2(T a) { return T(__fdividef(1.f, a.x()), __fdividef(1.f, a.y())); }
+__device__ __forceinline__ T rcp2(T a) { return T(rcp_approx(a.x()), rcp_approx(a.y())); }
 template <class T>
-__device__ __forceinline__ T rsqrt2(T a) { return T(rsqrtf(a.x()), rsqrtf(a.y())); }
+__device__ __forceinline__ T rsqrt2(T a) { return T(rsqrt_approx(a.x()), rsqrt_approx(a.y())); }
 
 // y = v mod n for pipeline rows (|v| is within a few rows of [0, n)).
 __device__ __forceinline__ int wrap_row(int v, int n) {
