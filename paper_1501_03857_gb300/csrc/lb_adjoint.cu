@@ -29,6 +29,20 @@ namespace lbgpu {
 
 namespace {
 
+// Reciprocal, 1/sqrt and sqrt (of a positive value) from single
+// special-function instructions (PTX rcp.approx, rsqrt.approx: relative
+// error about 1e-7, well inside the adjoint's FP32 budget).
+__device__ __forceinline__ float rcp_a(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_a(float a) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 __device__ constexpr int EXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int EYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
@@ -100,14 +114,14 @@ struct Eos {
 };
 
 __device__ __forceinline__ Eos eos(float rho, float T, const StepParams& P) {
-    const float sT = sqrtf(T);
+    const float rs = rsqrt_a(T), sT = T * rs;
     const float base = P.k0 - P.k1 * sT;  // 1 + kappa (1 - sqrt(T / Tc))
     const float phi = base * base;
-    const float dphi = P.k1k1 - P.k0k1 / sT;  // phi'(T)
+    const float dphi = P.k1k1 - P.k0k1 * rs;  // phi'(T)
     const float br = P.b * rho;
-    const float i1 = 1.f / (1.f - br);
+    const float i1 = rcp_a(1.f - br);
     const float D = 1.f + 2.f * br - br * br;
-    const float iD = 1.f / D;
+    const float iD = rcp_a(D);
     const float dD = 2.f * P.b - 2.f * P.b * br;  // dD/drho
     Eos e;
     e.p = rho * P.R * T * i1 - P.a * phi * rho * rho * iD;
@@ -250,11 +264,11 @@ __device__ __forceinline__ void rev_coef_cell(const StepParams& P, const AdjFiel
         A.lrho[i] = A.lvx[i] = A.lvy[i] = 0.f;
         return;
     }
-    const float rho = A.rho[i], irho = 1.f / rho;
+    const float rho = A.rho[i], irho = rcp_a(rho);
     const float lax = A.lax[i], lay = A.lay[i], lcA = A.lcA[i], lcB = A.lcB[i];
     const float br = P.b * rho;
-    const float i1 = 1.f / (1.f - br);
-    const float D = 1.f + 2.f * br - br * br, iD = 1.f / D;
+    const float i1 = rcp_a(1.f - br);
+    const float D = 1.f + 2.f * br - br * br, iD = rcp_a(D);
     const float dD = 2.f * P.b - 2.f * P.b * br;
     const float divv = A.divv[i];
     A.ldrx[i] = P.chi * lax * irho;
@@ -305,9 +319,9 @@ __global__ void rev_stage(const StepParams P, AdjFields A, const float* u, float
     float lax = 0.f, lay = 0.f, lcA = 0.f, lcB = 0.f;
     if (!wall && m != 0.f) {
         const float T = P.Ts + u[i];
-        const float sT = sqrtf(T);
-        const float dphi = P.k1k1 - P.k0k1 / sT;
-        const float d2phi = 0.5f * P.k0k1 / (sT * T);
+        const float rs = rsqrt_a(T);
+        const float dphi = P.k1k1 - P.k0k1 * rs;
+        const float d2phi = 0.5f * P.k0k1 * (rs * rs * rs);
         lu += (-(A.cA[i] - A.cB[i] * dphi) + T * A.cB[i] * d2phi) * m;
         float dx = 0.f, dy = 0.f;
 #pragma unroll
@@ -392,11 +406,12 @@ __global__ void rev_collide(const StepParams P, AdjFields A) {
     const float ne7 = m7 - rho * (vx * vx - vy * vy);
     const float ne8 = m8 - rho * vx * vy;
     const float psi2 = psi * psi;
-    const float R = psi2 > 0.f ? (Fmx * Fmx + Fmy * Fmy) / psi2 : 0.f;
+    const float ipsi2 = psi2 > 0.f ? rcp_a(psi2) : 0.f;
+    const float R = (Fmx * Fmx + Fmy * Fmy) * ipsi2;
     const float S7 = 2.f * (vx * Fx - vy * Fy), S8 = vx * Fy + vy * Fx;
     const float s = (rho - P.rho_v) * P.inv_drho;
     const float sfr = fminf(fmaxf(s, 0.f), 1.f);
-    const float snu = 1.f / (P.tau_v + P.dtau * sfr);
+    const float snu = rcp_a(P.tau_v + P.dtau * sfr);
     // dm = -Lambda (m - meq) + (I - Lambda/2) S, momentum rows dm_j = F
     const float lne1 = -P.s_e * ldm1, lS1 = (1.f - 0.5f * P.s_e) * ldm1;
     const float lne2 = -P.s_z * ldm2, lS2 = (1.f - 0.5f * P.s_z) * ldm2;
@@ -436,9 +451,9 @@ __global__ void rev_collide(const StepParams P, AdjFields A) {
     lFy += lvF * vy - 2.f * lS7 * vy + lS8 * vx;
     float lFmx = 0.f, lFmy = 0.f, lpsi = 0.f;
     if (psi2 > 0.f) {
-        lFmx += 2.f * Fmx * lR / psi2;
-        lFmy += 2.f * Fmy * lR / psi2;
-        lpsi += -2.f * R * lR / psi;
+        lFmx += 2.f * Fmx * lR * ipsi2;
+        lFmy += 2.f * Fmy * lR * ipsi2;
+        lpsi += -2.f * R * lR * psi * ipsi2;
     }
     // snu(rho)
     if (s > 0.f && s < 1.f) lrho += lsnu * (-snu * snu * P.dtau * P.inv_drho);
@@ -448,7 +463,7 @@ __global__ void rev_collide(const StepParams P, AdjFields A) {
     lvx += A.lvx[i] + lvx_c;
     lvy += A.lvy[i] + lvy_c;
     lrho += lr_c;
-    const float irho = 1.f / rho;
+    const float irho = rcp_a(rho);
     const float ljx = lvx * irho, ljy = lvy * irho;
     lFx += 0.5f * ljx;
     lFy += 0.5f * ljy;
@@ -514,7 +529,7 @@ __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
         const float rho = A.rho[i];
         const float T = P.Ts + A.theta[i];
         const Eos e = eos(rho, T, P);
-        const float k = lpsi / (P.G * psi);  // d psi = (dp - d rho / 3) / (G psi)
+        const float k = lpsi * rcp_a(P.G * psi);  // d psi = (dp - d rho / 3) / (G psi)
         lrho += k * (e.p_rho - 1.f / 3.f);
         lth += k * e.p_T;
     }

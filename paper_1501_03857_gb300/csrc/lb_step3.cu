@@ -681,11 +681,11 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_recompute(const StepParams P
 
 // Many independent simulations in one launch (the boiling-curve batch): the
 // blocks of instance i are [block_off[i], block_off[i+1]); each block copies
-// its instance's parameters to shared memory and runs the same step.
-template <int BD, int MINB, class T>
-__global__ void __launch_bounds__(BD, MINB) lb_step_batch(const StepParams* __restrict__ table,
-                                                        const int* __restrict__ block_off, int n) {
-    __shared__ StepParams sP;
+// its instance's parameter record to shared memory (sP) and returns the
+// block's index within its instance.
+template <int BD>
+__device__ __forceinline__ int batch_instance(const StepParams* __restrict__ table, const int* __restrict__ block_off,
+                                              int n, StepParams& sP) {
     __shared__ int s_inst;
     if (threadIdx.x == 0) {
         int lo = 0, hi = n - 1;  // largest i with block_off[i] <= blockIdx.x
@@ -703,33 +703,27 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_batch(const StepParams* __re
     for (int k = threadIdx.x; k < NW; k += BD)
         reinterpret_cast<int*>(&sP)[k] = __ldg(reinterpret_cast<const int*>(table + inst) + k);
     __syncthreads();
-    step_body<BD, T>(sP, sP, blockIdx.x - block_off[inst]);
+    return (int)blockIdx.x - block_off[inst];
 }
 
-// The same with the model constants shared by all instances (K, in the
+// The batch with every model constant from the instance's record.
+template <int BD, int MINB, class T>
+__global__ void __launch_bounds__(BD, MINB) lb_step_batch(const StepParams* __restrict__ table,
+                                                        const int* __restrict__ block_off, int n) {
+    __shared__ StepParams sP;
+    const int b = batch_instance<BD>(table, block_off, n, sP);
+    step_body<BD, T>(sP, sP, b);
+}
+
+// The batch with the model constants shared by all instances (K, in the
 // parameter bank); the table supplies each instance's buffers, sizes,
 // launch shape, wettability and rho_ave.
 template <int BD, int MINB, class T>
 __global__ void __launch_bounds__(BD, MINB) lb_step_batch_k(const StepParams K, const StepParams* __restrict__ table,
                                                           const int* __restrict__ block_off, int n) {
     __shared__ StepParams sP;
-    __shared__ int s_inst;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n - 1;  // largest i with block_off[i] <= blockIdx.x
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (block_off[mid] <= (int)blockIdx.x) lo = mid;
-            else hi = mid - 1;
-        }
-        s_inst = lo;
-    }
-    __syncthreads();
-    const int inst = s_inst;
-    constexpr int NW = (int)(sizeof(StepParams) / sizeof(int));
-    for (int k = threadIdx.x; k < NW; k += BD)
-        reinterpret_cast<int*>(&sP)[k] = __ldg(reinterpret_cast<const int*>(table + inst) + k);
-    __syncthreads();
-    step_body<BD, T>(sP, K, blockIdx.x - block_off[inst]);
+    const int b = batch_instance<BD>(table, block_off, n, sP);
+    step_body<BD, T>(sP, K, b);
 }
 
 namespace {
