@@ -490,7 +490,8 @@ __global__ void rev_collide(const StepParams P, AdjFields A) {
 
 // F_m neighbour sums (Eq. 7) and psi (Eq. 21) transposed, the heat flux
 // q(t) (in the window), rho = sum f; then the Zou-He fill transposed on the
-// wall rows. Writes the final lambda of the pulled populations and of theta.
+// wall rows and the pull-streaming transposed. Writes lambda of f*^n and of
+// theta^n.
 __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
@@ -567,19 +568,16 @@ __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
         lf[6] += lf[8];
         lf[4] = lf[7] = lf[8] = 0.f;
     }
-    for (int a = 0; a < 9; ++a) A.lf[a * pl + i] = lf[a];
-    A.lt_out[i] = lth;
-}
-
-// pull-streaming transposed: lambda_f*_a(y) = lambda_f_a(y + e_a)
-__global__ void rev_pull(const StepParams P, AdjFields A) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
+    // pull-streaming transposed (f_a(y) = f*_a(y - e_a)) as a scatter:
+    // lambda_f*_a(y - e_a) = lambda_f_a(y); a cell whose y + e_a lies beyond a
+    // wall receives nothing and is set to 0 here
+#pragma unroll
     for (int a = 0; a < 9; ++a) {
-        const int j = g.at(x, y, EXd[a], EYd[a]);
-        A.lf_out[a * P.plane + i] = j < 0 ? 0.f : A.lf[a * P.plane + j];
+        const int t = g.at(x, y, -EXd[a], -EYd[a]);
+        if (t >= 0) A.lf_out[a * pl + t] = lf[a];
+        if (g.at(x, y, EXd[a], EYd[a]) < 0) A.lf_out[a * pl + i] = 0.f;
     }
+    A.lt_out[i] = lth;
 }
 
 // Domains of at least this many cells recompute with the fused step (one
@@ -739,7 +737,6 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
     }
     rev_collide<<<grid, blk, 0, st>>>(P, A);
     rev_psi<<<grid, blk, 0, st>>>(P, A, lq);
-    rev_pull<<<grid, blk, 0, st>>>(P, A);
     return cudaGetLastError();
 }
 
