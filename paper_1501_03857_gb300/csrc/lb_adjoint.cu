@@ -82,7 +82,6 @@ struct AdjFields {
     // forward intermediates of the step being reversed
     const float* fstar;  // f*^n, 9 planes
     const float* theta;  // theta^n
-    float* f;            // pulled, wall-filled populations, 9 planes
     float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *Fx, *Fy, *vx, *vy;
     float *drx, *dry, *divv, *ax, *ay, *cA, *cB;
     float *u2, *u3, *u4;
@@ -132,18 +131,11 @@ __device__ __forceinline__ Eos eos(float rho, float T, const StepParams& P) {
     return e;
 }
 
-// ---- forward recompute by field kernels ---------------------------------------
-//
-// For small domains, where the fused step's 5-row pipeline halo and its
-// sequential march dominate (a 256 x 256 step takes ~20 us in it), the
-// intermediates are recomputed by these one-thread-per-cell kernels, which
-// follow the fused step's formulas.
-
-__global__ void fwd_pull(const StepParams P, AdjFields A) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    float f[9];
+// Pulled and wall-filled populations of cell (x, y) from f* (Eq. 3, Zou-He
+// on the wall rows), as the step computes them.
+__device__ __forceinline__ void pull_cell(const StepParams& P, const float* __restrict__ fstar, int x, int y,
+                                          float (&f)[9]) {
+#pragma unroll
     for (int a = 0; a < 9; ++a) {
         int yy = y - EYd[a];
         bool ok = true;
@@ -156,14 +148,26 @@ __global__ void fwd_pull(const StepParams P, AdjFields A) {
         int xx = x - EXd[a];
         if (xx < 0) xx += P.Lx;
         if (xx >= P.Lx) xx -= P.Lx;
-        f[a] = ok ? A.fstar[a * P.plane + yy * P.pitch + xx] : 0.f;
+        f[a] = ok ? fstar[a * P.plane + yy * P.pitch + xx] : 0.f;
     }
     wall_fill(P, y, f);
+}
+
+// ---- forward recompute by field kernels ---------------------------------------
+//
+// For small domains, where the fused step's 5-row pipeline halo and its
+// sequential march dominate (a 256 x 256 step takes ~20 us in it), the
+// intermediates are recomputed by these one-thread-per-cell kernels, which
+// follow the fused step's formulas.
+
+__global__ void fwd_pull(const StepParams P, AdjFields A) {
+    int x, y, i;
+    if (!cell(P, x, y, i)) return;
+    const Grid g = grid_of(P);
+    float f[9];
+    pull_cell(P, A.fstar, x, y, f);
     float rho = 0.f;
-    for (int a = 0; a < 9; ++a) {
-        rho += f[a];
-        A.f[a * P.plane + i] = f[a];
-    }
+    for (int a = 0; a < 9; ++a) rho += f[a];
     A.rho[i] = rho;
     A.jx[i] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     A.jy[i] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
@@ -381,10 +385,8 @@ __global__ void rev_collide(const StepParams P, AdjFields A) {
     }
     const int pl = P.plane;
     float f[9], lo[9];
-    for (int a = 0; a < 9; ++a) {
-        f[a] = A.f[a * pl + i];
-        lo[a] = A.lf_in[a * pl + i];
-    }
+    pull_cell(P, A.fstar, x, y, f);  // pulled again from f*: cheaper than a stored copy
+    for (int a = 0; a < 9; ++a) lo[a] = A.lf_in[a * pl + i];
     const float rho = A.rho[i], vx = A.vx[i], vy = A.vy[i];
     const float Fx = A.Fx[i], Fy = A.Fy[i], Fmx = A.Fmx[i], Fmy = A.Fmy[i], psi = A.psi[i];
     // lambda_dm = diag(1/9, 1/36, ...) M lambda_f*
@@ -586,9 +588,9 @@ __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
 // launches take ~15 us, the fused step ~20 us).
 constexpr size_t kFusedRecomputeCells = 512 * 512;
 
-// Work-buffer layout: 54 field planes, then dJ/d theta_b [pitch doubles], the
+// Work-buffer layout: 45 field planes, then dJ/d theta_b [pitch doubles], the
 // per-column dJ/dG_w parts [pitch doubles] and dJ/dG_w.
-constexpr int kPlanes = 54;
+constexpr int kPlanes = 45;
 
 AdjFields fields_at(const StepParams& P, void* work) {
     float* w = (float*)work;
@@ -604,7 +606,6 @@ AdjFields fields_at(const StepParams& P, void* work) {
     A.theta = nullptr;
     A.lf_in = A.lt_in = nullptr;
     A.lf_out = A.lt_out = nullptr;
-    A.f = next(9);
     A.rho = next(1);
     A.psi = next(1);
     A.jx = next(1);
@@ -713,8 +714,8 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
     Q.th_in = theta;
     Q.f_out = nullptr;
     Q.th_out = nullptr;
-    const RecomputeOut R{A.f,   A.rho, A.psi,  A.jx, A.jy, A.Fmx, A.Fmy, A.Fx, A.Fy, A.vx, A.vy,
-                         A.drx, A.dry, A.divv, A.ax, A.ay, A.cA,  A.cB,  A.u2, A.u3, A.u4};
+    const RecomputeOut R{A.rho, A.psi, A.jx, A.jy, A.Fmx, A.Fmy, A.Fx, A.Fy, A.vx, A.vy,
+                         A.drx, A.dry, A.divv, A.ax, A.ay, A.cA, A.cB, A.u2, A.u3, A.u4};
     if ((size_t)P.Lx * P.Ly >= kFusedRecomputeCells) {
         cudaError_t e = dual_recompute(Q, R, L, st);
         if (e != cudaSuccess) return e;

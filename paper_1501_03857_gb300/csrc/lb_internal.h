@@ -36,14 +36,12 @@ cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaS
 
 // The forward intermediates of one step that the adjoint's reverse kernels
 // read (lb_adjoint.cu), written by the dual-strip step in its recompute mode
-// (lb_step3.cu): the pulled and wall-filled populations (9 planes, plane
-// stride StepParams::plane) and the pitched [Ly][pitch] planes below. The
-// gradients drx, dry and div v carry the stencil weights; ax, ay, cA, cB are
-// the coefficients of K(T), Eq. 18 (0 on the wall rows); u2-u4 the RK stage
-// inputs (theta on the wall rows). The step itself (f*, theta of the next
-// level, heat flux) is not written in this mode.
+// (lb_step3.cu) into pitched [Ly][pitch] planes. The gradients drx, dry and
+// div v carry the stencil weights; ax, ay, cA, cB are the coefficients of
+// K(T), Eq. 18 (0 on the wall rows); u2-u4 the RK stage inputs (theta on the
+// wall rows). The step itself (f*, theta of the next level, heat flux) is
+// not written in this mode.
 struct RecomputeOut {
-    float* f;
     float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *Fx, *Fy, *vx, *vy;
     float *drx, *dry, *divv, *ax, *ay, *cA, *cB, *u2, *u3, *u4;
 };

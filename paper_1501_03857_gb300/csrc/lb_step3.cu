@@ -404,8 +404,6 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
             *LB_SMP(sTH + (L & 7) * W + s) = tc.f2();
             if constexpr (REC) {
                 if (L >= ys && L < ye) {
-#pragma unroll
-                    for (int a = 0; a < 9; ++a) put(R->f + (size_t)a * P.plane, y, fc[a]);
                     put(R->rho, y, rhoN);
                     put(R->psi, y, psiN);
                 }
