@@ -666,8 +666,17 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
 #undef LB_SMP
 #undef LB_SMC
 
+// Registers a thread of the single-domain step may use, by block size: 12
+// warps per SM (6 blocks of 64, 3 of 128). A cap given this way (150
+// registers used at 64 and 128 threads) measured 6 % faster on 4096^2 and
+// 8 % on 8192^2 than the same occupancy requested through __launch_bounds__'
+// minimum blocks (148 registers), and 4 % faster than a cap of 144 or 136.
+// 256 threads keep 2 blocks per SM through the minimum-blocks bound (118
+// registers; a bare cap of 128 spills).
+constexpr int dual_regs(int bd) { return bd == 64 ? 152 : bd == 128 ? 160 : 128; }
+
 template <int BD, int MINB, class T>
-__global__ void __launch_bounds__(BD, MINB) lb_step_dual(const StepParams P) {
+__global__ void __launch_bounds__(BD, BD == 256 ? 2 : 1) __maxnreg__(dual_regs(BD)) lb_step_dual(const StepParams P) {
     step_body<BD, T>(P, P, blockIdx.x);
 }
 
@@ -770,12 +779,13 @@ struct DualKernel {
 
 // the instantiations a launch can pick: (block size, paired FP32 or scalar).
 // The single-domain step is compiled for 12 warps per SM (6 blocks of 64 or
-// 3 of 128, up to 170 registers a thread; it takes about 148), not 16 (8 x 64
-// or 4 x 128 at 128 registers): within 128 registers the compiler spends ~50
-// more instructions per cell on copies and recomputation, which costs more
-// than the four warps gain (4096^2: 0.385 ms at 6 x 64 and 0.391 ms at 3 x 128
-// against 0.420 ms at 4 x 128). The batched step keeps 128 registers: with
-// its parameters in shared memory it ran 7 % slower with the larger budget.
+// 3 of 128 with ~150 registers a thread, dual_regs), not 16 (8 x 64 or 4 x
+// 128 at 128 registers): within 128 registers the compiler spends ~50 more
+// instructions per cell on copies and recomputation, which costs more than
+// the four warps gain (4096^2: 0.385 ms at 6 x 64 and 0.391 ms at 3 x 128
+// against 0.420 ms at 4 x 128, before the cap of dual_regs). The batched
+// step keeps 128 registers: with its parameters in shared memory it ran 7 %
+// slower with the larger budget.
 
 template <class T>
 cudaError_t dual_prepare_t() {
