@@ -666,18 +666,28 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
 #undef LB_SMP
 #undef LB_SMC
 
-// Registers a thread of the single-domain step may use, by block size: 12
-// warps per SM (6 blocks of 64, 3 of 128). A cap given this way (150
-// registers used at 64 and 128 threads) measured 6 % faster on 4096^2 and
-// 8 % on 8192^2 than the same occupancy requested through __launch_bounds__'
-// minimum blocks (148 registers), and 4 % faster than a cap of 144 or 136.
-// 256 threads keep 2 blocks per SM through the minimum-blocks bound (118
-// registers; a bare cap of 128 spills).
-constexpr int dual_regs(int bd) { return bd == 64 ? 152 : bd == 128 ? 160 : 128; }
+// The single-domain step at 64 and 128 threads gives the compiler only its
+// block size (154 registers: 12 warps per SM, 6 blocks of 64 or 3 of 128).
+// This measured 5 % faster on 4096^2 and 8 % on 8192^2 than the same
+// occupancy requested through __launch_bounds__' minimum blocks (148
+// registers, a different schedule), and faster than register caps of 144
+// (4 %) or 136 (6 %). 256 threads keep 2 blocks per SM through the
+// minimum-blocks bound (lb_step_dual_lb: 118 registers).
+template <int BD, int MINB, class T>
+__global__ void __launch_bounds__(BD) lb_step_dual(const StepParams P) {
+    step_body<BD, T>(P, P, blockIdx.x);
+}
 
 template <int BD, int MINB, class T>
-__global__ void __launch_bounds__(BD, BD == 256 ? 2 : 1) __maxnreg__(dual_regs(BD)) lb_step_dual(const StepParams P) {
+__global__ void __launch_bounds__(BD, MINB) lb_step_dual_lb(const StepParams P) {
     step_body<BD, T>(P, P, blockIdx.x);
+}
+
+// the step kernel of a block size
+template <int BD, int MINB, class T>
+constexpr auto dual_kernel() {
+    if constexpr (BD == 256) return lb_step_dual_lb<BD, MINB, T>;
+    else return lb_step_dual<BD, MINB, T>;
 }
 
 // The forward intermediates of one step for the adjoint (paired FP32).
@@ -742,14 +752,14 @@ template <int BD, int MINB, class T>
 struct DualKernel {
     static size_t smem() { return sizeof(float2) * ((size_t)SM_ROWS * (BD + 2) + 4 * RING * BD); }
     static cudaError_t prepare() {
-        return cudaFuncSetAttribute(lb_step_dual<BD, MINB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(dual_kernel<BD, MINB, T>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem());
     }
     static cudaError_t occupancy(int* n) {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lb_step_dual<BD, MINB, T>, BD, smem());
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, dual_kernel<BD, MINB, T>(), BD, smem());
     }
     static cudaError_t launch(const StepParams& P, int nblocks, cudaStream_t st) {
-        lb_step_dual<BD, MINB, T><<<nblocks, BD, smem(), st>>>(P);
+        dual_kernel<BD, MINB, T>()<<<nblocks, BD, smem(), st>>>(P);
         return cudaGetLastError();
     }
     static cudaError_t prepare_batch() {
@@ -778,15 +788,15 @@ struct DualKernel {
 };
 
 // the instantiations a launch can pick: (block size, paired FP32 or scalar).
-// The single-domain step is compiled for 12 warps per SM (6 blocks of 64 or
-// 3 of 128 with ~150 registers a thread, dual_regs), not 16 (8 x 64 or 4 x
-// 128 at 128 registers): within 128 registers the compiler spends ~50 more
-// instructions per cell on copies and recomputation, which costs more than
-// the four warps gain (4096^2: 0.385 ms at 6 x 64 and 0.391 ms at 3 x 128
-// against 0.420 ms at 4 x 128, before the cap of dual_regs). The batched
-// step keeps 128 registers: with its parameters in shared memory it ran 7 %
-// slower with the larger budget.
-
+// The single-domain step runs 12 warps per SM (6 blocks of 64 or 3 of 128
+// with ~154 registers a thread), not 16 (8 x 64 or 4 x 128 at 128
+// registers): within 128 registers the compiler spends ~50 more instructions
+// per cell on copies and recomputation, which costs more than the four warps
+// gain. For the single-domain kernels at 64 and 128 threads MINB names the
+// intended blocks per SM only (the occupancy query sizes the grid;
+// lb_step_dual gives the compiler its block size alone). The
+// batched step keeps 128 registers: with its parameters in shared memory it
+// ran 7 % slower with the larger budget.
 template <class T>
 cudaError_t dual_prepare_t() {
     cudaError_t e = DualKernel<64, 6, T>::prepare();
