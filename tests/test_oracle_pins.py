@@ -568,6 +568,45 @@ def test_autograd_adjoint_matches_central_differences(coex):
     assert abs(float(fd) - float(ggw)) < 1e-5 * abs(float(ggw)) + 1e-12
 
 
+def test_adjoint_is_transpose_of_tangent_linear_model(coex):
+    """Dot-product test of the whole-state adjoint: for the map Phi taking
+    (f*, theta) through n steps, <w, J u> from the tangent-linear model
+    (forward-mode derivatives) equals <J^T w, u> from the reverse sweep, for
+    random u and w, on a heated pool with interface, adhesion and gravity."""
+    import torch.autograd.forward_ad as fwAD
+    Tc, rv, rl = coex
+    Lx, Ly, n = 12, 10, 3
+    rho0 = inputs.pool_density(Lx, Ly, rl, rv, 5, noise_amp=1e-2, seed=3)
+    P = make(Lx, Ly, rho0, coex, Gw=0.05, superheat=0.02)
+    f0, th0 = O.initial_state(torch.tensor(rho0, dtype=F64), P)
+    for _ in range(5):
+        f0, th0, _ = O.step(f0, th0, P)
+
+    def phi(f, th):
+        for _ in range(n):
+            f, th, _ = O.step(f, th, P)
+        return f, th
+
+    g = torch.Generator().manual_seed(7)
+    uf, ut, wf, wt = (torch.randn(t.shape, generator=g, dtype=F64) for t in (f0, th0, f0, th0))
+    with fwAD.dual_level():
+        fo, to = phi(fwAD.make_dual(f0, uf), fwAD.make_dual(th0, ut))
+        jf, jt = fwAD.unpack_dual(fo).tangent, fwAD.unpack_dual(to).tangent
+    lhs = float((wf * jf).sum() + (wt * jt).sum())
+    fr, tr = f0.clone().requires_grad_(), th0.clone().requires_grad_()
+    fo, to = phi(fr, tr)
+    gf, gt = torch.autograd.grad((wf * fo).sum() + (wt * to).sum(), (fr, tr))
+    rhs = float((gf * uf).sum() + (gt * ut).sum())
+    assert abs(lhs) > 1e-3
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    # the tangent itself against a central difference of Phi along u
+    h = 1e-6
+    fp, tp = phi(f0 + h * uf, th0 + h * ut)
+    fm, tm = phi(f0 - h * uf, th0 - h * ut)
+    fd = float((wf * (fp - fm)).sum() + (wt * (tp - tm)).sum()) / (2 * h)
+    assert abs(fd - lhs) <= 1e-6 * abs(lhs)
+
+
 # --------------------------------------------------------------------------
 # Seeded input generator
 # --------------------------------------------------------------------------
