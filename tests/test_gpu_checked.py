@@ -23,7 +23,9 @@ CASES = [(8, 6, 0, 0, 0.0, 0, 5, 64, 0), (33, 17, 0, 0, 0.08, 0, 40, 64, 6), (33
          (517, 41, 1, 0, 0.065, 0, 10, 256, 7), (300, 70, 0, 0, 0.105, 0, 10, 128, 0),
          # the smallest grids the library accepts: one column, three rows
          (1, 3, 0, 0, 0.0, 0, 6, 64, 0), (1, 9, 2, 0, 0.0, 0, 6, 64, 2), (2, 3, 1, 0, 0.05, 0, 6, 128, 1),
-         (5, 4, 0, 1, 0.0, 0, 6, 64, 1), (3, 5, 2, 0, 0.0, 1, 6, 256, 0)]
+         (5, 4, 0, 1, 0.0, 0, 6, 64, 1), (3, 5, 2, 0, 0.0, 1, 6, 256, 0),
+         # wide enough for interior strips, whose columns do not wrap
+         (700, 30, 2, 0, 0.0, 0, 10, 64, 0), (1000, 20, 0, 0, 0.05, 0, 10, 128, 0), (1500, 12, 1, 0, 0.0, 0, 6, 256, 5)]
 
 
 def random_cases(n=40, seed=7):
