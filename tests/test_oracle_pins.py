@@ -568,6 +568,7 @@ def test_autograd_adjoint_matches_central_differences(coex):
     assert abs(float(fd) - float(ggw)) < 1e-5 * abs(float(ggw)) + 1e-12
 
 
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")  # torch scripts a forward-mode helper internally
 def test_adjoint_is_transpose_of_tangent_linear_model(coex):
     """Dot-product test of the whole-state adjoint: for the map Phi taking
     (f*, theta) through n steps, <w, J u> from the tangent-linear model
