@@ -1,0 +1,174 @@
+"""Planted mistakes: each plausible slip in the FP64 oracle must make at
+least one of its pins fail.
+
+Every case replaces one oracle function (or constant) by a copy with a single
+deliberate error, on the CPU, and runs the pins that should notice it. A
+pin that still passes under a mutation would not be pinning that part of the
+oracle. The pins are the functions of test_oracle_pins.py, called directly.
+"""
+
+import math
+
+import pytest
+import torch
+
+import oracle as O
+import oracle.lbm as L
+import test_oracle_pins as pins
+
+F64 = torch.float64
+
+
+@pytest.fixture(scope="module")
+def coex():
+    Tc = O.critical_temperature(pins.A_PAPER, pins.B_PAPER, 1.0)
+    rv, rl = O.maxwell_coexistence(pins.A_PAPER, pins.B_PAPER, 1.0, 0.344, 0.86 * Tc)
+    return Tc, rv, rl
+
+
+def _patch(monkeypatch, name, value):
+    """Replace `name` in the oracle module (seen by the oracle's own calls)
+    and in the package namespace (seen by the pins)."""
+    monkeypatch.setattr(L, name, value)
+    if hasattr(O, name):
+        monkeypatch.setattr(O, name, value)
+
+
+# ---- the mutations ---------------------------------------------------------
+
+_rhs = L.temperature_rhs
+_eq = L.equilibrium_moments
+_fm = L.forcing_moments
+_ads = L.adhesion_force
+_fill = L.wall_fill
+
+
+def rhs_advection_sign(T, fl, P):
+    """+v.grad T instead of -v.grad T in Eq. 18."""
+    dTx, dTy = L.grad_iso(T)
+    return _rhs(T, fl, P) + 2.0 * (fl.vx * dTx + fl.vy * dTy)
+
+
+def rhs_no_conductivity_gradient(T, fl, P):
+    """div(lambda grad T) without the grad lambda . grad T part."""
+    dTx, dTy = L.grad_iso(T)
+    return _rhs(T, fl, P) - P.cv_chi * (fl.drx * dTx + fl.dry * dTy) / (fl.rho * P.cv)
+
+
+def rhs_source_sign(T, fl, P):
+    """+T/(rho c_v) (dp/dT) div v instead of minus."""
+    dpdT = L.pr_dp_dT(fl.rho, T, P.a, P.b, P.R, P.omega, P.Tc)
+    return _rhs(T, fl, P) + 2.0 * T / (fl.rho * P.cv) * dpdT * fl.div_v
+
+
+def eq_energy_row(rho, vx, vy):
+    """e^eq = rho (-2 + 2 v^2) instead of rho (-2 + 3 v^2) (Eq. 5)."""
+    m = _eq(rho, vx, vy).clone()
+    m[1] = m[1] - rho * (vx * vx + vy * vy)
+    return m
+
+
+def forcing_pxy_row(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
+    """The p_xy row of S (Eq. 8) doubled."""
+    S = _fm(vx, vy, Fx, Fy, Fmx, Fmy, psi, P).clone()
+    S[8] = 2.0 * S[8]
+    return S
+
+
+def collide_forcing_factor(ff, P):
+    """(I - Lambda) S instead of (I - Lambda/2) S in Eq. 2."""
+    M, Minv = L.transform_matrix(), L.inverse_transform_matrix()
+    m = torch.einsum('ab,byx->ayx', M, ff.f)
+    meq = L.equilibrium_moments(ff.rho, ff.vx, ff.vy)
+    S = L.forcing_moments(ff.vx, ff.vy, ff.Fx, ff.Fy, ff.Fmx, ff.Fmy, ff.psi, P)
+    lam = L.relaxation_rates(ff.rho, P)
+    return torch.einsum('ab,byx->ayx', Minv, m - lam * (m - meq) + (1.0 - lam) * S)
+
+
+def rk4_stage3(theta, rho, vx, vy, P):
+    """The third RK stage taken from T + h2 instead of T + h2/2 (Eq. 19)."""
+    bot, top = L._row_masks(P)
+    fluid = (~(bot | top)).to(F64)
+    fl = L.frozen_flow(rho, vx, vy)
+    T = P.Ts + theta
+    h1 = fluid * L.temperature_rhs(T, fl, P)
+    h2 = fluid * L.temperature_rhs(T + 0.5 * h1, fl, P)
+    h3 = fluid * L.temperature_rhs(T + h2, fl, P)
+    h4 = fluid * L.temperature_rhs(T + h3, fl, P)
+    return theta + (h1 + 2.0 * h2 + 2.0 * h3 + h4) / 6.0
+
+
+def wall_fill_sign(f, fpost, P):
+    """Zou-He at the bottom wall with f5 = f7 + (f1 - f3)/2 (sign slip)."""
+    out = _fill(f, fpost, P).clone()
+    bot, _ = L._row_masks(P)
+    d = 0.5 * (out[1] - out[3])
+    out[5] = torch.where(bot, out[7] + d, out[5])
+    return out
+
+
+def adhesion_sign(psi, P):
+    """F_ads with the opposite sign (Eq. 22)."""
+    fx, fy = _ads(psi, P)
+    return -fx, -fy
+
+
+FORCE_W_WRONG = (0.0,) + (1.0 / 3.0,) * 4 + (1.0 / 6.0,) * 4  # diagonal 1/6 instead of 1/12
+
+# name -> (what is replaced, replacement, pins expected to fail)
+MUTATIONS = {
+    "advection sign": ("temperature_rhs", rhs_advection_sign, ["manufactured"]),
+    "dropped conductivity gradient": ("temperature_rhs", rhs_no_conductivity_gradient, ["manufactured"]),
+    "source-term sign": ("temperature_rhs", rhs_source_sign, ["manufactured"]),
+    "equilibrium energy row": ("equilibrium_moments", eq_energy_row, ["equilibrium"]),
+    "forcing p_xy row": ("forcing_moments", forcing_pxy_row, ["guo"]),
+    "forcing factor": ("collide", collide_forcing_factor, ["guo"]),
+    "RK4 stage": ("rk4_temperature", rk4_stage3, ["rk4"]),
+    "Zou-He sign": ("wall_fill", wall_fill_sign, ["zou_he"]),
+    "adhesion sign": ("adhesion_force", adhesion_sign, ["adhesion"]),
+    "force weight": ("FORCE_W", FORCE_W_WRONG, ["taylor"]),
+}
+
+PINS = {
+    "manufactured": lambda c: pins.test_temperature_rhs_manufactured_solution(c),
+    "equilibrium": lambda c: pins.test_equilibrium_moments_are_moments_of_textbook_equilibrium(),
+    "guo": lambda c: pins.test_collision_reduces_to_bgk_with_guo_forcing(1.3),
+    "rk4": lambda c: pins.test_rk4_fourier_mode_closed_form(c),
+    "zou_he": lambda c: pins.test_zou_he_wall_fill_solves_its_conditions(),
+    "adhesion": lambda c: pins.test_adhesion_force_bruteforce(),
+    "taylor": lambda c: pins.test_interaction_force_taylor_limit(),
+}
+
+
+@pytest.mark.parametrize("pin", sorted(PINS))
+def test_pin_passes_on_the_oracle(coex, pin):
+    PINS[pin](coex)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(coex, monkeypatch, name):
+    target, replacement, expected = MUTATIONS[name]
+    _patch(monkeypatch, target, replacement)
+    for pin in expected:
+        with pytest.raises(AssertionError):
+            PINS[pin](coex)
+
+
+def test_mutations_change_a_whole_step(coex, monkeypatch):
+    """Every mutation also changes what one full oracle step computes on a
+    heated pool with an interface (so none of them is a no-op)."""
+    Tc, rv, rl = coex
+    from paper_1501_03857_gb300 import inputs
+    Lx, Ly = 10, 12
+    rho0 = inputs.pool_density(Lx, Ly, rl, rv, 6, noise_amp=1e-2, seed=5)
+    P = pins.make(Lx, Ly, rho0, coex, Gw=0.05, superheat=0.02)
+    f0, th0 = O.initial_state(torch.tensor(rho0, dtype=F64), P)
+    f0, th0, _ = O.step(f0, th0, P)
+    ref_f, ref_t, _ = O.step(f0, th0, P)
+    for name, (target, replacement, _) in MUTATIONS.items():
+        with monkeypatch.context() as m:
+            m.setattr(L, target, replacement)
+            f, t, _ = L.step(f0, th0, P)
+        diff = max(float((f - ref_f).abs().max()), float((t - ref_t).abs().max()))
+        assert diff > 1e-12, name
+    assert math.isfinite(float(ref_f.sum()))
