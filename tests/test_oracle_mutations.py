@@ -113,21 +113,89 @@ def adhesion_sign(psi, P):
     return -fx, -fy
 
 
-FORCE_W_WRONG = (0.0,) + (1.0 / 3.0,) * 4 + (1.0 / 6.0,) * 4  # diagonal 1/6 instead of 1/12
+def stream_push(fpost, P):
+    """Streaming with e_a reversed (a push read as a pull, Eq. 3)."""
+    return torch.stack([torch.roll(fpost[a], shifts=(-L.EY[a], -L.EX[a]), dims=(0, 1)) for a in range(9)])
 
-# name -> (what is replaced, replacement, pins expected to fail)
+
+def psi_half(rho, T, P):
+    """psi without the factor 2 under the square root."""
+    p = L.pr_pressure(rho, T, P.a, P.b, P.R, P.omega, P.Tc)
+    arg = (p - rho * L.CS2) / P.G
+    return torch.sqrt(torch.clamp(arg, min=0.0)), arg < 0
+
+
+def tau_nu_no_half(rho, P):
+    """tau = nu / c_s^2 without the + 1/2."""
+    tl, tv = P.nu_l / L.CS2, P.nu_v / L.CS2
+    s = torch.clamp((rho - P.rho_v) / (P.rho_l - P.rho_v), 0.0, 1.0)
+    return tv + (tl - tv) * s
+
+
+def flux_first_order(theta, rho, P):
+    """q_w with the first-order wall difference T_1 - T_0."""
+    qw = -P.cv_chi * rho[0] * (theta[1] - theta[0])
+    return qw, qw.mean()
+
+
+_dphi = L.pr_dphi_dT
+
+
+def dphi_sign(T, Tc, omega):
+    """d phi / dT with the opposite sign."""
+    return -_dphi(T, Tc, omega)
+
+
+def buoyancy_sign(rho, P):
+    """F_b = -(rho - rho_ave) g: light fluid pushed down."""
+    return torch.zeros_like(rho), (rho - P.rho_ave) * P.g
+
+
+def area_half_log(v1, v2, T, a, b, R, omega, Tc):
+    """The attractive part of the isotherm's primitive with 1/sqrt(2) b in
+    place of 1/(2 sqrt(2) b)."""
+    ph = L.pr_phi(T, Tc, omega)
+    s2 = math.sqrt(2.0)
+
+    def prim(v):
+        return R * T * math.log(v - b) - a * ph / (s2 * b) * math.log((v + b - s2 * b) / (v + b + s2 * b))
+
+    return prim(v2) - prim(v1)
+
+
+FORCE_W_WRONG = (0.0,) + (1.0 / 3.0,) * 4 + (1.0 / 6.0,) * 4  # diagonal 1/6 instead of 1/12
+STENCIL_W_WRONG = (4.0 / 9.0,) + (1.0 / 9.0,) * 4 + (1.0 / 18.0,) * 4  # diagonal 1/18 instead of 1/36
+
+# name -> (what is replaced, replacement, pins expected to fail, changes a step)
 MUTATIONS = {
-    "advection sign": ("temperature_rhs", rhs_advection_sign, ["manufactured"]),
-    "dropped conductivity gradient": ("temperature_rhs", rhs_no_conductivity_gradient, ["manufactured"]),
-    "source-term sign": ("temperature_rhs", rhs_source_sign, ["manufactured"]),
-    "equilibrium energy row": ("equilibrium_moments", eq_energy_row, ["equilibrium"]),
-    "forcing p_xy row": ("forcing_moments", forcing_pxy_row, ["guo"]),
-    "forcing factor": ("collide", collide_forcing_factor, ["guo"]),
-    "RK4 stage": ("rk4_temperature", rk4_stage3, ["rk4"]),
-    "Zou-He sign": ("wall_fill", wall_fill_sign, ["zou_he"]),
-    "adhesion sign": ("adhesion_force", adhesion_sign, ["adhesion"]),
-    "force weight": ("FORCE_W", FORCE_W_WRONG, ["taylor"]),
+    "advection sign": ("temperature_rhs", rhs_advection_sign, ["manufactured"], True),
+    "dropped conductivity gradient": ("temperature_rhs", rhs_no_conductivity_gradient, ["manufactured"], True),
+    "source-term sign": ("temperature_rhs", rhs_source_sign, ["manufactured"], True),
+    "equilibrium energy row": ("equilibrium_moments", eq_energy_row, ["equilibrium"], True),
+    "forcing p_xy row": ("forcing_moments", forcing_pxy_row, ["guo"], True),
+    "forcing factor": ("collide", collide_forcing_factor, ["guo"], True),
+    "RK4 stage": ("rk4_temperature", rk4_stage3, ["rk4"], True),
+    "Zou-He sign": ("wall_fill", wall_fill_sign, ["zou_he"], True),
+    "adhesion sign": ("adhesion_force", adhesion_sign, ["adhesion"], True),
+    "force weight": ("FORCE_W", FORCE_W_WRONG, ["taylor"], True),
+    "streaming direction": ("stream_pull", stream_push, ["stream"], True),
+    "stencil weight": ("STENCIL_W", STENCIL_W_WRONG, ["quadratics", "symbol"], True),
+    "psi factor": ("pseudopotential", psi_half, ["bulk_pressure"], True),
+    "relaxation time": ("tau_nu", tau_nu_no_half, ["tau_nu"], True),
+    "wall derivative order": ("wall_heat_flux", flux_first_order, ["wall_flux"], True),
+    "d phi / dT sign": ("pr_dphi_dT", dphi_sign, ["dp_dT"], True),
+    "buoyancy sign": ("buoyancy", buoyancy_sign, ["buoyancy"], True),
+    "equal-area primitive": ("_pr_area", area_half_log, ["maxwell"], False),
 }
+
+
+def _maxwell_pins(_):
+    """The coexistence pins on densities recomputed under the mutation."""
+    Tc = O.critical_temperature(pins.A_PAPER, pins.B_PAPER, 1.0)
+    c = (Tc,) + tuple(O.maxwell_coexistence(pins.A_PAPER, pins.B_PAPER, 1.0, 0.344, 0.86 * Tc))
+    pins.test_maxwell_equal_area_by_quadrature(c)
+    pins.test_maxwell_matches_paper_printed_values(c)
+
 
 PINS = {
     "manufactured": lambda c: pins.test_temperature_rhs_manufactured_solution(c),
@@ -137,6 +205,15 @@ PINS = {
     "zou_he": lambda c: pins.test_zou_he_wall_fill_solves_its_conditions(),
     "adhesion": lambda c: pins.test_adhesion_force_bruteforce(),
     "taylor": lambda c: pins.test_interaction_force_taylor_limit(),
+    "stream": lambda c: pins.test_stream_pull_bruteforce(),
+    "quadratics": lambda c: pins.test_stencils_exact_on_quadratics(),
+    "symbol": lambda c: pins.test_laplacian_fourier_symbol(),
+    "bulk_pressure": lambda c: pins.test_pseudopotential_bulk_pressure(c),
+    "tau_nu": lambda c: pins.test_tau_nu_endpoints(c),
+    "wall_flux": lambda c: pins.test_wall_flux_exact_on_quadratic(c),
+    "dp_dT": lambda c: pins.test_dp_dT_against_central_difference(c),
+    "buoyancy": lambda c: pins.test_buoyancy_direction(),
+    "maxwell": _maxwell_pins,
 }
 
 
@@ -147,7 +224,7 @@ def test_pin_passes_on_the_oracle(coex, pin):
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(coex, monkeypatch, name):
-    target, replacement, expected = MUTATIONS[name]
+    target, replacement, expected, _ = MUTATIONS[name]
     _patch(monkeypatch, target, replacement)
     for pin in expected:
         with pytest.raises(AssertionError):
@@ -155,8 +232,9 @@ def test_planted_mistake_is_caught(coex, monkeypatch, name):
 
 
 def test_mutations_change_a_whole_step(coex, monkeypatch):
-    """Every mutation also changes what one full oracle step computes on a
-    heated pool with an interface (so none of them is a no-op)."""
+    """Every mutation of the step's arithmetic also changes what one full
+    oracle step computes (populations, temperature or the wall flux) on a
+    heated pool with an interface, so none of them is a no-op."""
     Tc, rv, rl = coex
     from paper_1501_03857_gb300 import inputs
     Lx, Ly = 10, 12
@@ -164,11 +242,13 @@ def test_mutations_change_a_whole_step(coex, monkeypatch):
     P = pins.make(Lx, Ly, rho0, coex, Gw=0.05, superheat=0.02)
     f0, th0 = O.initial_state(torch.tensor(rho0, dtype=F64), P)
     f0, th0, _ = O.step(f0, th0, P)
-    ref_f, ref_t, _ = O.step(f0, th0, P)
-    for name, (target, replacement, _) in MUTATIONS.items():
+    ref_f, ref_t, ref = O.step(f0, th0, P)
+    for name, (target, replacement, _, in_step) in MUTATIONS.items():
+        if not in_step:
+            continue
         with monkeypatch.context() as m:
             m.setattr(L, target, replacement)
-            f, t, _ = L.step(f0, th0, P)
-        diff = max(float((f - ref_f).abs().max()), float((t - ref_t).abs().max()))
+            f, t, info = L.step(f0, th0, P)
+        diff = max(float((f - ref_f).abs().max()), float((t - ref_t).abs().max()), abs(float(info.q - ref.q)))
         assert diff > 1e-12, name
     assert math.isfinite(float(ref_f.sum()))
