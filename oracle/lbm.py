@@ -42,6 +42,15 @@ notes):
 * Wall heat flux q_w = -lambda dT/dy at y = 0 with the second-order one-sided
   difference (-3 T0 + 4 T1 - T2)/2 (Sec. 3.2 defines q_w, not its stencil),
   evaluated from (theta^t, rho^t) inside step t.
+
+Parity unpinned: the sigma term in the zeta row of S (Eq. 8, in
+:func:`forcing_moments`). No pin isolates it. Leaving it out moves the
+coexistence densities of a relaxed flat interface by 0.16 %, inside the
+tolerance of the coexistence pin, because the zeta moment does not enter
+the macroscopic equations at second order. It is taken as Eq. 8 prints
+it. Every other term of the step is pinned (tests/test_oracle_pins.py;
+tests/test_oracle_mutations.py plants a slip in each and checks that a pin
+fails).
 """
 
 from __future__ import annotations

@@ -163,6 +163,18 @@ def area_half_log(v1, v2, T, a, b, R, omega, Tc):
     return prim(v2) - prim(v1)
 
 
+def forcing_sigma_tau(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
+    """The sigma term of Eq. 8 over tau_e, tau_zeta instead of tau - 1/2."""
+    S = _fm(vx, vy, Fx, Fy, Fmx, Fmy, psi, P).clone()
+    psi2 = psi * psi
+    ratio = torch.where(psi2 > 0, (Fmx * Fmx + Fmy * Fmy) / torch.where(psi2 > 0, psi2, torch.ones_like(psi2)),
+                        torch.zeros_like(psi2))
+    te, tz = 1.0 / P.s_e, 1.0 / P.s_z
+    S[1] = S[1] + P.sigma * ratio * (1.0 / te - 1.0 / (te - 0.5))
+    S[2] = S[2] - P.sigma * ratio * (1.0 / tz - 1.0 / (tz - 0.5))
+    return S
+
+
 FORCE_W_WRONG = (0.0,) + (1.0 / 3.0,) * 4 + (1.0 / 6.0,) * 4  # diagonal 1/6 instead of 1/12
 STENCIL_W_WRONG = (4.0 / 9.0,) + (1.0 / 9.0,) * 4 + (1.0 / 18.0,) * 4  # diagonal 1/18 instead of 1/36
 
@@ -186,6 +198,7 @@ MUTATIONS = {
     "d phi / dT sign": ("pr_dphi_dT", dphi_sign, ["dp_dT"], True),
     "buoyancy sign": ("buoyancy", buoyancy_sign, ["buoyancy"], True),
     "equal-area primitive": ("_pr_area", area_half_log, ["maxwell"], False),
+    "sigma-term denominator": ("forcing_moments", forcing_sigma_tau, ["coexistence"], True),
 }
 
 
@@ -214,6 +227,7 @@ PINS = {
     "dp_dT": lambda c: pins.test_dp_dT_against_central_difference(c),
     "buoyancy": lambda c: pins.test_buoyancy_direction(),
     "maxwell": _maxwell_pins,
+    "coexistence": lambda c: pins.test_flat_interface_coexistence_matches_maxwell(c),
 }
 
 
