@@ -45,6 +45,8 @@ def tune_simulation(sim, candidates: Optional[Iterable[Tuple[int, int]]] = None,
             if best is None or ms < best[2]:
                 best = (bx, seg, ms)
         sim.load(blob)
+        if best is None:
+            raise RuntimeError("the simulation accepted none of the candidate launch shapes")
         _CACHE[key] = best
     bx, seg, ms = _CACHE[key]
     sim.set_launch(bx, seg)
@@ -70,6 +72,8 @@ def tune_batch(batch, candidates: Optional[Iterable[Tuple[int, int]]] = None, st
                 best = (bx, seg, ms)
         for i, (f, th) in enumerate(saved):
             batch.set_state(i, f, th)
+        if best is None:
+            raise RuntimeError("the batch accepted none of the candidate launch shapes")
         _CACHE[key] = best
     bx, seg, ms = _CACHE[key]
     batch.set_launch(bx, seg)
