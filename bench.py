@@ -95,6 +95,12 @@ class ClockSampler:
         time.sleep(0.1)
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
+        return self.summarise(out, t0, t1)
+
+    @staticmethod
+    def summarise(out: str, t0: float, t1: float):
+        """Median SM clock, the largest maximum clock and the active throttle
+        reasons over the samples inside [t0, t1] (25 ms slack)."""
         rows = []
         for line in out.strip().splitlines():
             parts = [p.strip() for p in line.split(",")]
