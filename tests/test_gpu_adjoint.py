@@ -1,7 +1,7 @@
 """The hand-written discrete adjoint against the FP64 oracle: gradients of
 the window-averaged wall heat flux with respect to the wall temperature
 profile and G_w, compared with the oracle's autograd adjoint and with FP64
-central differences of the oracle (the benchmark spec's bound: 1e-3 relative)."""
+central differences of the oracle (required agreement: 1e-3 relative)."""
 
 import numpy as np
 import pytest

@@ -4,8 +4,8 @@ oracle on the same seeded inputs.
 Tolerances (normalised max-norm error, max|gpu - oracle| / max|oracle| per
 field) follow from FP32 storage and arithmetic: one step from an FP32 state
 carries a few ulp (2^-24 ~ 6e-8) of rounding per operation through about a
-hundred dependent operations, so 2e-6; after 200 steps the benchmark spec's bound
-1e-5 applies.
+hundred dependent operations, so 2e-6; after 200 steps the required bound
+is 1e-5.
 """
 
 import math
