@@ -37,6 +37,24 @@ def test_library_exports_every_declared_symbol(lb):
         assert hasattr(lb.lib, n), n
 
 
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_is_plain_c_and_cxx(lang, std, tmp_path):
+    """include/lb.h compiles on its own as strict C99 and as C++17, and a C
+    translation unit can take the address of every declared entry point
+    (the signatures use plain pointers and sizes only)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use." + ("c" if lang == "c" else "cpp"))
+    refs = "\n".join(f"    (void)&{n};" for n in declared_symbols())
+    src.write_text('#include "lb.h"\nvoid touch(void) {\n' + refs + "\n}\n")
+    r = subprocess.run([cc, "-fsyntax-only", std, "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_checked_build_exports_every_declared_symbol(lb):
     """The bounds-checked build (-DLB_CHECKED) exposes the same C ABI."""
     import ctypes
