@@ -55,6 +55,52 @@ def test_header_is_plain_c_and_cxx(lang, std, tmp_path):
     assert r.returncode == 0, r.stderr
 
 
+def test_plain_c_program_links_and_calls_host_entry_points(lb, tmp_path):
+    """A C program (no Python, no PyTorch) links liblbboil.so and calls the
+    host-only entry points: T_c, the coexistence densities and the
+    workspace size agree with the oracle and the layout rule; a bad grid
+    returns LB_E_INVAL with a message."""
+    import shutil
+    import subprocess
+    from paper_1501_03857_gb300 import build
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "host.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "lb.h"
+int main(void) {
+    lb_eos e = {3.0 / 49.0, 2.0 / 21.0, 1.0, 0.344, -1.0, 1.2};
+    double Tc, rv, rl;
+    size_t n;
+    lb_grid g = {100, 100, LB_BC_WALLS, 0, 0, 0};
+    lb_grid bad = {0, 100, LB_BC_WALLS, 0, 0, 0};
+    if (lb_critical_temperature(&e, &Tc) != LB_OK) return 1;
+    if (lb_coexistence(&e, 0.86 * Tc, &rv, &rl) != LB_OK) return 2;
+    if (lb_workspace_bytes(&g, &n) != LB_OK) return 3;
+    if (lb_workspace_bytes(&bad, &n) != LB_E_INVAL || lb_last_error()[0] == 0) return 4;
+    lb_workspace_bytes(&g, &n);
+    printf("%.17g %.17g %.17g %zu\n", Tc, rv, rl, n);
+    return 0;
+}
+""")
+    exe = tmp_path / "host"
+    libdir = os.path.dirname(build.LIB)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-o", str(exe), "-L", libdir, "-llbboil", "-Wl,-rpath," + libdir],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    Tc, rv, rl, nbytes = r.stdout.split()
+    Tc_o = O.critical_temperature(3 / 49, 2 / 21, 1.0)
+    rv_o, rl_o = O.maxwell_coexistence(3 / 49, 2 / 21, 1.0, 0.344, 0.86 * Tc_o)
+    assert abs(float(Tc) - Tc_o) < 1e-14 * Tc_o
+    assert abs(float(rv) - rv_o) < 1e-9 * rv_o and abs(float(rl) - rl_o) < 1e-9 * rl_o
+    assert int(nbytes) == lb.workspace_bytes(lb.Config(Lx=100, Ly=100))
+
+
 def test_checked_build_exports_every_declared_symbol(lb):
     """The bounds-checked build (-DLB_CHECKED) exposes the same C ABI."""
     import ctypes
