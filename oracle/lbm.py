@@ -43,14 +43,12 @@ notes):
   difference (-3 T0 + 4 T1 - T2)/2 (Sec. 3.2 defines q_w, not its stencil),
   evaluated from (theta^t, rho^t) inside step t.
 
-Parity unpinned: the sigma term in the zeta row of S (Eq. 8, in
-:func:`forcing_moments`). No pin isolates it. Leaving it out moves the
-coexistence densities of a relaxed flat interface by 0.16 %, inside the
-tolerance of the coexistence pin, because the zeta moment does not enter
-the macroscopic equations at second order. It is taken as Eq. 8 prints
-it. Every other term of the step is pinned (tests/test_oracle_pins.py;
-tests/test_oracle_mutations.py plants a slip in each and checks that a pin
-fails).
+Every term of the step is pinned (tests/test_oracle_pins.py), including the
+sigma term of Eq. 8 in both rows it enters: the e row through the relaxed
+flat interface's coexistence densities, and the zeta row through its fixed
+relation to the e row (its share of m*_zeta is -s_zeta/s_e times the e row's
+share, for any rates). tests/test_oracle_mutations.py plants a slip in each
+part and checks that a pin fails.
 """
 
 from __future__ import annotations

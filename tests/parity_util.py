@@ -31,6 +31,13 @@ def norm_err(got, ref, scale=None):
     return float(np.abs(got - ref).max() / (scale if scale > 0 else 1.0))
 
 
+def rel_err(got, ref):
+    """max over elements of |got - ref| / |ref| (for strictly positive fields)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float((np.abs(got - ref) / np.abs(ref)).max())
+
+
 def theta_err(got, ref, superheat):
     """Temperature error relative to the temperature scale of the problem,
     max(max |theta_ref|, wall superheat): where theta is still ~0 (only the

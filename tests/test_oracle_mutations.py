@@ -175,6 +175,35 @@ def forcing_sigma_tau(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
     return S
 
 
+def _sigma_ratio(Fmx, Fmy, psi):
+    psi2 = psi * psi
+    return torch.where(psi2 > 0, (Fmx * Fmx + Fmy * Fmy) / torch.where(psi2 > 0, psi2, torch.ones_like(psi2)),
+                       torch.zeros_like(psi2))
+
+
+def forcing_zeta_sigma_dropped(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
+    """The zeta row of S (Eq. 8) without its sigma term."""
+    S = _fm(vx, vy, Fx, Fy, Fmx, Fmy, psi, P).clone()
+    S[2] = S[2] + P.sigma * _sigma_ratio(Fmx, Fmy, psi) / (1.0 / P.s_z - 0.5)
+    return S
+
+
+def forcing_zeta_sigma_sign(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
+    """The sigma term of the zeta row of S (Eq. 8) with a plus sign."""
+    S = _fm(vx, vy, Fx, Fy, Fmx, Fmy, psi, P).clone()
+    S[2] = S[2] + 2.0 * P.sigma * _sigma_ratio(Fmx, Fmy, psi) / (1.0 / P.s_z - 0.5)
+    return S
+
+
+def forcing_zeta_sigma_tau_e(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
+    """The sigma term of the zeta row of S (Eq. 8) over tau_e - 1/2 instead of
+    tau_zeta - 1/2."""
+    S = _fm(vx, vy, Fx, Fy, Fmx, Fmy, psi, P).clone()
+    r = P.sigma * _sigma_ratio(Fmx, Fmy, psi)
+    S[2] = S[2] + r / (1.0 / P.s_z - 0.5) - r / (1.0 / P.s_e - 0.5)
+    return S
+
+
 FORCE_W_WRONG = (0.0,) + (1.0 / 3.0,) * 4 + (1.0 / 6.0,) * 4  # diagonal 1/6 instead of 1/12
 STENCIL_W_WRONG = (4.0 / 9.0,) + (1.0 / 9.0,) * 4 + (1.0 / 18.0,) * 4  # diagonal 1/18 instead of 1/36
 
@@ -199,7 +228,18 @@ MUTATIONS = {
     "buoyancy sign": ("buoyancy", buoyancy_sign, ["buoyancy"], True),
     "equal-area primitive": ("_pr_area", area_half_log, ["maxwell"], False),
     "sigma-term denominator": ("forcing_moments", forcing_sigma_tau, ["coexistence"], True),
+    "zeta sigma term dropped": ("forcing_moments", forcing_zeta_sigma_dropped, ["sigma_rows"], True),
+    "zeta sigma term sign": ("forcing_moments", forcing_zeta_sigma_sign, ["sigma_rows"], True),
+    # identical to the oracle at the default s_e = s_zeta, so not a change of
+    # the default step; the pin runs it at unequal rates
+    "zeta sigma term rate": ("forcing_moments", forcing_zeta_sigma_tau_e, ["sigma_rows"], False),
 }
+
+
+def _sigma_rows(_):
+    """The e/zeta sigma-term pin at unequal and at equal rates."""
+    pins.test_sigma_term_of_e_and_zeta_rows(0.8, 1.25)
+    pins.test_sigma_term_of_e_and_zeta_rows(0.8, 0.8)
 
 
 def _maxwell_pins(_):
@@ -228,6 +268,7 @@ PINS = {
     "buoyancy": lambda c: pins.test_buoyancy_direction(),
     "maxwell": _maxwell_pins,
     "coexistence": lambda c: pins.test_flat_interface_coexistence_matches_maxwell(c),
+    "sigma_rows": _sigma_rows,
 }
 
 

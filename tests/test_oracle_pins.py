@@ -189,6 +189,45 @@ def test_collision_reduces_to_bgk_with_guo_forcing(tau):
     assert torch.allclose(got, want, atol=1e-14, rtol=1e-12)
 
 
+def sigma_term_split(s_e, s_z, sigmas=(0.0, 1.2, 2.5)):
+    """Post-collision moments m* = M f* of one oracle collision on a heated
+    pool with an interface (F_m, psi non-zero), for each sigma of Eq. 8."""
+    Lx, Ly = 12, 10
+    Tc = O.critical_temperature(A_PAPER, B_PAPER, 1.0)
+    rv, rl = O.maxwell_coexistence(A_PAPER, B_PAPER, 1.0, 0.344, 0.86 * Tc)
+    rho0, fpost, th0 = inputs.random_state(Lx, Ly, rl, rv, 5, seed=21)
+    out = {}
+    for sigma in sigmas:
+        P = O.Params(Lx=Lx, Ly=Ly, bc_y=O.BC_PERIODIC, s_e=s_e, s_z=s_z, sigma=sigma)
+        P.finalize(rho0=rho0, rho_v=rv, rho_l=rl)
+        ff = O.flow_fields(torch.tensor(fpost, dtype=F64), torch.tensor(th0, dtype=F64), P)
+        out[sigma] = torch.einsum('ab,byx->ayx', O.transform_matrix(), O.collide(ff, P))
+    return out
+
+
+@pytest.mark.parametrize("s_e,s_z", [(0.8, 0.8), (0.8, 1.25), (1.4, 0.7)])
+def test_sigma_term_of_e_and_zeta_rows(s_e, s_z):
+    """The sigma term of Eq. 8 enters the e row as +sigma X/(tau_e - 1/2) and
+    the zeta row as -sigma X/(tau_zeta - 1/2) (X = |F_m|^2/psi^2); Eq. 2 then
+    scales each by (1 - s/2), and (1 - s/2)/(1/s - 1/2) = s. So the sigma
+    part of m*_e is sigma X s_e and that of m*_zeta is -sigma X s_zeta:
+    dm*_e/s_e + dm*_zeta/s_zeta = 0 for any rates, which with tau_e =
+    tau_zeta says m*_e + m*_zeta is independent of sigma. Both parts are
+    linear in sigma, they are not zero where F_m is not, and sigma touches
+    no other moment (it only changes the bulk and fourth-order energy
+    moments, not mass or momentum)."""
+    m = sigma_term_split(s_e, s_z)
+    d1 = {s: m[s] - m[0.0] for s in (1.2, 2.5)}
+    de, dz = d1[1.2][1], d1[1.2][2]
+    assert float(de.abs().max()) > 1e-3 * float(m[0.0][1].abs().max())
+    assert torch.allclose(de / s_e + dz / s_z, torch.zeros_like(de), atol=1e-13)
+    assert torch.allclose(d1[2.5][1:3], d1[1.2][1:3] * (2.5 / 1.2), atol=1e-13, rtol=1e-11)
+    others = [k for k in range(9) if k not in (1, 2)]
+    assert torch.allclose(d1[1.2][others], torch.zeros_like(d1[1.2][others]), atol=1e-13)
+    if s_e == s_z:
+        assert torch.allclose(m[1.2][1] + m[1.2][2], m[0.0][1] + m[0.0][2], atol=1e-13)
+
+
 def test_stream_pull_bruteforce():
     Ly, Lx = 4, 5
     fpost = torch.arange(9 * Ly * Lx, dtype=F64).view(9, Ly, Lx)
