@@ -123,14 +123,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "window_s": t1 - t0}
 
 
-def cpu_baseline(seconds: float = 12.0, rows: int = 48):
-    """The FP64 oracle on a band of `rows` rows (full 4096 width, the bottom
-    wall band) of the workload, for about `seconds` of CPU time."""
+# rows of the workload's bottom band (full 4096 width) that the FP64 oracle
+# steps: the same band for the cpu_baseline block and the reference arm
+CPU_BAND_ROWS = 32
+
+
+def oracle_band(rows: int = CPU_BAND_ROWS):
+    """The workload's bottom band of `rows` rows for the FP64 oracle: its
+    parameters (rho_ave of the whole domain) and initial state."""
     import torch
     import oracle as O
     from paper_1501_03857_gb300 import inputs
-    cores = os.cpu_count() or 1
-    torch.set_num_threads(cores)
     a, b, R, om = 3 / 49, 2 / 21, 1.0, 0.344
     Tc = O.critical_temperature(a, b, R)
     rv, rl = O.maxwell_coexistence(a, b, R, om, 0.86 * Tc)
@@ -140,6 +143,19 @@ def cpu_baseline(seconds: float = 12.0, rows: int = 48):
     P.finalize(rho0=rho0, superheat=0.1 * Tc, rho_v=rv, rho_l=rl)
     P.rho_ave = float(np.asarray(rho_full, np.float64).mean())
     f, th = O.initial_state(rho0, P)
+    return P, f, th
+
+
+def cpu_baseline(seconds: float = 12.0, rows: int = CPU_BAND_ROWS):
+    """The FP64 oracle on a band of `rows` rows (full 4096 width, the bottom
+    wall band) of the workload, for about `seconds` of CPU time."""
+    import torch
+    import oracle as O
+    from paper_1501_03857_gb300 import inputs
+    cores = os.cpu_count() or 1
+    torch.set_num_threads(cores)
+    a, b, R, om = 3 / 49, 2 / 21, 1.0, 0.344
+    P, f, th = oracle_band(rows)
     f, th, _ = O.step(f, th, P)  # warm-up
     n, t0 = 0, time.perf_counter()
     while True:
@@ -222,15 +238,19 @@ def wettability_calibration(torch, lb):
             "curve_Gw": [float(g) for g in targets], "ms": ev[0].elapsed_time(ev[1])}
 
 
-def batched_curve(torch, lb, gw_of_angle, steps_batch=64, steps_seq=32):
+def batched_curve(torch, lb, gw_of_angle, steps_batch=64, steps_seq=32, dist=None):
     """48 boiling-curve instances (uneven 200-400 x 200-600 domains, superheat
     0.02-0.4 Tc, contact angles 40-150 deg through the calibrated G_w of
     gw_of_angle) in one launch per step vs. the same instances stepped one
-    after another through the plain path."""
-    from paper_1501_03857_gb300 import inputs, tune
-    pts = inputs.boiling_curve_batch(48, seed=3)
+    after another through the plain path. With N ranks (dist) the instances
+    are dealt out to the ranks (replicas.shard): each rank times its share,
+    and the job's times are the slowest rank's."""
+    from paper_1501_03857_gb300 import inputs, replicas, tune
+    rank, world = (dist.get_rank(), dist.get_world_size()) if dist is not None else (0, 1)
+    pts = replicas.shard(list(enumerate(inputs.boiling_curve_batch(48, seed=3))), rank, world)
+    n_all = 48
     insts = []
-    for i, d in enumerate(pts):
+    for i, d in pts:
         cfg = lb.Config(Lx=d["Lx"], Ly=d["Ly"], bc_y=lb.BC_WALLS, pool_height=0.4 * d["Ly"], seed=100 + i)
         Tc = lb.critical_temperature(cfg)
         insts.append({"cfg": cfg, "superheat": d["superheat_frac"] * Tc, "Gw": gw_of_angle[d["wet_index"]]})
@@ -260,11 +280,15 @@ def batched_curve(torch, lb, gw_of_angle, steps_batch=64, steps_seq=32):
         torch.cuda.synchronize()
         t_seq += ev[0].elapsed_time(ev[1]) / steps_seq
         sim.close()
-    sph = lambda t: len(insts) * 3600.0 / (CURVE_STEPS * t * 1e-3)
-    return {"instances": len(insts), "cells": cells, "steps_per_sim": CURVE_STEPS,
+    t_b = replicas.max_over_ranks(t_b, dist, device="cuda")
+    t_seq = replicas.max_over_ranks(t_seq, dist, device="cuda")
+    cells = int(round(replicas.max_over_ranks(cells, dist, device="cuda")))  # the largest share
+    sph = lambda t: n_all * 3600.0 / (CURVE_STEPS * t * 1e-3)
+    return {"instances": n_all, "ranks": world, "instances_per_rank_max": len(insts),
+            "cells_largest_share": cells, "steps_per_sim": CURVE_STEPS,
             "ms_per_step_batched": t_b, "ms_per_step_sequential": t_seq,
             "sims_per_hour_batched": sph(t_b), "sims_per_hour_sequential": sph(t_seq),
-            "speedup": t_seq / t_b, "mlups_batched": cells / (t_b * 1e3),
+            "speedup": t_seq / t_b, "mlups_batched": cells / (t_b * 1e3) * world,
             "launch": {"block_x": bx, "seg_rows": seg, "blocks": info["blocks"],
                        "graph": "32-step captured graphs"}}
 
@@ -331,16 +355,17 @@ CURVE_SUPERHEATS = (0.008, 0.01, 0.0137, 0.0165, 0.019, 0.021, 0.023, 0.025, 0.0
 CURVE_SEEDS = (1, 2, 3)  # seeds of the pool's initial noise averaged per case
 
 
-def paper_experiments(torch):
+def paper_experiments(torch, dist=None):
     """The boiling curves of Sec. 3.2-3.3 on the paper's 600 x 150 pool (12
     superheats x G_w 0, 0.065, 0.105 x 3 seeds of the initial noise in one
     batch; 20000 steps at the base superheat, switch, 5000 settling, 15000
     averaged; case statistics are seed-ensemble means) and Fig. 3's top-wall
-    pressure; compact summary and wall time."""
-    from paper_1501_03857_gb300 import experiments as E
+    pressure; compact summary and wall time. With N ranks (dist) the curve's
+    runs are dealt out to the ranks and gathered back."""
+    from paper_1501_03857_gb300 import experiments as E, replicas
     t0 = time.perf_counter()
-    r = E.boiling_curve(CURVE_SUPERHEATS, Gw_values=(0.0, 0.065, 0.105), seeds=CURVE_SEEDS)
-    t_curve = time.perf_counter() - t0
+    r = E.boiling_curve(CURVE_SUPERHEATS, Gw_values=(0.0, 0.065, 0.105), seeds=CURVE_SEEDS, dist=dist)
+    t_curve = replicas.max_over_ranks(time.perf_counter() - t0, dist, device="cuda")
     curves = {}
     for gw, c in r["curves"].items():
         grp = [x for x in r["cases"] if x["Gw"] == gw]
@@ -351,7 +376,7 @@ def paper_experiments(torch):
     t_top = time.perf_counter() - t0
     steps = r["t_switch"] + r["t_settle"] + r["t_avg"]
     sims = len(r["cases"]) * len(r["seeds"])
-    return {"grid": "600x150", "cases": len(r["cases"]), "seeds": r["seeds"], "simulations": sims,
+    return {"grid": "600x150", "cases": len(r["cases"]), "seeds": r["seeds"], "simulations": sims, "ranks": r["ranks"],
             "steps_per_case": steps, "s_curves": t_curve, "sims_per_hour": sims * 3600.0 / t_curve, "curves": curves,
             "top_wall_pressure": {str(k): v["p_top"] for k, v in tp["cases"].items()}, "s_top_wall_pressure": t_top}
 
@@ -410,16 +435,8 @@ def run_reference(args):
     from paper_1501_03857_gb300 import inputs
     cores = os.cpu_count() or 1
     torch.set_num_threads(cores)
-    rows = 32
-    a, b, R, om = 3 / 49, 2 / 21, 1.0, 0.344
-    Tc = O.critical_temperature(a, b, R)
-    rv, rl = O.maxwell_coexistence(a, b, R, om, 0.86 * Tc)
-    rho_full = inputs.bubble_density(L, L, rl, rv, n_bubbles=256, r_min=20.0, r_max=60.0, seed=4)
-    rho0 = torch.tensor(rho_full[:rows], dtype=torch.float64)
-    P = O.Params(Lx=L, Ly=rows, a=a, b=b, R=R, omega=om)
-    P.finalize(rho0=rho0, superheat=0.1 * Tc, rho_v=rv, rho_l=rl)
-    P.rho_ave = float(np.asarray(rho_full, np.float64).mean())
-    f, th = O.initial_state(rho0, P)
+    rows = CPU_BAND_ROWS
+    P, f, th = oracle_band(rows)
     for _ in range(args.warmup):
         f, th, _ = O.step(f, th, P)
     t0 = time.perf_counter()
@@ -533,15 +550,20 @@ def run_ours(args):
                              "kernel": "lb_step_dual (paired-FP32 dual-strip fused step)", "bytes_per_lu": BYTES_PER_LU,
                              "avg_kernel_ms": avg_ms},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks}
-        if not args.no_batched:
-            cal = wettability_calibration(torch, lb)
-            line["batched"] = batched_curve(torch, lb, cal["curve_Gw"])
-            line["batched"]["wettability"] = cal
+    # the boiling-curve blocks on every rank: their instances are dealt out
+    # to the ranks (the natural replica unit) and gathered back on rank 0
+    extras = {}
+    if not args.no_batched:
+        cal = wettability_calibration(torch, lb)
+        extras["batched"] = batched_curve(torch, lb, cal["curve_Gw"], dist=dist)
+        extras["batched"]["wettability"] = cal
+    if not args.no_experiments:
+        extras["experiments"] = paper_experiments(torch, dist)
+    if rank == 0:
+        line.update(extras)
         if not args.no_adjoint:
             line["adjoint"] = adjoint_window(torch, lb)
             line["adjoint"]["large"] = adjoint_roofline(torch, lb)
-        if not args.no_experiments:
-            line["experiments"] = paper_experiments(torch)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -143,22 +143,11 @@ def ensemble(runs: list) -> dict:
             "film_fraction": float(np.mean(film)), "none_fraction": float(np.mean(none))}
 
 
-def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, base_superheat: float = 0.0137,
-                  t_switch: int = 20000, t_settle: int = 5000, t_avg: int = 15000, sample_every: int = 500,
-                  seeds=None, stream=None) -> dict:
-    """The boiling curve(s) for every (Delta T, G_w) pair in one batch;
-    returns per case q_bar, q_std, h_c, the wall coverage (mean, min, max),
-    the bubble count (mean, max) and the regime, and per G_w the superheat
-    and value of the largest mean heat flux (chf), the nucleate_limit
-    superheat and the superheat and value of the largest h_c. `seeds`
-    (default: cfg.seed alone) runs every case once per seed of the pool's
-    initial noise; the case statistics are then ensemble averages (see
-    `ensemble`), with q_sem the standard error of q_bar over the seeds."""
-    cfg = cfg or paper_config()
-    seeds = [cfg.seed] if seeds is None else [int(s) for s in seeds]
-    rv, rl = lb.coexistence(cfg)
-    cases = [(float(dT), float(gw)) for gw in Gw_values for dT in superheats]
-    runs = [(c, sd) for c in cases for sd in seeds]
+def run_cases(runs, cfg: lb.Config, rho_v: float, rho_l: float, base_superheat: float, t_switch: int,
+              t_settle: int, t_avg: int, sample_every: int, stream=None) -> list:
+    """Run the ((Delta T, G_w), seed) pairs `runs` as the instances of one
+    batch (the protocol of boiling_curve) and return, per run, q_mean, q_std
+    and the sampled wall coverage and bubble counts."""
     insts = [{"cfg": replace(cfg, seed=sd), "Gw": gw, "superheat": (base_superheat if dT > base_superheat else dT)}
              for (dT, gw), sd in runs]
     batch = lb.Batch(insts, stream=stream)
@@ -178,16 +167,49 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
             done += n
             for i in range(len(runs)):
                 rho = batch.fields(i, ("rho",))["rho"]
-                cov[i].append(wall_coverage(rho, rl, rv))
-                nbub[i].append(len(diagnostics.bubbles(rho, rl, rv)))
+                cov[i].append(wall_coverage(rho, rho_l, rho_v))
+                nbub[i].append(len(diagnostics.bubbles(rho, rho_l, rho_v)))
         hf = batch.heat_flux()
     finally:
         batch.close()
+    return [{"q_mean": float(hf["q_mean"][i]), "q_std": float(hf["q_std"][i]), "coverage": cov[i],
+             "bubbles": nbub[i]} for i in range(len(runs))]
+
+
+def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, base_superheat: float = 0.0137,
+                  t_switch: int = 20000, t_settle: int = 5000, t_avg: int = 15000, sample_every: int = 500,
+                  seeds=None, stream=None, dist=None, runner=None) -> dict:
+    """The boiling curve(s) for every (Delta T, G_w) pair in one batch;
+    returns per case q_bar, q_std, h_c, the wall coverage (mean, min, max),
+    the bubble count (mean, max) and the regime, and per G_w the superheat
+    and value of the largest mean heat flux (chf), the nucleate_limit
+    superheat and the superheat and value of the largest h_c. `seeds`
+    (default: cfg.seed alone) runs every case once per seed of the pool's
+    initial noise; the case statistics are then ensemble averages (see
+    `ensemble`), with q_sem the standard error of q_bar over the seeds.
+
+    With `dist` (torch.distributed with an initialised group of N ranks,
+    one GPU each) the runs are dealt out to the ranks (replicas.shard), each
+    rank steps its share as one batch, and the per-run results are gathered
+    back in order on every rank (replicas.gather_shards), so every rank
+    returns the whole curve. `runner` replaces run_cases (same arguments)."""
+    from . import replicas
+    cfg = cfg or paper_config()
+    seeds = [cfg.seed] if seeds is None else [int(s) for s in seeds]
+    rv, rl = lb.coexistence(cfg)
+    cases = [(float(dT), float(gw)) for gw in Gw_values for dT in superheats]
+    runs = [(c, sd) for c in cases for sd in seeds]
+    rank, world = 0, 1
+    if dist is not None and dist.is_initialized():
+        rank, world = dist.get_rank(), dist.get_world_size()
+    mine = replicas.shard(runs, rank, world)
+    runner = runner or run_cases
+    res = runner(mine, cfg, rv, rl, base_superheat, t_switch, t_settle, t_avg, sample_every, stream) if mine else []
+    res = replicas.gather_shards(res, rank, world, dist)
     out = []
     for k, (dT, gw) in enumerate(cases):
         idx = [i for i, (c, _) in enumerate(runs) if c == (dT, gw)]
-        st = ensemble([{"q_mean": float(hf["q_mean"][i]), "q_std": float(hf["q_std"][i]), "coverage": cov[i],
-                        "bubbles": nbub[i]} for i in idx])
+        st = ensemble([res[i] for i in idx])
         out.append(dict({"superheat": dT, "Gw": gw, "h_c": st["q_mean"] / dT}, **st))
     for c, lab in zip(out, classify_curve(out)):
         c["regime"] = lab
@@ -201,4 +223,4 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
                       "nucleate_limit_superheat": nucleate_limit(boil) if boil else None,
                       "hc_max_superheat": best["superheat"], "hc_max": best["h_c"]}
     return {"t_switch": t_switch, "t_settle": t_settle, "t_avg": t_avg, "base_superheat": base_superheat,
-            "seeds": seeds, "cases": out, "curves": curves}
+            "seeds": seeds, "cases": out, "curves": curves, "ranks": world, "runs_on_this_rank": len(mine)}
