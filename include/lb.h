@@ -171,20 +171,11 @@ int lb_sync(lb_handle* h);
  * (a multiple of 32; 10 of them are x-halo columns) and rows per segment. */
 int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblocks);
 
-/* Override the launch shape of the current kernel (seg_rows >= 1; 0 keeps
- * the automatic choice; block_x 0 picks the kernel's default). The
- * dual-strip kernels (2, 3) take block_x 64, 128 or 256 (default: 64 up to
- * 4096 columns, 128 beyond), the two-row kernel
- * (1) 128 or 256, the row-wise kernel (0) any multiple of 32 in [64, 1024].
- * Results do not depend on the launch shape. Used by the autotuner. */
+/* Override the launch shape of the fused step (seg_rows >= 1; 0 keeps the
+ * automatic choice; block_x 64, 128 or 256, 0 for the default: 64 up to
+ * 4096 columns, 128 beyond). Results do not depend on the launch shape.
+ * Used by the autotuner. */
 int lb_set_launch(lb_handle* h, int block_x, int seg_rows);
-
-/* Select the step kernel: 2 (default) marches one row per iteration over
- * two column strips per block with paired FP32 arithmetic; 3 is the same
- * with scalar FP32; 1 advances two rows per iteration with paired FP32; 0
- * is the row-wise scalar kernel. All compute the same update (to FP32
- * rounding); the launch shape returns to its automatic choice. */
-int lb_set_kernel(lb_handle* h, int kernel);
 
 /* Checkpoint: lb_save_bytes gives the blob size; lb_save writes the state,
  * step count, accumulators and wall profile into host memory; lb_load
@@ -332,22 +323,28 @@ int lb_eos_pressure(const lb_eos* eos, int64_t n, const float* rho, const float*
  *
  * Inputs (device pointers, unpitched, row-major as everywhere in this
  * header): fpost[9*Ly*Lx] post-collision populations and theta[Ly*Lx] =
- * T - T_s; rho_ave is the mean initial density of Eq. 9 and Gw the strength
- * of Eq. 22. Outputs (device, [Ly*Lx] each, any may be NULL): rho, ux, uy
- * and T exactly as lb_fields computes them. Grid fields other than Lx, Ly,
- * bc_y and ghost_layer, and the pool fields of th, are ignored.
+ * T - T_s; rho_ave is the mean density at the start of the run (the
+ * reference density of the buoyancy force) and Gw the strength of the
+ * heating wall's fluid-solid force, both as given to lb_init. Outputs
+ * (device, [Ly*Lx] each, any may be NULL): rho, ux, uy and T exactly as
+ * lb_fields computes them. Grid fields other than Lx, Ly, bc_y and
+ * ghost_layer, and the pool fields of th, are ignored.
  *
  * Scratch: the intermediate planes live in one static device array of
- * 4 * LB_NOALLOC_MAX_CELLS floats (4 MiB) plus 256 bytes inside the library,
- * which every GPU that loads the library holds until the process exits.
+ * 4 * LB_NOALLOC_MAX_CELLS floats (4 MiB) plus 256 bytes inside the library.
  * Grids larger than LB_NOALLOC_MAX_CELLS are rejected with LB_E_INVAL. The
  * first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before starting
- * any stream capture. All calls share the one array: calls that overlap on
- * the GPU (other streams, other host threads) race on it, so serialise
- * them. The call is issued on `stream` and synchronises it before
- * returning; it calls no cudaMalloc, cudaFree or other allocating routine.
- * Returns LB_E_EOS_DOMAIN if a cell's density lies outside the EOS domain. */
+ * device, with the device current); with the CUDA runtime's lazy module
+ * loading (its default) that lookup also places the 4 MiB array in device
+ * memory, so make the first call while that much device memory is still
+ * free, and before starting any stream capture. Every GPU on which it has
+ * been called keeps the array until the process exits. All calls share the
+ * one array: calls that overlap on the GPU (other streams, other host
+ * threads) race on it, so serialise them. The call is issued on `stream`
+ * and synchronises it before returning; on a stream that is being captured
+ * it enqueues nothing and returns LB_E_INVAL. It calls no cudaMalloc,
+ * cudaFree or other allocating routine. Returns LB_E_EOS_DOMAIN if a cell's
+ * density lies outside the domain of the equation of state. */
 int lb_fields_noalloc(const lb_grid* grid, const lb_eos* eos, const lb_thermal* th,
                       double Gw, double rho_ave, const float* fpost, const float* theta,
                       float* rho, float* ux, float* uy, float* T, void* stream);

@@ -22,7 +22,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbboil.so")
 LIB_CHECKED = os.path.join(OUT_DIR, "liblbboil_checked.so")
-SOURCES = ["lb_step.cu", "lb_step2.cu", "lb_step3.cu", "lb_aux.cu", "lb_host.cu", "lb_noalloc.cu", "lb_adjoint.cu"]
+SOURCES = ["lb_step3.cu", "lb_aux.cu", "lb_host.cu", "lb_noalloc.cu", "lb_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -9,24 +9,25 @@ namespace {
 __constant__ float kW[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
                             1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
 
+// The per-cell kernels below take rows blockIdx.y, blockIdx.y + gridDim.y, ...
+// (gridDim.y is capped at the 65535 limit of the launch).
 __global__ void init_kernel(const StepParams P, const float* __restrict__ rho0, float* f, float* th) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
     if (x >= P.Lx) return;
-    const int i = y * P.pitch + x;
-    const float r = rho0[i];
+    for (int y = blockIdx.y; y < P.Ly; y += gridDim.y) {
+        const int i = y * P.pitch + x;
+        const float r = rho0[i];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) f[a * P.plane + i] = kW[a] * r;
-    float t = 0.f;
-    if (P.bc != BC_PERIODIC && y == 0) t = P.thb[x];
-    th[i] = t;
+        for (int a = 0; a < 9; ++a) f[a * P.plane + i] = kW[a] * r;
+        float t = 0.f;
+        if (P.bc != BC_PERIODIC && y == 0) t = P.thb[x];
+        th[i] = t;
+    }
 }
 
-// Pass 1: pulled populations -> rho, psi, momentum sums into scratch planes.
-__global__ void macro_pass1(const StepParams P, float* scr) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= P.Lx) return;
+// Pass 1 at one cell: the pulled populations give rho, psi and the momentum
+// sums.
+__device__ __forceinline__ void macro1_cell(const StepParams& P, float* scr, int x, int y) {
     const int xm = x == 0 ? P.Lx - 1 : x - 1;
     const int xp = x == P.Lx - 1 ? 0 : x + 1;
     float f[9], th;
@@ -47,12 +48,9 @@ __global__ void macro_pass1(const StepParams P, float* scr) {
     scr[3 * P.plane + i] = jy;
 }
 
-// Pass 2: forces (Eqs. 7, 9, 22) and u = (j + F/2)/rho (Eq. 6).
-__global__ void macro_pass2(const StepParams P, const float* __restrict__ scr, float* orho, float* oux,
-                            float* ouy, float* oT, int ostride) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x >= P.Lx) return;
+// Pass 2 at one cell.
+__device__ __forceinline__ void macro2_cell(const StepParams& P, const float* __restrict__ scr, float* orho,
+                                            float* oux, float* ouy, float* oT, int ostride, int x, int y) {
     const int Lx = P.Lx, Ly = P.Ly, pitch = P.pitch;
     const bool periodic = P.bc == BC_PERIODIC;
     const bool wall = !periodic && (y == 0 || y == Ly - 1);
@@ -84,6 +82,21 @@ __global__ void macro_pass2(const StepParams P, const float* __restrict__ scr, f
     if (oT) oT[o] = P.Ts + P.th_in[i];
 }
 
+// Pass 1: pulled populations -> rho, psi, momentum sums into scratch planes.
+__global__ void macro_pass1(const StepParams P, float* scr) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P.Lx) return;
+    for (int y = blockIdx.y; y < P.Ly; y += gridDim.y) macro1_cell(P, scr, x, y);
+}
+
+// Pass 2: forces (Eqs. 7, 9, 22) and u = (j + F/2)/rho (Eq. 6).
+__global__ void macro_pass2(const StepParams P, const float* __restrict__ scr, float* orho, float* oux,
+                            float* ouy, float* oT, int ostride) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P.Lx) return;
+    for (int y = blockIdx.y; y < P.Ly; y += gridDim.y) macro2_cell(P, scr, orho, oux, ouy, oT, ostride, x, y);
+}
+
 __global__ void mass_kernel(const StepParams P, const float* __restrict__ f) {
     __shared__ double red[32];
     double s = 0.0;
@@ -109,14 +122,14 @@ __global__ void mass_kernel(const StepParams P, const float* __restrict__ f) {
 }  // namespace
 
 cudaError_t launch_init(const StepParams& P, const float* rho0, float* f, float* th, cudaStream_t st) {
-    dim3 grid((P.Lx + 127) / 128, P.Ly);
+    dim3 grid((P.Lx + 127) / 128, P.Ly < 65535 ? P.Ly : 65535);
     init_kernel<<<grid, 128, 0, st>>>(P, rho0, f, th);
     return cudaGetLastError();
 }
 
 cudaError_t launch_macro(const StepParams& P, float* scratch, float* rho, float* ux, float* uy, float* T,
                          int ostride, cudaStream_t st) {
-    dim3 grid((P.Lx + 127) / 128, P.Ly);
+    dim3 grid((P.Lx + 127) / 128, P.Ly < 65535 ? P.Ly : 65535);
     macro_pass1<<<grid, 128, 0, st>>>(P, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

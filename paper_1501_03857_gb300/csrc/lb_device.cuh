@@ -11,6 +11,9 @@
 namespace lbgpu {
 
 constexpr int HALO = 5;    // x-halo columns per side recomputed by a block
+// the narrowest block (64 threads) covers 2 (64 - 2 HALO) = 108 columns, so a
+// grid has at most ceil(Lx / 108) strips: the heat-flux slots per instance
+constexpr int MIN_STRIP_COLS = 2 * (64 - 2 * HALO);
 constexpr int RING = 4;    // rows kept per stencil field in shared memory
 constexpr int TRING = 8;   // rows kept of theta^t
 constexpr int SM_ROWS = 7 * RING + TRING;  // psi rho vx vy u2 u3 u4 + theta
@@ -20,7 +23,7 @@ enum : unsigned { ERR_EOS = 1u, ERR_NONFINITE = 2u, ERR_BOUNDS = 4u };
 
 // FP64 device accumulators (wall heat flux of Sec. 3.2, mass, fault flags).
 struct Acc {
-    double q_partial;   // sum over x of q_w for the step in flight
+    double spare;
     double q_last;      // q(t) of the last completed step
     double q_sum, q_sum2, q_n;
     double mass;
@@ -37,6 +40,9 @@ struct StepParams {
     float* th_out;
     const float* thb;   // theta_b(x) = T_b(x) - T_s on the bottom wall
     Acc* acc;
+    // one slot per column strip of the bottom segment: the strip's sum of
+    // q_w for the step in flight, folded in strip order by the last strip
+    double* qpart;
     int Lx, Ly, pitch, plane;
     int bc, ghost, isothermal;
     int nout, nstrips, seg_h;

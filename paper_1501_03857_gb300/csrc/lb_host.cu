@@ -168,8 +168,12 @@ inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
     int pitch;
-    size_t plane, f0, f1, t0, t1, thb, acc, total;
+    size_t plane, f0, f1, t0, t1, thb, acc, qpart, total;
 };
+
+// FP64 slots of the per-strip heat-flux sums (the most strips any launch
+// shape gives this width)
+inline size_t qpart_bytes(int Lx) { return sizeof(double) * (size_t)((Lx + MIN_STRIP_COLS - 1) / MIN_STRIP_COLS); }
 
 Layout layout(const lb_grid* g) {
     Layout L;
@@ -182,7 +186,8 @@ Layout layout(const lb_grid* g) {
     L.t1 = align256(L.t0 + tb);
     L.thb = align256(L.t1 + tb);
     L.acc = align256(L.thb + (size_t)L.pitch * sizeof(float));
-    L.total = align256(L.acc + sizeof(Acc));
+    L.qpart = align256(L.acc + sizeof(Acc));
+    L.total = align256(L.qpart + qpart_bytes(g->Lx));
     return L;
 }
 
@@ -202,6 +207,7 @@ struct lb_handle {
     float* t[2];
     float* thb;
     Acc* acc;
+    double* qpart;
     int cur;
     cudaStream_t st;
     int64_t steps;
@@ -248,6 +254,7 @@ void fill_params(lb_handle* h) {
     const lb_thermal& t = h->th;
     P.thb = h->thb;
     P.acc = h->acc;
+    P.qpart = h->qpart;
     P.Lx = g.Lx;
     P.Ly = g.Ly;
     P.pitch = h->lay.pitch;
@@ -285,34 +292,22 @@ void fill_params(lb_handle* h) {
     set_pairs(P);
 }
 
-// The launch shape of `kernel` for this grid (block_x, seg_rows 0: automatic).
-int compute_launch(const lb_handle* h, int kernel, int block_x, int seg_rows, Launch* out) {
+// The launch shape of the fused step for this grid (block_x, seg_rows 0:
+// automatic).
+int compute_launch(const lb_handle* h, int block_x, int seg_rows, Launch* out) {
     int dev = 0, nsm = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     const int Lx = h->grid.Lx, Ly = h->grid.Ly;
-    if (kernel < KERNEL_ROWS || kernel > KERNEL_DUAL_SCALAR) return fail(LB_E_INVAL, "unknown kernel %d", kernel);
-    const bool dual = kernel == KERNEL_DUAL || kernel == KERNEL_DUAL_SCALAR;
+    // 64 threads up to 4096 columns, 128 beyond (measured: 64 is 1-5 %
+    // faster on 1024^2-4096^2, 128 2 % faster on 8192^2)
     int bx = block_x, occ = 0;
-    if (dual) {
-        // 64 threads up to 4096 columns, 128 beyond (measured: 64 is 1-5 %
-        // faster on 1024^2-4096^2, 128 2 % faster on 8192^2)
-        if (bx <= 0) bx = Lx <= 4096 ? 64 : 128;
-        if (!dual_supported(bx)) return fail(LB_E_INVAL, "the dual-strip kernel takes block_x 64, 128 or 256, not %d", bx);
-        LB_CUDA(dual_occupancy(bx, kernel == KERNEL_DUAL, &occ), "occupancy");
-    } else if (kernel == KERNEL_PAIRS) {
-        if (bx <= 0) bx = 128;
-        if (!pairs_supported(bx)) return fail(LB_E_INVAL, "the paired kernel takes block_x 128 or 256, not %d", bx);
-        LB_CUDA(pairs_occupancy(bx, &occ), "occupancy");
-    } else {
-        if (bx <= 0) bx = (Lx + 2 * HALO <= 256) ? std::max(64, (Lx + 2 * HALO + 31) / 32 * 32) : 256;
-        if (bx < 64 || bx > 1024 || bx % 32)
-            return fail(LB_E_INVAL, "block_x %d must be a multiple of 32 in [64, 1024]", bx);
-        LB_CUDA((cudaError_t)step_occupancy(bx, &occ), "occupancy");
-    }
+    if (bx <= 0) bx = Lx <= 4096 ? 64 : 128;
+    if (!dual_supported(bx)) return fail(LB_E_INVAL, "the fused step takes block_x 64, 128 or 256, not %d", bx);
+    LB_CUDA(dual_occupancy(bx, &occ), "occupancy");
     if (occ < 1) return fail(LB_E_INVAL, "block_x %d does not fit on an SM", bx);
     const int nout = bx - 2 * HALO;
-    const int cols = dual ? 2 * nout : nout;  // output columns per block
+    const int cols = 2 * nout;  // output columns per block
     const int nstrips = (Lx + cols - 1) / cols;
     int seg = seg_rows;
     if (seg <= 0) {
@@ -320,8 +315,6 @@ int compute_launch(const lb_handle* h, int kernel, int block_x, int seg_rows, La
         const int nseg = std::max(1, slots / nstrips);
         seg = std::max(8, (Ly + nseg - 1) / nseg);
     }
-    if (kernel == KERNEL_PAIRS) seg += seg & 1;  // segments start on even rows
-    out->kernel = kernel;
     out->block_x = bx;
     out->seg_rows = seg;
     out->nstrips = nstrips;
@@ -336,9 +329,9 @@ void apply_launch(StepParams& P, const Launch& L) {
     P.seg_h = L.seg_rows;
 }
 
-int choose_launch(lb_handle* h, int kernel, int block_x, int seg_rows) {
+int choose_launch(lb_handle* h, int block_x, int seg_rows) {
     Launch L;
-    const int rc = compute_launch(h, kernel, block_x, seg_rows, &L);
+    const int rc = compute_launch(h, block_x, seg_rows, &L);
     if (rc) return rc;
     h->launch = L;
     apply_launch(h->base, L);
@@ -557,6 +550,7 @@ int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_th
     h->t[1] = (float*)(h->ws + lay.t1);
     h->thb = (float*)(h->ws + lay.thb);
     h->acc = (Acc*)(h->ws + lay.acc);
+    h->qpart = (double*)(h->ws + lay.qpart);
     h->cur = 0;
     h->st = (cudaStream_t)stream;
     h->steps = 0;
@@ -594,11 +588,9 @@ int lb_init(lb_handle** out, const lb_grid* grid, const lb_eos* eos, const lb_th
     }
     h->rho_ave = sum / ((double)Lx * Ly);
     fill_params(h);
-    cudaError_t e = step_prepare(1024);
-    if (e == cudaSuccess) e = pairs_prepare();
-    if (e == cudaSuccess) e = dual_prepare();
+    cudaError_t e = dual_prepare();
     if (e != cudaSuccess) { release(h); return cuda_fail(e, "cudaFuncSetAttribute"); }
-    rc = choose_launch(h, KERNEL_DUAL, 0, 0);  // paired-FP32 dual-strip kernel by default
+    rc = choose_launch(h, 0, 0);
     if (rc) { release(h); return rc; }
 
     auto bail = [&](cudaError_t err, const char* what) { release(h); return cuda_fail(err, what); };
@@ -746,12 +738,7 @@ int lb_info(lb_handle* h, int64_t* steps, int* block_x, int* seg_rows, int* nblo
 int lb_set_launch(lb_handle* h, int block_x, int seg_rows) {
     if (!h) return fail(LB_E_INVAL, "null handle");
     if (seg_rows < 0) return fail(LB_E_INVAL, "seg_rows must be >= 0");
-    return choose_launch(h, h->launch.kernel, block_x, seg_rows);
-}
-
-int lb_set_kernel(lb_handle* h, int kernel) {
-    if (!h) return fail(LB_E_INVAL, "null handle");
-    return choose_launch(h, kernel, 0, 0);
+    return choose_launch(h, block_x, seg_rows);
 }
 
 namespace {
@@ -813,7 +800,6 @@ int lb_load(lb_handle* h, const void* host_buf, size_t bytes) {
     memcpy(&a, p, sizeof(Acc));
     a.err = 0;
     a.count = 0;
-    a.q_partial = 0.0;
     LB_CUDA(cudaMemcpyAsync(h->acc, &a, sizeof(Acc), cudaMemcpyHostToDevice, h->st), "load accumulators");
     p += sizeof(Acc);
     const size_t cells = (size_t)h->grid.Lx * h->grid.Ly;
@@ -1002,7 +988,6 @@ int batch_layout(lb_batch* b) {
             const int nseg = std::max(1, (int)(share * nsm * occ / nstrips));
             seg = std::max(8, (h->grid.Ly + nseg - 1) / nseg);
         }
-        h->launch.kernel = KERNEL_DUAL;
         h->launch.block_x = b->block_x;
         h->launch.seg_rows = seg;
         h->launch.nstrips = nstrips;
@@ -1382,15 +1367,10 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         }
         return LB_OK;
     };
-    // the reverse step recomputes the step's intermediates with the paired
-    // dual-strip kernel: its launch shape (the current one if that kernel is
-    // in use)
-    Launch RL = h->launch;
-    StepParams RB = base;
-    if (RL.kernel != KERNEL_DUAL && RL.kernel != KERNEL_DUAL_SCALAR) {
-        if ((rc = compute_launch(h, KERNEL_DUAL, 0, 0, &RL))) return rc;
-        apply_launch(RB, RL);
-    }
+    // the reverse step recomputes the step's intermediates with the fused
+    // step in its write-out mode, in the current launch shape
+    const Launch RL = h->launch;
+    const StepParams RB = base;
     auto sweep = [&](int len, int buf, int c0, cudaStream_t q) -> int {
         int c = c0;
         for (int j = len - 1; j >= 0; --j) {

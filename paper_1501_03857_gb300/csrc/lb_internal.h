@@ -8,31 +8,19 @@
 
 namespace lbgpu {
 
-// Launch shape of the fused step: block_x threads per block (block_x - 2*HALO
-// output columns), seg_rows rows per block, nstrips x nseg blocks.
+// Launch shape of the fused step (lb_step3.cu): block_x threads per block,
+// each thread owning one column of two strips of block_x - 2*HALO output
+// columns; seg_rows rows per block; nstrips x nseg blocks.
 struct Launch {
     int block_x, seg_rows, nstrips, nseg;
-    int kernel;  // KERNEL_ROWS or KERNEL_PAIRS
 };
 
-enum { KERNEL_ROWS = 0, KERNEL_PAIRS = 1, KERNEL_DUAL = 2, KERNEL_DUAL_SCALAR = 3 };
-
-size_t step_smem_bytes(int block_x);
-cudaError_t step_prepare(int block_x);  // opt in to the dynamic shared memory
-cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
-int step_occupancy(int block_x, int* blocks_per_sm);
-
-// The two-rows-per-iteration kernel with paired FP32 arithmetic (lb_step2.cu).
-bool pairs_supported(int block_x);
-cudaError_t pairs_prepare();
-cudaError_t pairs_occupancy(int block_x, int* blocks_per_sm);
-cudaError_t pairs_launch(const StepParams& P, const Launch& L, cudaStream_t st);
-
-// One row per iteration, two column strips per block in paired FP32 (lb_step3.cu).
+// One step of the fused kernel: one row per iteration, two column strips per
+// block in paired FP32 (block_x 64, 128 or 256).
 bool dual_supported(int block_x);
-cudaError_t dual_prepare();
-cudaError_t dual_occupancy(int block_x, bool paired, int* blocks_per_sm);
-cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st);
+cudaError_t dual_prepare();  // opt in to the dynamic shared memory
+cudaError_t dual_occupancy(int block_x, int* blocks_per_sm);
+cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
 
 // The forward intermediates of one step that the adjoint's reverse kernels
 // read (lb_adjoint.cu), written by the dual-strip step in its recompute mode

@@ -8,9 +8,10 @@
 // because lb_init received a caller-allocated workspace; this entry point
 // needs no handle and no workspace. Its scratch (four planes: density,
 // pseudopotential and the two momentum sums of the pulled populations, plus
-// the fault-flag word) lives in the file-scope array below, which the CUDA
-// runtime places in device memory when the library is loaded on a device and
-// which every GPU that loads the library keeps until the process exits.
+// the fault-flag word) lives in the file-scope array below. With the CUDA
+// runtime's lazy module loading (its default) the array is placed in device
+// memory when the first call on a device looks up its address, and that
+// device keeps it until the process exits.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -66,6 +67,15 @@ extern "C" int lb_fields_noalloc(const lb_grid* grid, const lb_eos* eos, const l
     if (!grid || !eos || !th || !fpost || !theta) return fail(LB_E_INVAL, "null argument");
     if (grid->Lx < 1 || grid->Ly < 3 || grid->bc_y < LB_BC_WALLS || grid->bc_y > LB_BC_PERIODIC)
         return fail(LB_E_INVAL, "bad grid (need Lx >= 1, Ly >= 3, bc_y in 0..2)");
+    // the call waits for the stream before it returns, which a stream under
+    // capture does not allow: refuse before anything is enqueued, so that the
+    // caller's capture stays valid
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(st, &cap);
+    if (ce != cudaSuccess) return fail(LB_E_CUDA, cudaGetErrorString(ce));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(LB_E_INVAL, "the stream is being captured; lb_fields_noalloc synchronises its stream");
     const long long cells = (long long)grid->Lx * grid->Ly;
     if (cells > LB_NOALLOC_MAX_CELLS)
         return fail(LB_E_INVAL, "grid has more cells than LB_NOALLOC_MAX_CELLS; use lb_fields with a workspace");
@@ -75,12 +85,11 @@ extern "C" int lb_fields_noalloc(const lb_grid* grid, const lb_eos* eos, const l
     void* base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return fail(LB_E_CUDA, cudaGetErrorString(e));
-    cudaStream_t st = (cudaStream_t)stream;
     Acc* acc = (Acc*)base;
     float* planes = (float*)((unsigned char*)base + kAccBytes);
 
-    // parameters of the pulled populations, the EOS (Eq. 21) and the forces
-    // (Eqs. 7, 9, 22) at this level; the arrays are unpitched [.][Ly][Lx]
+    // parameters of the pulled populations, the equation of state and the
+    // forces at this level; the arrays are unpitched [.][Ly][Lx]
     StepParams P;
     memset(&P, 0, sizeof(P));
     const double Tc = 0.0778 * eos->a / (0.45724 * eos->b * eos->R);

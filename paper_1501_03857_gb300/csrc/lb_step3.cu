@@ -1,9 +1,9 @@
 // The fused time step, one row per iteration, two column strips per block,
 // with paired FP32 arithmetic.
 //
-// Same pipeline as the row-wise kernel (lb_step.cu): a block marches up a
-// segment of rows; every population and temperature value is read from HBM
-// once and written once per step. Here a block owns TWO adjacent column
+// A block marches up a segment of rows through a pipeline of stages, each
+// one row behind the previous; every population and temperature value is
+// read from HBM once and written once per step. A block owns TWO adjacent column
 // strips of (BD - 10) output columns each, and thread lc computes column lc
 // of both; the two cells are packed in one float2 (strip A in .x, strip B in
 // .y). A stencil neighbour of the pair is then again an aligned float2 in
@@ -51,24 +51,6 @@ __device__ __forceinline__ P2 operator-(P2 a) { return P2(make_float2(-a.v.x, -a
 __device__ __forceinline__ P2 operator*(P2 a, P2 b) { return P2(__fmul2_rn(a.v, b.v)); }
 __device__ __forceinline__ P2 operator*(float s, P2 b) { return P2(__fmul2_rn(make_float2(s, s), b.v)); }
 __device__ __forceinline__ P2 fma2(P2 a, P2 b, P2 c) { return P2(__ffma2_rn(a.v, b.v, c.v)); }
-
-// The same two cells with scalar FP32 instructions.
-struct S2 {
-    float a, b;
-    __device__ __forceinline__ S2() {}
-    __device__ __forceinline__ explicit S2(float2 v) : a(v.x), b(v.y) {}
-    __device__ __forceinline__ S2(float x, float y) : a(x), b(y) {}
-    __device__ __forceinline__ float x() const { return a; }
-    __device__ __forceinline__ float y() const { return b; }
-    __device__ __forceinline__ float2 f2() const { return make_float2(a, b); }
-    static __device__ __forceinline__ S2 bc(float s) { return S2(s, s); }
-};
-__device__ __forceinline__ S2 operator+(S2 p, S2 q) { return S2(p.a + q.a, p.b + q.b); }
-__device__ __forceinline__ S2 operator-(S2 p, S2 q) { return S2(p.a - q.a, p.b - q.b); }
-__device__ __forceinline__ S2 operator-(S2 p) { return S2(-p.a, -p.b); }
-__device__ __forceinline__ S2 operator*(S2 p, S2 q) { return S2(p.a * q.a, p.b * q.b); }
-__device__ __forceinline__ S2 operator*(float s, S2 q) { return S2(s * q.a, s * q.b); }
-__device__ __forceinline__ S2 fma2(S2 p, S2 q, S2 r) { return S2(fmaf(p.a, q.a, r.a), fmaf(p.b, q.b, r.b)); }
 
 // the special-function unit's approximate reciprocal and 1/sqrt (PTX
 // rcp.approx / rsqrt.approx, flushing subnormals: none occur in the step)
@@ -284,6 +266,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
     constexpr int W = BD + 2;
     extern __shared__ float2 sm2[];
     __shared__ double red[BD / 32];
+    __shared__ bool s_last;
     float2* const sPSI = sm2;
     float2* const sRHO = sPSI + RING * W;
     float2* const sVX = sRHO + RING * W;
@@ -421,18 +404,26 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
             for (int o = 16; o > 0; o >>= 1) qv += __shfl_down_sync(0xffffffffu, qv, o);
             if ((lc & 31) == 0) red[lc >> 5] = qv;
             __syncthreads();
+            // each strip's sum goes to its own slot; the strip that arrives
+            // last folds the slots in strip order, so q(t) does not depend on
+            // the order in which the blocks finish
             if (lc == 0) {
                 double sum = 0.0;
 #pragma unroll
                 for (int w = 0; w < BD / 32; ++w) sum += red[w];
-                Acc* A = P.acc;
-                atomicAdd(&A->q_partial, sum);
+                P.qpart[strip] = sum;
                 __threadfence();
-                const unsigned t = atomicAdd(&A->count, 1u);
-                if (t == (unsigned)P.nstrips - 1u) {
-                    __threadfence();
-                    const double tot = __longlong_as_double(
-                        (long long)atomicExch((unsigned long long*)&A->q_partial, 0ull));
+                s_last = atomicAdd(&P.acc->count, 1u) == (unsigned)P.nstrips - 1u;
+            }
+            __syncthreads();
+            if (s_last && lc < 32) {
+                __threadfence();
+                double tot = 0.0;
+                for (int k = lc; k < P.nstrips; k += 32) tot += __ldcg(P.qpart + k);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                if (lc == 0) {
+                    Acc* A = P.acc;
                     const double qt = tot / (double)Lx;
                     A->q_last = qt;
                     A->q_sum += qt;
@@ -797,11 +788,10 @@ struct DualKernel {
 // lb_step_dual gives the compiler its block size alone). The
 // batched step keeps 128 registers: with its parameters in shared memory it
 // ran 7 % slower with the larger budget.
-template <class T>
 cudaError_t dual_prepare_t() {
-    cudaError_t e = DualKernel<64, 6, T>::prepare();
-    if (e == cudaSuccess) e = DualKernel<128, 3, T>::prepare();
-    if (e == cudaSuccess) e = DualKernel<256, 2, T>::prepare();
+    cudaError_t e = DualKernel<64, 6, P2>::prepare();
+    if (e == cudaSuccess) e = DualKernel<128, 3, P2>::prepare();
+    if (e == cudaSuccess) e = DualKernel<256, 2, P2>::prepare();
     return e;
 }
 
@@ -813,19 +803,17 @@ cudaError_t batch_prepare_t() {
     return e;
 }
 
-template <class T>
 cudaError_t dual_occupancy_t(int block_x, int* n) {
-    if (block_x == 64) return DualKernel<64, 6, T>::occupancy(n);
-    if (block_x == 128) return DualKernel<128, 3, T>::occupancy(n);
-    return DualKernel<256, 2, T>::occupancy(n);
+    if (block_x == 64) return DualKernel<64, 6, P2>::occupancy(n);
+    if (block_x == 128) return DualKernel<128, 3, P2>::occupancy(n);
+    return DualKernel<256, 2, P2>::occupancy(n);
 }
 
-template <class T>
 cudaError_t dual_launch_t(const StepParams& P, const Launch& L, cudaStream_t st) {
     const int nb = L.nstrips * L.nseg;
-    if (L.block_x == 64) return DualKernel<64, 6, T>::launch(P, nb, st);
-    if (L.block_x == 128) return DualKernel<128, 3, T>::launch(P, nb, st);
-    return DualKernel<256, 2, T>::launch(P, nb, st);
+    if (L.block_x == 64) return DualKernel<64, 6, P2>::launch(P, nb, st);
+    if (L.block_x == 128) return DualKernel<128, 3, P2>::launch(P, nb, st);
+    return DualKernel<256, 2, P2>::launch(P, nb, st);
 }
 
 }  // namespace
@@ -857,21 +845,16 @@ cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Lau
 }
 
 cudaError_t dual_prepare() {
-    cudaError_t e = dual_prepare_t<P2>();
-    if (e == cudaSuccess) e = dual_prepare_t<S2>();
+    cudaError_t e = dual_prepare_t();
     if (e == cudaSuccess) e = recompute_prepare_t<64, 6>();
     if (e == cudaSuccess) e = recompute_prepare_t<128, 3>();
     if (e == cudaSuccess) e = recompute_prepare_t<256, 2>();
     return e;
 }
 
-cudaError_t dual_occupancy(int block_x, bool paired, int* n) {
-    return paired ? dual_occupancy_t<P2>(block_x, n) : dual_occupancy_t<S2>(block_x, n);
-}
+cudaError_t dual_occupancy(int block_x, int* n) { return dual_occupancy_t(block_x, n); }
 
-cudaError_t dual_launch(const StepParams& P, const Launch& L, bool paired, cudaStream_t st) {
-    return paired ? dual_launch_t<P2>(P, L, st) : dual_launch_t<S2>(P, L, st);
-}
+cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st) { return dual_launch_t(P, L, st); }
 
 bool batch_supported(int block_x) { return block_x == 64 || block_x == 128; }
 

@@ -72,7 +72,6 @@ def _load():
         "lb_sync": [P],
         "lb_info": [P, I64P, C.POINTER(I), C.POINTER(I), C.POINTER(I)],
         "lb_set_launch": [P, I, I],
-        "lb_set_kernel": [P, I],
         "lb_save_bytes": [P, C.POINTER(C.c_size_t)],
         "lb_save": [P, P, SZ],
         "lb_load": [P, P, SZ],
@@ -203,9 +202,21 @@ def fields_noalloc(cfg: Config, Gw: float, rho_ave: float, fpost, theta, rho=Non
     """Macroscopic fields of a device-resident state without a handle or any
     device allocation (lb_fields_noalloc). fpost [9, Ly, Lx] and theta
     [Ly, Lx] are contiguous float32 CUDA tensors; outputs are preallocated
-    float32 CUDA tensors [Ly, Lx] or None. Grids above NOALLOC_MAX_CELLS cells
-    are rejected."""
+    contiguous float32 CUDA tensors [Ly, Lx] or None. Grids above
+    NOALLOC_MAX_CELLS cells are rejected. Raises ValueError before any call
+    into the library when a tensor has the wrong dtype, device, layout or
+    shape (the kernels would read or write past a smaller buffer)."""
     import torch
+    shapes = {"fpost": (9, cfg.Ly, cfg.Lx), "theta": (cfg.Ly, cfg.Lx)}
+    for name, x in (("fpost", fpost), ("theta", theta), ("rho", rho), ("ux", ux), ("uy", uy), ("T", T)):
+        if x is None:
+            if name in shapes:
+                raise ValueError(f"{name} is required")
+            continue
+        want = shapes.get(name, (cfg.Ly, cfg.Lx))
+        if not isinstance(x, torch.Tensor) or x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() \
+                or tuple(x.shape) != want:
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {want}")
     g, e, t = cfg.structs()
     st = stream if stream is not None else torch.cuda.current_stream()
     ptr = lambda x: None if x is None else x.data_ptr()
@@ -260,11 +271,6 @@ class Simulation:
 
     def set_launch(self, block_x: int = 0, seg_rows: int = 0):
         check(lib.lb_set_launch(self.h, int(block_x), int(seg_rows)))
-
-    def set_kernel(self, kernel: int):
-        """2: dual-strip paired FP32 kernel (default); 3: the same with scalar
-        FP32; 1: two rows per iteration, paired FP32; 0: row-wise scalar."""
-        check(lib.lb_set_kernel(self.h, int(kernel)))
 
     def info(self):
         st, bx, sr, nb = C.c_int64(), C.c_int(), C.c_int(), C.c_int()

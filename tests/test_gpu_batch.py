@@ -1,6 +1,8 @@
 """The batched form: several uneven-size simulations advanced by one launch
 per step (with captured graphs for runs of 32 steps) give bit-identical
-results to stepping each instance alone, for odd and even step counts."""
+results to stepping each instance alone, for odd and even step counts. The
+heat flux is folded from fixed per-strip slots in strip order, so with the
+same block size (the same strips) its statistics are identical too."""
 
 import numpy as np
 import pytest
@@ -42,13 +44,14 @@ def test_batch_equals_single_instances(lb, shape):
     q = batch.heat_flux()
     for i, d in enumerate(insts):
         sim = lb.Simulation(d["cfg"], superheat=d["superheat"], Gw=d["Gw"], rho0=d["rho0"])
+        sim.set_launch(shape[0], 0)
         sim.step(80)
         fs, ts = sim.get_state()
         fb, tb = batch.get_state(i)
         assert np.array_equal(fs, fb) and np.array_equal(ts, tb), i
         hs = sim.heat_flux()
         assert q["n"][i] == hs["n"] == 80
-        assert abs(q["q_mean"][i] - hs["q_mean"]) <= 1e-12 * abs(hs["q_mean"])
+        assert q["q_mean"][i] == hs["q_mean"] and q["q_std"][i] == hs["q_std"]
         # macroscopic fields of the instance (lb_batch_fields) equal the
         # single run's (lb_fields); a subset is computed when asked
         fb_all = batch.fields(i)

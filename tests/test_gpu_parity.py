@@ -48,14 +48,12 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernel", [2, 3, 1, 0])
 @pytest.mark.parametrize("Lx,Ly,bc,ghost,Gw,iso", CASES)
-def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
+def test_one_step_from_random_state(lb, Lx, Ly, bc, ghost, Gw, iso):
     cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, ghost_layer=ghost, isothermal=iso)
     rv, rl = coex(lb, cfg)
     rho0, f0, th0 = inputs.random_state(Lx, Ly, rl, rv, Ly * 0.45, seed=Lx * 1000 + Ly)
     sim = lb.Simulation(cfg, superheat=0.012, Gw=Gw, rho0=rho0)
-    sim.set_kernel(kernel)
     sim.set_launch(0, 6)  # several segments even on small grids
     sim.set_state(f0, th0)
     sim.step(1)
@@ -74,9 +72,8 @@ MINIMAL = [(1, 3, 0, False, 0.0, False), (1, 9, 2, False, 0.0, False), (2, 3, 1,
            (5, 4, 0, True, 0.0, False), (3, 5, 2, False, 0.0, True)]
 
 
-@pytest.mark.parametrize("kernel", [2, 3])
 @pytest.mark.parametrize("Lx,Ly,bc,ghost,Gw,iso", MINIMAL)
-def test_one_step_minimal_grids(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
+def test_one_step_minimal_grids(lb, Lx, Ly, bc, ghost, Gw, iso):
     """The smallest grids the library accepts (one column, three rows, every
     boundary treatment) against the oracle, after the bounds-checked build
     ran them without a flag (test_gpu_checked.py)."""
@@ -84,7 +81,6 @@ def test_one_step_minimal_grids(lb, Lx, Ly, bc, ghost, Gw, iso, kernel):
     rv, rl = coex(lb, cfg)
     rho0, f0, th0 = inputs.random_state(Lx, Ly, rl, rv, Ly * 0.45, seed=Lx * 1000 + Ly)
     sim = lb.Simulation(cfg, superheat=0.012, Gw=Gw, rho0=rho0)
-    sim.set_kernel(kernel)
     sim.set_state(f0, th0)
     sim.step(1)
     fg, tg = sim.get_state()
@@ -195,23 +191,18 @@ def test_200_steps_paper_scale_300x400(lb):
     assert abs(h["q_mean"] / np.mean(qs) - 1) < 1e-5
 
 
-SHAPES = {0: ((0, 0), (64, 1), (96, 7), (256, 57), (512, 3), (128, 1000)),
-          1: ((0, 0), (128, 2), (256, 6), (128, 1000), (256, 58), (128, 14)),
-          2: ((0, 0), (64, 1), (128, 5), (256, 57), (64, 1000), (128, 13)),
-          3: ((0, 0), (64, 1), (128, 5), (256, 57), (64, 1000), (128, 13))}
+SHAPES = ((0, 0), (64, 1), (128, 5), (256, 57), (64, 1000), (128, 13))
 
 
-@pytest.mark.parametrize("kernel", [2, 3, 1, 0])
-def test_launch_shape_does_not_change_results(lb, kernel):
+def test_launch_shape_does_not_change_results(lb):
     """Each cell's arithmetic is the same whatever the strip width and segment
     height, so the results are bit-identical across launch shapes."""
     cfg = lb.Config(Lx=263, Ly=57, bc_y=0)
     rv, rl = coex(lb, cfg)
     rho0, f0, th0 = inputs.random_state(cfg.Lx, cfg.Ly, rl, rv, 25, seed=5)
     ref = None
-    for bx, seg in SHAPES[kernel]:
+    for bx, seg in SHAPES:
         sim = lb.Simulation(cfg, superheat=0.01, Gw=0.05, rho0=rho0)
-        sim.set_kernel(kernel)
         sim.set_launch(bx, seg)
         sim.set_state(f0, th0)
         sim.step(3)
@@ -220,6 +211,23 @@ def test_launch_shape_does_not_change_results(lb, kernel):
             ref = (fg, tg)
         else:
             assert np.array_equal(fg, ref[0]) and np.array_equal(tg, ref[1]), (bx, seg)
+
+
+def test_heat_flux_is_reproducible(lb):
+    """Two runs of the same wide domain (38 column strips, so 38 blocks add
+    to q(t) every step, finishing in whatever order the GPU schedules them)
+    give identical heat-flux statistics: each strip's sum has its own slot
+    and the slots are folded in strip order."""
+    cfg = lb.Config(Lx=4096, Ly=48, bc_y=0, pool_height=20, noise_amp=1e-3, seed=7)
+    out = []
+    for _ in range(2):
+        sim = lb.Simulation(cfg, superheat=0.02, Gw=0.05)
+        sim.step(70)
+        out.append(sim.heat_flux())
+        sim.close()
+    assert out[0]["n"] == 70
+    assert out[0]["q_mean"] == out[1]["q_mean"] and out[0]["q_std"] == out[1]["q_std"]
+    assert out[0]["q_inst"] == out[1]["q_inst"]
 
 
 def test_fields_and_mass_match_oracle(lb):

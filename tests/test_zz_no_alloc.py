@@ -50,12 +50,67 @@ def test_noalloc_fields_match_lb_fields_on_two_calls(lb, bc, ghost):
         ref = [torch.empty(Ly, Lx, **dev) for _ in range(4)]
         sim.fields_device(*ref)
         out = [torch.full((Ly, Lx), float("nan"), **dev) for _ in range(4)]
+        torch.cuda.synchronize()
+        before = (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated())
         lb.fields_noalloc(cfg, Gw, rho_ave, f, th, *out)
         torch.cuda.synchronize()
+        if call == 1:
+            # the first call may place the library's static array (lazy
+            # module loading); the second must not take any device memory
+            assert (torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()) == before
         for name, a, b in zip(("rho", "ux", "uy", "T"), out, ref):
             assert torch.isfinite(a).all(), (call, name)
             assert _norm_err(a, b) <= TOL, (call, name, _norm_err(a, b))
         sim.step(5)  # a different state for the second call
+
+
+def test_noalloc_tall_grid_matches_lb_fields(lb):
+    """A grid taller than the 65535 blocks a launch takes in y (2 x 70000
+    cells, within the scratch): the per-cell kernels loop over rows."""
+    Lx, Ly = 2, 70000
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=0, pool_height=30000)
+    rho0 = lb.initial_density(cfg)
+    sim = lb.Simulation(cfg, superheat=0.01, rho0=rho0)
+    sim.step(3)
+    dev = dict(dtype=torch.float32, device="cuda")
+    f = torch.empty(9, Ly, Lx, **dev)
+    th = torch.empty(Ly, Lx, **dev)
+    sim.get_state_device(f, th)
+    ref = [torch.empty(Ly, Lx, **dev) for _ in range(4)]
+    sim.fields_device(*ref)
+    out = [torch.full((Ly, Lx), float("nan"), **dev) for _ in range(4)]
+    lb.fields_noalloc(cfg, 0.0, float(np.asarray(rho0, np.float64).mean()), f, th, *out)
+    torch.cuda.synchronize()
+    for name, a, b in zip(("rho", "ux", "uy", "T"), out, ref):
+        assert torch.isfinite(a).all(), name
+        assert _norm_err(a, b) <= TOL, (name, _norm_err(a, b))
+    sim.close()
+
+
+def test_noalloc_refuses_a_capturing_stream(lb):
+    """The call synchronises its stream, which a stream under capture does
+    not allow: it returns LB_E_INVAL without enqueuing anything, and the
+    caller's capture stays valid and can be completed and replayed."""
+    Lx, Ly = 32, 16
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=0)
+    dev = dict(dtype=torch.float32, device="cuda")
+    f = torch.full((9, Ly, Lx), 0.5, **dev)
+    th = torch.zeros(Ly, Lx, **dev)
+    x = torch.zeros(4, **dev)
+    lb.fields_noalloc(cfg, 0.0, 4.5, f, th, torch.empty(Ly, Lx, **dev))  # set-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    out = torch.empty(Ly, Lx, **dev)
+    with torch.cuda.graph(g, stream=s):
+        x.add_(1.0)
+        with pytest.raises(lb.LBError) as ei:
+            lb.fields_noalloc(cfg, 0.0, 4.5, f, th, out, stream=s)
+        x.add_(1.0)
+    assert ei.value.code == -1 and "captured" in str(ei.value)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x, torch.full((4,), 2.0, **dev))
 
 
 def test_noalloc_rejects_grids_above_its_scratch(lb):
