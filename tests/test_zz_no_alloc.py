@@ -117,8 +117,8 @@ def test_noalloc_rejects_grids_above_its_scratch(lb):
     cfg = lb.Config(Lx=1024, Ly=1024)
     assert cfg.Lx * cfg.Ly > lb.NOALLOC_MAX_CELLS
     dev = dict(dtype=torch.float32, device="cuda")
-    f = torch.zeros(9, 4, 4, **dev)
-    th = torch.zeros(4, 4, **dev)
+    f = torch.zeros(9, cfg.Ly, cfg.Lx, **dev)
+    th = torch.zeros(cfg.Ly, cfg.Lx, **dev)
     with pytest.raises(lb.LBError) as ei:
         lb.fields_noalloc(cfg, 0.0, 3.0, f, th)
     assert ei.value.code == -1 and "LB_NOALLOC_MAX_CELLS" in str(ei.value)
