@@ -266,7 +266,6 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
     constexpr int W = BD + 2;
     extern __shared__ float2 sm2[];
     __shared__ double red[BD / 32];
-    __shared__ bool s_last;
     float2* const sPSI = sm2;
     float2* const sRHO = sPSI + RING * W;
     float2* const sVX = sRHO + RING * W;
@@ -404,33 +403,12 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
             for (int o = 16; o > 0; o >>= 1) qv += __shfl_down_sync(0xffffffffu, qv, o);
             if ((lc & 31) == 0) red[lc >> 5] = qv;
             __syncthreads();
-            // each strip's sum goes to its own slot; the strip that arrives
-            // last folds the slots in strip order, so q(t) does not depend on
-            // the order in which the blocks finish
+            // each strip's sum goes to its own slot (folded at the block's end)
             if (lc == 0) {
                 double sum = 0.0;
 #pragma unroll
                 for (int w = 0; w < BD / 32; ++w) sum += red[w];
                 P.qpart[strip] = sum;
-                __threadfence();
-                s_last = atomicAdd(&P.acc->count, 1u) == (unsigned)P.nstrips - 1u;
-            }
-            __syncthreads();
-            if (s_last && lc < 32) {
-                __threadfence();
-                double tot = 0.0;
-                for (int k = lc; k < P.nstrips; k += 32) tot += __ldcg(P.qpart + k);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-                if (lc == 0) {
-                    Acc* A = P.acc;
-                    const double qt = tot / (double)Lx;
-                    A->q_last = qt;
-                    A->q_sum += qt;
-                    A->q_sum2 += qt * qt;
-                    A->q_n += 1.0;
-                    atomicExch(&A->count, 0u);
-                }
             }
         }
 
@@ -653,6 +631,35 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
     for (; L <= ye + 4; ++L) iter(L, std::false_type{});
     if (eos_bad) atomicOr(&P.acc->err, ERR_EOS);
     if (nonfinite) atomicOr(&P.acc->err, ERR_NONFINITE);
+    // the strip that finishes last among the bottom segment's folds the slots
+    // in strip order into q(t), so q(t) does not depend on the order in which
+    // the blocks finish (folding here, when the block has no work left,
+    // costs nothing; folding right after the partial sums delayed that block
+    // and lengthened the step by 4 %)
+    if (!REC && !periodic && ys == 0) {
+        __shared__ bool s_last;
+        if (lc == 0) {
+            __threadfence();
+            s_last = atomicAdd(&P.acc->count, 1u) == (unsigned)P.nstrips - 1u;
+        }
+        __syncthreads();
+        if (s_last && lc < 32) {
+            __threadfence();
+            double tot = 0.0;
+            for (int k = lc; k < P.nstrips; k += 32) tot += __ldcg(P.qpart + k);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            if (lc == 0) {
+                Acc* A = P.acc;
+                const double qt = tot / (double)Lx;
+                A->q_last = qt;
+                A->q_sum += qt;
+                A->q_sum2 += qt * qt;
+                A->q_n += 1.0;
+                A->count = 0u;
+            }
+        }
+    }
 }
 #undef LB_SMP
 #undef LB_SMC
