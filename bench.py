@@ -257,7 +257,12 @@ def batched_curve(torch, lb, gw_of_angle, steps_batch=64, steps_seq=32, dist=Non
     cells = sum(d["cfg"].Lx * d["cfg"].Ly for d in insts)
     st = torch.cuda.current_stream()
     batch = lb.Batch(insts, stream=st)
-    bx, seg, _ = tune.tune_batch(batch)
+    # every candidate launch (one launch per step, and the persistent launch
+    # with 1-4 tiles per block) timed; the fastest is the batched figure
+    cands = tune.time_batch_candidates(batch)
+    best_step = min((v, k) for k, v in cands.items() if k[2] == 0)
+    best_pers = min(((v, k) for k, v in cands.items() if k[2] > 0), default=None)
+    bx, seg, _, tpb = tune.tune_batch(batch)
     batch.step(GRAPH_WARM)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.synchronize()
@@ -289,8 +294,13 @@ def batched_curve(torch, lb, gw_of_angle, steps_batch=64, steps_seq=32, dist=Non
             "ms_per_step_batched": t_b, "ms_per_step_sequential": t_seq,
             "sims_per_hour_batched": sph(t_b), "sims_per_hour_sequential": sph(t_seq),
             "speedup": t_seq / t_b, "mlups_batched": cells / (t_b * 1e3) * world,
-            "launch": {"block_x": bx, "seg_rows": seg, "blocks": info["blocks"],
-                       "graph": "32-step captured graphs"}}
+            "launch": {"block_x": bx, "seg_rows": seg, "tiles_per_block": tpb, "blocks": info["blocks"],
+                       "mode": ("persistent: one cooperative launch per 32 steps" if tpb
+                                else "one launch per step") + ", replayed from captured graphs"},
+            "tuner_ms_per_step": {"per_step_launch": {"ms": best_step[0], "block_x": best_step[1][0],
+                                                      "seg_rows": best_step[1][1]},
+                                  "persistent": None if best_pers is None else
+                                  {"ms": best_pers[0], "block_x": best_pers[1][0], "tiles_per_block": best_pers[1][2]}}}
 
 
 GRAPH_WARM = 32

@@ -245,6 +245,24 @@ int lb_batch_step(lb_batch* b, int nsteps);
  * every instance a share of one full wave proportional to its cells. */
 int lb_batch_set_launch(lb_batch* b, int block_x, int seg_rows);
 
+/* Persistent mode (the batched boiling curve of Sec. 3.2-3.3 in one launch
+ * per run of steps). tiles_per_block = 0 returns to one launch per step.
+ * With tiles_per_block >= 1 (<= 64), lb_batch_step advances every instance
+ * through runs of 32 steps, each run ONE cooperative launch of a fixed grid
+ * (at most the blocks that fit on the GPU at once) replayed from a captured
+ * CUDA graph, and the rest of the steps in one more launch. The instances
+ * are cut into tiles (a block's two column strips x a segment of rows;
+ * with seg_rows 0 the segments give about tiles_per_block tiles per block),
+ * the tiles are dealt out to the blocks (longest first to the least loaded
+ * block), and a tile starts a step once every tile of its instance has
+ * finished the previous one. Results are bit-identical to stepping each
+ * instance alone with the same block size. Each of those waits polls a
+ * device counter at most wait_limit times (<= 0: the default, about 1-2
+ * seconds); a wait that runs out ends its block and latches LB_E_TIMEOUT,
+ * which lb_batch_sync and lb_batch_heat_flux report (the instances are then
+ * only partly advanced and must be reset). */
+int lb_batch_set_persistent(lb_batch* b, int tiles_per_block, long long wait_limit);
+
 /* Per-instance heat-flux statistics into arrays of n entries (any may be
  * NULL); see lb_heat_flux. Synchronises. */
 int lb_batch_heat_flux(lb_batch* b, double* q_inst, double* q_mean, double* q_std,
@@ -259,7 +277,8 @@ int lb_batch_fields(lb_batch* b, int i, float* rho, float* ux, float* uy, float*
 int lb_batch_set_wall_temperature(lb_batch* b, int i, const double* Tb_profile, double superheat);
 int lb_batch_set_wettability(lb_batch* b, int i, double Gw);
 
-/* Steps taken, block size and blocks per launch. */
+/* Steps taken, block size and blocks per launch (the persistent grid in
+ * persistent mode). */
 int lb_batch_info(lb_batch* b, int64_t* steps, int* block_x, int* nblocks);
 
 /* Wait and report latched device faults of any instance. */

@@ -19,7 +19,7 @@ constexpr int TRING = 8;   // rows kept of theta^t
 constexpr int SM_ROWS = 7 * RING + TRING;  // psi rho vx vy u2 u3 u4 + theta
 
 enum { BC_WALLS = 0, BC_TOP_OUTFLOW = 1, BC_PERIODIC = 2 };
-enum : unsigned { ERR_EOS = 1u, ERR_NONFINITE = 2u, ERR_BOUNDS = 4u };
+enum : unsigned { ERR_EOS = 1u, ERR_NONFINITE = 2u, ERR_BOUNDS = 4u, ERR_TIMEOUT = 8u };
 
 // FP64 device accumulators (wall heat flux of Sec. 3.2, mass, fault flags).
 struct Acc {
@@ -107,10 +107,23 @@ __device__ __forceinline__ float lb_ldg(const float* p, const float* base, size_
 __device__ __forceinline__ void lb_st(float* p, float v, const float* base, size_t n, Acc* acc) {
     if (lb_inside(p, base, n * sizeof(float), sizeof(float), acc)) *p = v;
 }
+__device__ __forceinline__ float lb_ldcg(const float* p, const float* base, size_t n, Acc* acc) {
+    return lb_inside(p, base, n * sizeof(float), sizeof(float), acc) ? __ldcg(p) : 0.f;
+}
 #else
 __device__ __forceinline__ float lb_ldg(const float* p, const float*, size_t, Acc*) { return __ldg(p); }
+__device__ __forceinline__ float lb_ldcg(const float* p, const float*, size_t, Acc*) { return __ldcg(p); }
 __device__ __forceinline__ void lb_st(float* p, float v, const float*, size_t, Acc*) { *p = v; }
 #endif
+// Loads of the step's input state: through the read-only path in a kernel
+// that runs one step (lb_ldg), at L2 (lb_ldcg, bypassing the SM's L1, which
+// is not kept coherent with other SMs' writes) in the persistent batch, where
+// other blocks rewrite the buffers during the launch.
+template <bool CG>
+__device__ __forceinline__ float lb_ld(const float* p, const float* base, size_t n, Acc* acc) {
+    if constexpr (CG) return lb_ldcg(p, base, n, acc);
+    else return lb_ldg(p, base, n, acc);
+}
 
 // psi(rho, T) = sqrt(2 (p_EOS - rho c_s^2) / G), c = 1 (Sec. 2 and Eq. 21).
 __device__ __forceinline__ float eos_psi(float rho, float T, const StepParams& P, bool& bad) {

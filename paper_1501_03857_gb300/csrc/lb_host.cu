@@ -345,6 +345,9 @@ int report_device_errors(lb_handle* h, unsigned err) {
     const unsigned z = 0;
     LB_CUDA(cudaMemcpy(&h->acc->err, &z, sizeof(unsigned), cudaMemcpyHostToDevice), "clear error flags");
     if (err & ERR_BOUNDS) return fail(LB_E_BOUNDS, "a device index left its buffer (checked build)");
+    if (err & ERR_TIMEOUT)
+        return fail(LB_E_TIMEOUT, "a wait of the persistent batch step gave up (its wait limit); the instances' "
+                                  "states are only partly advanced");
     if (err & ERR_NONFINITE) return fail(LB_E_NONFINITE, "non-finite density or temperature on the device");
     if (err & ERR_EOS) return fail(LB_E_EOS_DOMAIN, "pseudopotential argument 2(p - rho/3)/G < 0 (EOS domain)");
     return LB_OK;
@@ -931,11 +934,26 @@ struct lb_batch {
     cudaGraphExec_t graph;       // GRAPH_STEPS steps starting at parity 0
     bool kshared;                // all instances share the model constants
     StepParams kconst;           // ... which are these (instance 0's parameters)
+    // persistent mode (tpb > 0): one cooperative launch per run of steps, a
+    // grid of at most one wave, about tpb tiles per block
+    int tpb;
+    unsigned long long wait_limit;
+    int max_tiles;               // capacity of the tile arrays
+    int2* d_tiles;               // device [max_tiles]: (instance, block index)
+    int* d_tile_off;             // device [max_tiles + 1]: first tile of each block
+    int* d_ntiles;               // device [n]
+    unsigned* d_arrive;          // device [n]
+    std::vector<int2> h_tiles;
+    std::vector<int> h_tile_off, h_ntiles;
+    int pgrid;                   // blocks of the persistent launch
+    cudaGraphExec_t pgraph;      // PERSIST_STEPS steps in one launch
 };
 
 namespace {
 
 constexpr int GRAPH_STEPS = 32;  // steps per captured graph (even: parity returns)
+constexpr int PERSIST_STEPS = 32;  // steps per persistent launch in the captured graph (even)
+constexpr unsigned long long PERSIST_WAIT_DEFAULT = 1ull << 24;  // polls (64 ns sleeps): about 1-2 s
 
 size_t batch_tail_offset(const lb_batch_desc* d, int n, std::vector<size_t>* offs) {
     size_t off = 0;
@@ -944,6 +962,33 @@ size_t batch_tail_offset(const lb_batch_desc* d, int n, std::vector<size_t>* off
         off += layout(&d[i].grid).total;
     }
     return off;
+}
+
+// Most tiles a batch can have: the 64-thread blocks' strips (the narrowest)
+// and segments of one row.
+long long batch_max_tiles(const lb_batch_desc* d, int n) {
+    long long t = 0;
+    for (int i = 0; i < n; ++i)
+        t += (long long)((d[i].grid.Lx + MIN_STRIP_COLS - 1) / MIN_STRIP_COLS) * d[i].grid.Ly;
+    return t;
+}
+
+// Byte offsets of the batch's device arrays after the instances' workspaces.
+struct BatchTail {
+    size_t table, block_off, tiles, tile_off, ntiles, arrive, total;
+};
+
+BatchTail batch_tail(const lb_batch_desc* d, int n) {
+    BatchTail T;
+    const long long mt = batch_max_tiles(d, n);
+    T.table = align256(batch_tail_offset(d, n, nullptr));
+    T.block_off = align256(T.table + 2 * n * sizeof(StepParams));
+    T.tiles = align256(T.block_off + (n + 1) * sizeof(int));
+    T.tile_off = align256(T.tiles + (size_t)mt * sizeof(int2));
+    T.ntiles = align256(T.tile_off + (size_t)(mt + 1) * sizeof(int));
+    T.arrive = align256(T.ntiles + n * sizeof(int));
+    T.total = align256(T.arrive + n * sizeof(unsigned));
+    return T;
 }
 
 // The model constants the step reads from K (step_body, lb_step3.cu): the
@@ -966,15 +1011,18 @@ void batch_constants(lb_batch* b) {
 
 // Common block size, per-instance segment height and block offsets. With an
 // automatic segment height every instance gets a share of one full wave
-// proportional to its cells.
+// proportional to its cells (tpb waves' worth in the persistent mode, whose
+// grid is one wave that takes about tpb tiles per block).
 int batch_layout(lb_batch* b) {
     const int n = (int)b->inst.size();
     int dev = 0, nsm = 0, occ = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     batch_constants(b);
-    LB_CUDA(batch_occupancy(b->block_x, b->kshared, &occ), "occupancy");
+    if (b->tpb > 0) LB_CUDA(persist_occupancy(b->block_x, b->kshared, &occ), "occupancy");
+    else LB_CUDA(batch_occupancy(b->block_x, b->kshared, &occ), "occupancy");
     if (occ < 1) return fail(LB_E_INVAL, "batch block_x %d does not fit on an SM", b->block_x);
+    const int waves = std::max(1, b->tpb);
     const int nout = b->block_x - 2 * HALO;
     long long cells = 0;
     for (lb_handle* h : b->inst) cells += (long long)h->grid.Lx * h->grid.Ly;
@@ -985,7 +1033,7 @@ int batch_layout(lb_batch* b) {
         int seg = b->seg_req;
         if (seg <= 0) {
             const double share = (double)h->grid.Lx * h->grid.Ly / (double)cells;
-            const int nseg = std::max(1, (int)(share * nsm * occ / nstrips));
+            const int nseg = std::max(1, (int)(share * nsm * occ * waves / nstrips));
             seg = std::max(8, (h->grid.Ly + nseg - 1) / nseg);
         }
         h->launch.block_x = b->block_x;
@@ -1002,8 +1050,65 @@ int batch_layout(lb_batch* b) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
+    if (b->pgraph) {
+        cudaGraphExecDestroy(b->pgraph);
+        b->pgraph = nullptr;
+    }
     LB_CUDA(cudaMemcpyAsync(b->block_off, b->h_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->st),
             "batch offsets upload");
+    if (b->tpb > 0) {
+        // Deal the tiles out to a grid of at most one wave, longest first to
+        // the least loaded block (a tile costs its rows plus the pipeline's
+        // 10 rows of halo); each block then takes its tiles in (instance,
+        // tile) order, the same order on every block.
+        const int ntile = b->nblocks;
+        if (ntile > b->max_tiles) return fail(LB_E_INVAL, "batch has %d tiles, more than the %d provided for", ntile, b->max_tiles);
+        const int G = std::min(ntile, nsm * occ);
+        std::vector<std::pair<int, int>> order;  // (cost, tile)
+        std::vector<int2> tiles(ntile);
+        b->h_ntiles.assign(n, 0);
+        for (int i = 0; i < n; ++i) {
+            lb_handle* h = b->inst[i];
+            const int nt = b->h_off[i + 1] - b->h_off[i];
+            b->h_ntiles[i] = nt;
+            for (int k = 0; k < nt; ++k) {
+                const int seg = k / h->launch.nstrips;
+                const int rows = std::min(h->launch.seg_rows, h->grid.Ly - seg * h->launch.seg_rows);
+                tiles[b->h_off[i] + k] = make_int2(i, k);
+                order.push_back({rows + 2 * HALO, b->h_off[i] + k});
+            }
+        }
+        std::stable_sort(order.begin(), order.end(), [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+            return x.first > y.first;
+        });
+        std::vector<long long> load(G, 0);
+        std::vector<std::vector<int>> mine(G);
+        std::vector<std::pair<long long, int>> heap;  // (load, block), a min-heap
+        for (int g = 0; g < G; ++g) heap.push_back({0, g});
+        auto cmp = [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) { return x > y; };
+        for (const auto& o : order) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto& top = heap.back();
+            top.first += o.first;
+            mine[top.second].push_back(o.second);
+            std::push_heap(heap.begin(), heap.end(), cmp);
+        }
+        b->h_tiles.clear();
+        b->h_tile_off.assign(1, 0);
+        for (int g = 0; g < G; ++g) {
+            std::sort(mine[g].begin(), mine[g].end());  // tile ids are ordered by (instance, tile)
+            for (int t : mine[g]) b->h_tiles.push_back(tiles[t]);
+            b->h_tile_off.push_back((int)b->h_tiles.size());
+        }
+        b->pgrid = G;
+        LB_CUDA(cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), ntile * sizeof(int2), cudaMemcpyHostToDevice, b->st),
+                "tiles upload");
+        LB_CUDA(cudaMemcpyAsync(b->d_tile_off, b->h_tile_off.data(), (G + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                                b->st),
+                "tile offsets upload");
+        LB_CUDA(cudaMemcpyAsync(b->d_ntiles, b->h_ntiles.data(), n * sizeof(int), cudaMemcpyHostToDevice, b->st),
+                "tile counts upload");
+    }
     b->dirty = true;
     return LB_OK;
 }
@@ -1040,6 +1145,42 @@ int batch_launch_one(lb_batch* b, cudaStream_t s, int parity) {
     return LB_OK;
 }
 
+// One persistent launch of `nsteps` steps (the arrival counters zeroed first).
+int persist_launch_one(lb_batch* b, cudaStream_t s, int nsteps) {
+    const int n = (int)b->inst.size();
+    PersistArgs A;
+    A.table = b->table;
+    A.tiles = b->d_tiles;
+    A.tile_off = b->d_tile_off;
+    A.ntiles = b->d_ntiles;
+    A.arrive = b->d_arrive;
+    A.n = n;
+    A.nsteps = nsteps;
+    A.wait_limit = b->wait_limit;
+    LB_CUDA(cudaMemsetAsync(b->d_arrive, 0, n * sizeof(unsigned), s), "clear arrival counters");
+    LB_CUDA(persist_launch(b->block_x, b->kshared ? &b->kconst : nullptr, A, b->pgrid, s), "persistent batch launch");
+    return LB_OK;
+}
+
+int persist_graph(lb_batch* b, cudaGraphExec_t* out) {
+    if (!b->pgraph) {
+        cudaGraph_t g = nullptr;
+        LB_CUDA(cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int rc = persist_launch_one(b, b->gs, PERSIST_STEPS);
+        cudaError_t e = cudaStreamEndCapture(b->gs, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&b->pgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    }
+    *out = b->pgraph;
+    return LB_OK;
+}
+
 int batch_graph(lb_batch* b, cudaGraphExec_t* out) {
     if (!b->graph) {
         cudaGraph_t g = nullptr;
@@ -1065,6 +1206,7 @@ void batch_release(lb_batch* b) {
     if (b->st) cudaStreamSynchronize(b->st);
     if (b->gs) cudaStreamSynchronize(b->gs);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->gs) cudaStreamDestroy(b->gs);
@@ -1080,9 +1222,7 @@ int lb_batch_workspace_bytes(const lb_batch_desc* d, int n, size_t* bytes) {
     if (!d || n < 1 || !bytes) return fail(LB_E_INVAL, "need n >= 1 descriptors and an output");
     for (int i = 0; i < n; ++i)
         if (d[i].grid.Lx < 1 || d[i].grid.Ly < 3) return fail(LB_E_INVAL, "instance %d: grid too small", i);
-    size_t off = batch_tail_offset(d, n, nullptr);
-    off = align256(off) + align256(2 * n * sizeof(StepParams)) + align256((n + 1) * sizeof(int));
-    *bytes = off;
+    *bytes = batch_tail(d, n).total;
     return LB_OK;
 }
 
@@ -1107,6 +1247,13 @@ int lb_batch_init(lb_batch** out, const lb_batch_desc* d, int n, void* dev_works
     b->block_x = 128;
     b->seg_req = 0;
     b->dirty = true;
+    b->tpb = 0;
+    b->wait_limit = PERSIST_WAIT_DEFAULT;
+    b->pgrid = 0;
+    b->pgraph = nullptr;
+    b->d_tiles = nullptr;
+    b->d_tile_off = b->d_ntiles = nullptr;
+    b->d_arrive = nullptr;
     char* ws = (char*)dev_workspace;
     const size_t tail = batch_tail_offset(d, n, &b->ws_off);
     for (int i = 0; i < n; ++i) {
@@ -1120,8 +1267,15 @@ int lb_batch_init(lb_batch** out, const lb_batch_desc* d, int n, void* dev_works
         }
         b->inst.push_back(h);
     }
-    b->table = (StepParams*)(ws + align256(tail));
-    b->block_off = (int*)(ws + align256(tail) + align256(2 * n * sizeof(StepParams)));
+    const BatchTail T = batch_tail(d, n);
+    (void)tail;
+    b->table = (StepParams*)(ws + T.table);
+    b->block_off = (int*)(ws + T.block_off);
+    b->d_tiles = (int2*)(ws + T.tiles);
+    b->d_tile_off = (int*)(ws + T.tile_off);
+    b->d_ntiles = (int*)(ws + T.ntiles);
+    b->d_arrive = (unsigned*)(ws + T.arrive);
+    b->max_tiles = (int)std::min<long long>(batch_max_tiles(d, n), INT32_MAX);
     cudaError_t e = batch_prepare();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
@@ -1150,12 +1304,36 @@ int lb_batch_set_launch(lb_batch* b, int block_x, int seg_rows) {
     return batch_layout(b);
 }
 
+int lb_batch_set_persistent(lb_batch* b, int tiles_per_block, long long wait_limit) {
+    if (!b) return fail(LB_E_INVAL, "null batch");
+    if (tiles_per_block < 0 || tiles_per_block > 64) return fail(LB_E_INVAL, "tiles_per_block must be in 0..64");
+    b->tpb = tiles_per_block;
+    b->wait_limit = wait_limit > 0 ? (unsigned long long)wait_limit : PERSIST_WAIT_DEFAULT;
+    return batch_layout(b);
+}
+
 int lb_batch_step(lb_batch* b, int nsteps) {
     if (!b) return fail(LB_E_INVAL, "null batch");
     if (nsteps < 0) return fail(LB_E_INVAL, "nsteps must be >= 0");
     int rc = batch_upload(b);
     if (rc) return rc;
     int left = nsteps, parity = 0;
+    if (b->tpb > 0) {
+        // runs of PERSIST_STEPS steps: one persistent launch each, replayed
+        // from a captured graph on the private stream; the rest in one launch
+        if (left >= PERSIST_STEPS) {
+            cudaGraphExec_t g = nullptr;
+            rc = persist_graph(b, &g);
+            if (rc) return rc;
+            LB_CUDA(cudaEventRecord(b->ev_in, b->st), "cudaEventRecord");
+            LB_CUDA(cudaStreamWaitEvent(b->gs, b->ev_in, 0), "cudaStreamWaitEvent");
+            for (; left >= PERSIST_STEPS; left -= PERSIST_STEPS) LB_CUDA(cudaGraphLaunch(g, b->gs), "cudaGraphLaunch");
+            LB_CUDA(cudaEventRecord(b->ev_out, b->gs), "cudaEventRecord");
+            LB_CUDA(cudaStreamWaitEvent(b->st, b->ev_out, 0), "cudaStreamWaitEvent");
+        }
+        if (left > 0 && (rc = persist_launch_one(b, b->st, left))) return rc;
+        left = 0;
+    }
     if (left >= GRAPH_STEPS) {
         // whole chunks as a captured graph on the private stream, ordered
         // after and before the caller's stream
@@ -1181,14 +1359,22 @@ int lb_batch_step(lb_batch* b, int nsteps) {
     return LB_OK;
 }
 
+// Every instance is read (and its fault flags cleared); the first failure
+// is returned.
 int lb_batch_heat_flux(lb_batch* b, double* q_inst, double* q_mean, double* q_std, int64_t* nsamples, int reset) {
     if (!b) return fail(LB_E_INVAL, "null batch");
+    int first = LB_OK;
+    std::string msg;
     for (size_t i = 0; i < b->inst.size(); ++i) {
         int rc = lb_heat_flux(b->inst[i], q_inst ? q_inst + i : nullptr, q_mean ? q_mean + i : nullptr,
                               q_std ? q_std + i : nullptr, nsamples ? nsamples + i : nullptr, reset);
-        if (rc) return rc;
+        if (rc && first == LB_OK) {
+            first = rc;
+            msg = g_err;
+        }
     }
-    return LB_OK;
+    if (first) g_err = msg;
+    return first;
 }
 
 int lb_batch_get_state(lb_batch* b, int i, float* fpost, float* theta, int on_device) {
@@ -1222,17 +1408,23 @@ int lb_batch_info(lb_batch* b, int64_t* steps, int* block_x, int* nblocks) {
     if (!b) return fail(LB_E_INVAL, "null batch");
     if (steps) *steps = b->steps;
     if (block_x) *block_x = b->block_x;
-    if (nblocks) *nblocks = b->nblocks;
+    if (nblocks) *nblocks = b->tpb > 0 ? b->pgrid : b->nblocks;
     return LB_OK;
 }
 
 int lb_batch_sync(lb_batch* b) {
     if (!b) return fail(LB_E_INVAL, "null batch");
+    int first = LB_OK;
+    std::string msg;
     for (lb_handle* h : b->inst) {
         int rc = check_device_errors(h);
-        if (rc) return rc;
+        if (rc && first == LB_OK) {
+            first = rc;
+            msg = g_err;
+        }
     }
-    return LB_OK;
+    if (first) g_err = msg;
+    return first;
 }
 
 int lb_batch_destroy(lb_batch* b) {

@@ -46,6 +46,26 @@ cudaError_t batch_occupancy(int block_x, bool shared_k, int* blocks_per_sm);
 cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,
                          const StepParams* K, cudaStream_t st);
 
+// The persistent batch (lb_batch_persist in lb_step3.cu): one cooperative
+// launch of a fixed grid advances every instance by nsteps steps; block g
+// takes tiles tile_off[g] .. tile_off[g+1]-1 (instance, block index within
+// the instance) every step, after all tiles of the instance finished the
+// previous step (arrive[i] counts finished tiles of instance i since the
+// launch began and must be zero at launch). A wait gives up after
+// wait_limit polls, sets ERR_TIMEOUT in the instance's fault flags and ends
+// the block.
+struct PersistArgs {
+    const StepParams* table;  // [2][n], by step parity
+    const int2* tiles;
+    const int* tile_off;
+    const int* ntiles;        // [n] tiles per instance
+    unsigned* arrive;         // [n]
+    int n, nsteps;
+    unsigned long long wait_limit;
+};
+cudaError_t persist_occupancy(int block_x, bool shared_k, int* blocks_per_sm);
+cudaError_t persist_launch(int block_x, const StepParams* K, const PersistArgs& A, int nblocks, cudaStream_t st);
+
 // Initial state: f* = w_a rho0 (rest equilibrium), theta = 0 with the wall
 // rows at their Dirichlet values. rho0 is pitched [Ly][pitch].
 cudaError_t launch_init(const StepParams& P, const float* rho0, float* f, float* th, cudaStream_t st);

@@ -80,7 +80,7 @@ __device__ __forceinline__ int wrap_row(int v, int n) {
 // Pulled populations (Eq. 3: f_a(x) = f*_a(x - e_a)) and theta of row y for
 // the two columns; sources beyond a wall read 0 (filled by Zou-He), with the
 // outflow top the source row is clamped to the top row.
-template <class T>
+template <class T, bool CG>
 __device__ __forceinline__ void load_row2(const StepParams& P, int y, int xa, int xam, int xap, int xb, int xbm,
                                           int xbp, T (&f)[9], T& th) {
     const float* __restrict__ F = P.f_in;
@@ -101,25 +101,25 @@ __device__ __forceinline__ void load_row2(const StepParams& P, int y, int xa, in
     const float* Rc = F + y * pitch;
     const float* Rm = F + ym * pitch;
     const float* Rp = F + yp * pitch;
-    f[0] = T(lb_ldg(Rc + xa, F, nF, P.acc), lb_ldg(Rc + xb, F, nF, P.acc));
-    f[1] = T(lb_ldg(Rc + pl + xam, F, nF, P.acc), lb_ldg(Rc + pl + xbm, F, nF, P.acc));
-    f[3] = T(lb_ldg(Rc + 3 * pl + xap, F, nF, P.acc), lb_ldg(Rc + 3 * pl + xbp, F, nF, P.acc));
+    f[0] = T(lb_ld<CG>(Rc + xa, F, nF, P.acc), lb_ld<CG>(Rc + xb, F, nF, P.acc));
+    f[1] = T(lb_ld<CG>(Rc + pl + xam, F, nF, P.acc), lb_ld<CG>(Rc + pl + xbm, F, nF, P.acc));
+    f[3] = T(lb_ld<CG>(Rc + 3 * pl + xap, F, nF, P.acc), lb_ld<CG>(Rc + 3 * pl + xbp, F, nF, P.acc));
     if (okm) {
-        f[2] = T(lb_ldg(Rm + 2 * pl + xa, F, nF, P.acc), lb_ldg(Rm + 2 * pl + xb, F, nF, P.acc));
-        f[5] = T(lb_ldg(Rm + 5 * pl + xam, F, nF, P.acc), lb_ldg(Rm + 5 * pl + xbm, F, nF, P.acc));
-        f[6] = T(lb_ldg(Rm + 6 * pl + xap, F, nF, P.acc), lb_ldg(Rm + 6 * pl + xbp, F, nF, P.acc));
+        f[2] = T(lb_ld<CG>(Rm + 2 * pl + xa, F, nF, P.acc), lb_ld<CG>(Rm + 2 * pl + xb, F, nF, P.acc));
+        f[5] = T(lb_ld<CG>(Rm + 5 * pl + xam, F, nF, P.acc), lb_ld<CG>(Rm + 5 * pl + xbm, F, nF, P.acc));
+        f[6] = T(lb_ld<CG>(Rm + 6 * pl + xap, F, nF, P.acc), lb_ld<CG>(Rm + 6 * pl + xbp, F, nF, P.acc));
     } else {
         f[2] = f[5] = f[6] = T::bc(0.f);
     }
     if (okp) {
-        f[4] = T(lb_ldg(Rp + 4 * pl + xa, F, nF, P.acc), lb_ldg(Rp + 4 * pl + xb, F, nF, P.acc));
-        f[7] = T(lb_ldg(Rp + 7 * pl + xap, F, nF, P.acc), lb_ldg(Rp + 7 * pl + xbp, F, nF, P.acc));
-        f[8] = T(lb_ldg(Rp + 8 * pl + xam, F, nF, P.acc), lb_ldg(Rp + 8 * pl + xbm, F, nF, P.acc));
+        f[4] = T(lb_ld<CG>(Rp + 4 * pl + xa, F, nF, P.acc), lb_ld<CG>(Rp + 4 * pl + xb, F, nF, P.acc));
+        f[7] = T(lb_ld<CG>(Rp + 7 * pl + xap, F, nF, P.acc), lb_ld<CG>(Rp + 7 * pl + xbp, F, nF, P.acc));
+        f[8] = T(lb_ld<CG>(Rp + 8 * pl + xam, F, nF, P.acc), lb_ld<CG>(Rp + 8 * pl + xbm, F, nF, P.acc));
     } else {
         f[4] = f[7] = f[8] = T::bc(0.f);
     }
     const float* Tc = P.th_in + y * pitch;
-    th = T(lb_ldg(Tc + xa, P.th_in, (size_t)pl, P.acc), lb_ldg(Tc + xb, P.th_in, (size_t)pl, P.acc));
+    th = T(lb_ld<CG>(Tc + xa, P.th_in, (size_t)pl, P.acc), lb_ld<CG>(Tc + xb, P.th_in, (size_t)pl, P.acc));
 }
 
 // Isotropic central differences (Lee and Lin; Sec. 2 after Eq. 20) at
@@ -260,7 +260,7 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
 // writes the forward intermediates of its own cells to R instead of the
 // collided populations, theta^{t+1} and the heat flux (RecomputeOut,
 // lb_internal.h).
-template <int BD, class T, bool REC = false>
+template <int BD, class T, bool REC = false, bool CG = false>
 __device__ __forceinline__ void step_body(const StepParams& P, const StepParams& K, const int block,
                                           const RecomputeOut* R = nullptr) {
     constexpr int W = BD + 2;
@@ -332,7 +332,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
     const T zero = T::bc(0.f);
 
     T fc[9], tc = zero;
-    if (loP < hiP) load_row2(P, wrap_row(loP, Ly), xa, xam, xap, xb, xbm, xbp, fc, tc);
+    if (loP < hiP) load_row2<T, CG>(P, wrap_row(loP, Ly), xa, xam, xap, xb, xbm, xbp, fc, tc);
     T fP[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) fP[a] = zero;
@@ -358,7 +358,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
         // and their latency shows up as long-scoreboard stalls, 1.3 cycles
         // per issued instruction instead of 0.2)
         if (L + 1 < hiP) {
-            load_row2(P, yN, xa, xam, xap, xb, xbm, xbp, fn, tn);
+            load_row2<T, CG>(P, yN, xa, xam, xap, xb, xbm, xbp, fn, tn);
         } else {
 #pragma unroll
             for (int a = 0; a < 9; ++a) fn[a] = zero;
@@ -650,13 +650,15 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
             if (lc == 0) {
+                // the sums are read and written at L2: in the persistent
+                // batch another SM may hold an old copy of them in its L1
                 Acc* A = P.acc;
                 const double qt = tot / (double)Lx;
-                A->q_last = qt;
-                A->q_sum += qt;
-                A->q_sum2 += qt * qt;
-                A->q_n += 1.0;
-                A->count = 0u;
+                __stcg(&A->q_last, qt);
+                __stcg(&A->q_sum, __ldcg(&A->q_sum) + qt);
+                __stcg(&A->q_sum2, __ldcg(&A->q_sum2) + qt * qt);
+                __stcg(&A->q_n, __ldcg(&A->q_n) + 1.0);
+                atomicExch(&A->count, 0u);
             }
         }
     }
@@ -741,6 +743,68 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_batch_k(const StepParams K, 
     step_body<BD, T>(sP, K, b);
 }
 
+// ---------------------------------------------------------------------------
+// The persistent batch: one launch advances every instance by `nsteps` steps.
+//
+// The instances' tiles (a pair of column strips x a segment of rows, the
+// unit one block of the per-step kernel computes) are dealt out to a fixed,
+// co-resident grid (a cooperative launch); block g takes tiles
+// tile_off[g] .. tile_off[g+1]-1 in that order, step after step. A tile may
+// start step k once every tile of its instance has finished step k-1:
+// its pulled rows and the strips beside it are then complete (read after
+// write), and no tile of the instance still reads the buffer step k writes
+// (write after read). arrive[i] counts the tiles of instance i that have
+// finished a step since the launch began (zeroed before each launch), so
+// the wait is arrive[i] >= k * ntiles[i]. The wait spins at most
+// `wait_limit` polls (with a short sleep between them); a block that gives
+// up sets ERR_TIMEOUT in its instance's fault flags and leaves the kernel,
+// which lets every block waiting on it give up in turn, so the launch always
+// ends. The step's input state is loaded at L2 (other SMs rewrite it during
+// the launch), and every tile runs the same step body as the per-step
+// kernel, so results are bit-identical to it.
+// ---------------------------------------------------------------------------
+
+// Poll *p until it reaches `target`, at most `limit` times; true if reached.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target, unsigned long long limit) {
+    for (unsigned long long it = 0;; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+        if (v >= target) return true;
+        if (it >= limit) return false;
+        __nanosleep(64);
+    }
+}
+
+template <int BD, int MINB, bool SK>
+__global__ void __launch_bounds__(BD, MINB) lb_batch_persist(const StepParams K, const PersistArgs A) {
+    __shared__ StepParams sP;
+    __shared__ bool s_go;
+    const int t0 = A.tile_off[blockIdx.x], t1 = A.tile_off[blockIdx.x + 1];
+    for (int k = 0; k < A.nsteps; ++k) {
+        for (int t = t0; t < t1; ++t) {
+            const int2 tl = A.tiles[t];
+            const int inst = tl.x;
+            if (threadIdx.x == 0) {
+                s_go = k == 0 || wait_at_least(A.arrive + inst, (unsigned)k * (unsigned)A.ntiles[inst], A.wait_limit);
+                if (!s_go) atomicOr(&A.table[inst].acc->err, ERR_TIMEOUT);
+            }
+            constexpr int NW = (int)(sizeof(StepParams) / sizeof(int));
+            __syncthreads();
+            if (!s_go) return;
+            const StepParams* src = A.table + (k & 1) * A.n + inst;
+            for (int w = threadIdx.x; w < NW; w += BD)
+                reinterpret_cast<int*>(&sP)[w] = __ldg(reinterpret_cast<const int*>(src) + w);
+            __syncthreads();
+            step_body<BD, P2, false, true>(sP, SK ? K : sP, tl.y);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(A.arrive + inst, 1u);
+            }
+        }
+    }
+}
+
 namespace {
 
 // blocks per SM the shared-constant batch kernel is compiled for
@@ -783,6 +847,31 @@ struct DualKernel {
         lb_step_batch_k<BD, MINB, T><<<nblocks, BD, smem(), st>>>(K, table, off, n);
         return cudaGetLastError();
     }
+    template <bool SK>
+    static cudaError_t prepare_persist() {
+        return cudaFuncSetAttribute(lb_batch_persist<BD, MINB, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem());
+    }
+    template <bool SK>
+    static cudaError_t occupancy_persist(int* n) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, lb_batch_persist<BD, MINB, SK>, BD, smem());
+    }
+    // a cooperative launch: the runtime refuses it unless every block can be
+    // resident at once, which the blocks' waits on one another need
+    template <bool SK>
+    static cudaError_t launch_persist(const StepParams& K, const PersistArgs& A, int nblocks, cudaStream_t st) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nblocks);
+        cfg.blockDim = dim3(BD);
+        cfg.dynamicSmemBytes = smem();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, lb_batch_persist<BD, MINB, SK>, K, A);
+    }
 };
 
 // the instantiations a launch can pick: (block size, paired FP32 or scalar).
@@ -807,6 +896,10 @@ cudaError_t batch_prepare_t() {
     if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_batch();
     if (e == cudaSuccess) e = DualKernel<64, BATCH_K_MINB64, P2>::prepare_batch_k();
     if (e == cudaSuccess) e = DualKernel<128, BATCH_K_MINB128, P2>::prepare_batch_k();
+    if (e == cudaSuccess) e = DualKernel<64, 8, P2>::prepare_persist<true>();
+    if (e == cudaSuccess) e = DualKernel<64, 8, P2>::prepare_persist<false>();
+    if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_persist<true>();
+    if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_persist<false>();
     return e;
 }
 
@@ -872,6 +965,21 @@ cudaError_t batch_occupancy(int block_x, bool shared_k, int* n) {
         return block_x == 64 ? DualKernel<64, BATCH_K_MINB64, P2>::occupancy_batch_k(n)
                              : DualKernel<128, BATCH_K_MINB128, P2>::occupancy_batch_k(n);
     return block_x == 64 ? DualKernel<64, 8, P2>::occupancy_batch(n) : DualKernel<128, 4, P2>::occupancy_batch(n);
+}
+
+cudaError_t persist_occupancy(int block_x, bool shared_k, int* n) {
+    if (block_x == 64)
+        return shared_k ? DualKernel<64, 8, P2>::occupancy_persist<true>(n) : DualKernel<64, 8, P2>::occupancy_persist<false>(n);
+    return shared_k ? DualKernel<128, 4, P2>::occupancy_persist<true>(n) : DualKernel<128, 4, P2>::occupancy_persist<false>(n);
+}
+
+cudaError_t persist_launch(int block_x, const StepParams* K, const PersistArgs& A, int nblocks, cudaStream_t st) {
+    const StepParams k0 = K ? *K : StepParams{};
+    if (block_x == 64)
+        return K ? DualKernel<64, 8, P2>::launch_persist<true>(k0, A, nblocks, st)
+                 : DualKernel<64, 8, P2>::launch_persist<false>(k0, A, nblocks, st);
+    return K ? DualKernel<128, 4, P2>::launch_persist<true>(k0, A, nblocks, st)
+             : DualKernel<128, 4, P2>::launch_persist<false>(k0, A, nblocks, st);
 }
 
 cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,

@@ -80,6 +80,7 @@ def _load():
         "lb_batch_init": [C.POINTER(P), C.POINTER(lb_batch_desc), I, P, SZ, P],
         "lb_batch_step": [P, I],
         "lb_batch_set_launch": [P, I, I],
+        "lb_batch_set_persistent": [P, I, C.c_longlong],
         "lb_batch_heat_flux": [P, P, P, P, P, I],
         "lb_batch_get_state": [P, I, FP, FP, I],
         "lb_batch_set_state": [P, I, FP, FP, I],
@@ -425,6 +426,11 @@ class Batch:
 
     def set_launch(self, block_x: int = 128, seg_rows: int = 0):
         check(lib.lb_batch_set_launch(self.h, int(block_x), int(seg_rows)))
+
+    def set_persistent(self, tiles_per_block: int = 2, wait_limit: int = 0):
+        """tiles_per_block >= 1: one cooperative launch per run of 32 steps
+        (lb_batch_set_persistent); 0: one launch per step."""
+        check(lib.lb_batch_set_persistent(self.h, int(tiles_per_block), int(wait_limit)))
 
     def info(self):
         st, bx, nb = C.c_int64(), C.c_int(), C.c_int()

@@ -112,8 +112,118 @@ def test_tune_batch_keeps_state(lb):
     batch = lb.Batch(insts)
     batch.step(4)
     before = [batch.get_state(i) for i in range(2)]
-    bx, seg, ms = tune.tune_batch(batch, candidates=((64, 0), (128, 0)), steps=2)
-    assert bx in (64, 128) and ms > 0
+    bx, seg, ms, tpb = tune.tune_batch(batch, candidates=((64, 0), (128, 0), (64, 0, 2)), steps=2)
+    assert bx in (64, 128) and ms > 0 and tpb in (0, 2)
     after = [batch.get_state(i) for i in range(2)]
     for (f0, t0), (f1, t1) in zip(before, after):
         assert np.array_equal(f0, f1) and np.array_equal(t0, t1)
+
+
+# ---- the persistent batch: one cooperative launch per run of 32 steps ------
+
+@pytest.mark.parametrize("block_x,tpb", [(64, 1), (64, 2), (128, 3)])
+def test_persistent_batch_equals_single_instances(lb, block_x, tpb):
+    """Every instance advanced by the persistent launches (tiles dealt out to
+    one co-resident grid, a tile waiting for its instance's previous step)
+    is bit-identical to the instance stepped alone, heat-flux statistics
+    included, for runs below, at and above the 32 steps of one launch."""
+    insts = make_instances(lb)
+    batch = lb.Batch(insts)
+    batch.set_launch(block_x, 0)
+    batch.set_persistent(tpb)
+    for n in (3, 32, 5, 40):
+        batch.step(n)
+    batch.sync()
+    q = batch.heat_flux()
+    for i, d in enumerate(insts):
+        sim = lb.Simulation(d["cfg"], superheat=d["superheat"], Gw=d["Gw"], rho0=d["rho0"])
+        sim.set_launch(block_x, 0)
+        sim.step(80)
+        fs, ts = sim.get_state()
+        fb, tb = batch.get_state(i)
+        assert np.array_equal(fs, fb) and np.array_equal(ts, tb), i
+        hs = sim.heat_flux()
+        assert q["n"][i] == hs["n"] == 80
+        assert q["q_mean"][i] == hs["q_mean"] and q["q_std"][i] == hs["q_std"]
+        sim.close()
+    batch.close()
+
+
+def test_persistent_batch_with_different_model_constants(lb):
+    """Instances that differ in sigma and gravity take every constant from
+    their own record in the persistent kernel too."""
+    insts = make_instances(lb)[:3]
+    from dataclasses import replace
+    insts[1]["cfg"] = replace(insts[1]["cfg"], sigma=1.1)
+    insts[2]["cfg"] = replace(insts[2]["cfg"], g=2e-5)
+    batch = lb.Batch(insts)
+    batch.set_launch(64, 0)
+    batch.set_persistent(2)
+    batch.step(37)
+    batch.sync()
+    for i, d in enumerate(insts):
+        sim = lb.Simulation(d["cfg"], superheat=d["superheat"], Gw=d["Gw"], rho0=d["rho0"])
+        sim.step(37)
+        fs, ts = sim.get_state()
+        fb, tb = batch.get_state(i)
+        assert np.array_equal(fs, fb) and np.array_equal(ts, tb), i
+        sim.close()
+    batch.close()
+
+
+def test_persistent_wait_limit_reports_timeout_and_recovers(lb):
+    """A wait limit of one poll makes the tiles' waits for the rest of their
+    instance run out: the launch ends, LB_E_TIMEOUT is reported, the context
+    stays usable, and with the default limit and the states reset the batch
+    again equals the single runs."""
+    insts = make_instances(lb)
+    batch = lb.Batch(insts)
+    batch.set_launch(64, 8)  # many tiles per instance
+    init = [batch.get_state(i) for i in range(len(insts))]
+    batch.set_persistent(1, wait_limit=1)
+    batch.step(32)
+    with pytest.raises(lb.LBError) as ei:
+        batch.sync()
+    assert ei.value.code == -5
+    batch.sync()  # reported once, then cleared
+    batch.set_persistent(1)
+    for i, (f0, t0) in enumerate(init):
+        batch.set_state(i, f0, t0)
+    batch.step(33)
+    batch.sync()
+    for i, d in enumerate(insts):
+        sim = lb.Simulation(d["cfg"], superheat=d["superheat"], Gw=d["Gw"], rho0=d["rho0"])
+        sim.step(33)
+        fs, ts = sim.get_state()
+        fb, tb = batch.get_state(i)
+        assert np.array_equal(fs, fb) and np.array_equal(ts, tb), i
+        sim.close()
+    batch.close()
+
+
+@pytest.mark.parametrize("tpb", [0, 2])
+def test_batch_instance_matches_oracle(lb, tpb):
+    """One instance of an uneven batch (one launch per step, and the
+    persistent launch) against the FP64 oracle directly: 40 steps of a
+    heated pool with wettability, within the 1e-5 bound of the parity tests
+    (normalised, and per element for the populations)."""
+    import oracle as O
+    from parity_util import norm_err, oracle_initial_fp32, oracle_params, rel_err, run_oracle, theta_err
+    insts = make_instances(lb)[:3]
+    d = insts[1]
+    cfg = d["cfg"]
+    P = oracle_params(cfg, d["rho0"], superheat=d["superheat"], Gw=d["Gw"])
+    f0, th0 = oracle_initial_fp32(d["rho0"], P)
+    batch = lb.Batch(insts)
+    batch.set_launch(64, 0)
+    batch.set_persistent(tpb)
+    batch.set_state(1, f0, th0)
+    batch.step(40)
+    fb, tb = batch.get_state(1)
+    q = batch.heat_flux()
+    batch.close()
+    fr, tr, qs = run_oracle(f0, th0, P, 40)
+    assert norm_err(fb, fr.numpy()) < 1e-5
+    assert rel_err(fb, fr.numpy()) < 1e-5
+    assert theta_err(tb, tr.numpy(), d["superheat"]) < 1e-5
+    assert abs(q["q_mean"][1] / np.mean(qs) - 1) < 1e-5

@@ -115,9 +115,34 @@ class FakeBatch:
         self.state[i] = (f, th)
 
 
+class FakePersistentBatch(FakeBatch):
+    """A batch with the persistent mode: its cost depends on (bx, seg, tpb)."""
+
+    tpb = 0
+
+    def set_persistent(self, tpb):
+        self.tpb = tpb
+
+    def step(self, n):
+        FakeClock.now += n * self.cost[self.shape + (self.tpb,)]
+        self.state = {i: ("stepped", "stepped") for i in range(self.n)}
+
+
 def test_batch_keeps_fastest_shape_and_restores_every_instance():
     cost = {(64, 0): 0.4, (64, 32): 0.25, (128, 0): 0.3}
     b = FakeBatch(cost)
-    bx, seg, ms = tune.tune_batch(b, candidates=list(cost))
-    assert (bx, seg) == (64, 32) and ms == pytest.approx(0.25) and b.shape == (64, 32)
+    bx, seg, ms, tpb = tune.tune_batch(b, candidates=list(cost))
+    assert (bx, seg, tpb) == (64, 32, 0) and ms == pytest.approx(0.25) and b.shape == (64, 32)
     assert b.state == {i: ("f%d" % i, "t%d" % i) for i in range(3)}
+
+
+def test_batch_picks_the_persistent_mode_when_faster():
+    cost = {(64, 0, 0): 0.4, (64, 0, 2): 0.2, (128, 0, 1): 0.3, (64, 32, 0): 0.35}
+    b = FakePersistentBatch(cost)
+    bx, seg, ms, tpb = tune.tune_batch(b, candidates=list(cost))
+    assert (bx, seg, tpb) == (64, 0, 2) and ms == pytest.approx(0.2)
+    assert b.shape == (64, 0) and b.tpb == 2
+    assert b.state == {i: ("f%d" % i, "t%d" % i) for i in range(3)}
+    # the cached choice is applied again, mode included
+    b.set_persistent(0)
+    assert tune.tune_batch(b, candidates=list(cost))[3] == 2 and b.tpb == 2
