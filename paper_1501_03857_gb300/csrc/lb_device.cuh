@@ -107,21 +107,22 @@ __device__ __forceinline__ float lb_ldg(const float* p, const float* base, size_
 __device__ __forceinline__ void lb_st(float* p, float v, const float* base, size_t n, Acc* acc) {
     if (lb_inside(p, base, n * sizeof(float), sizeof(float), acc)) *p = v;
 }
-__device__ __forceinline__ float lb_ldcg(const float* p, const float* base, size_t n, Acc* acc) {
-    return lb_inside(p, base, n * sizeof(float), sizeof(float), acc) ? __ldcg(p) : 0.f;
+__device__ __forceinline__ float lb_ldco(const float* p, const float* base, size_t n, Acc* acc) {
+    return lb_inside(p, base, n * sizeof(float), sizeof(float), acc) ? *p : 0.f;
 }
 #else
 __device__ __forceinline__ float lb_ldg(const float* p, const float*, size_t, Acc*) { return __ldg(p); }
-__device__ __forceinline__ float lb_ldcg(const float* p, const float*, size_t, Acc*) { return __ldcg(p); }
+__device__ __forceinline__ float lb_ldco(const float* p, const float*, size_t, Acc*) { return *p; }
 __device__ __forceinline__ void lb_st(float* p, float v, const float*, size_t, Acc*) { *p = v; }
 #endif
 // Loads of the step's input state: through the read-only path in a kernel
-// that runs one step (lb_ldg), at L2 (lb_ldcg, bypassing the SM's L1, which
-// is not kept coherent with other SMs' writes) in the persistent batch, where
-// other blocks rewrite the buffers during the launch.
-template <bool CG>
+// that runs one step (lb_ldg), as plain coherent loads (lb_ldco) in the
+// persistent batch, where other blocks rewrite the buffers during the launch:
+// the read-only path may serve data it cached before that; a plain load after
+// the block's acquire of the other blocks' progress sees their writes.
+template <bool CO>
 __device__ __forceinline__ float lb_ld(const float* p, const float* base, size_t n, Acc* acc) {
-    if constexpr (CG) return lb_ldcg(p, base, n, acc);
+    if constexpr (CO) return lb_ldco(p, base, n, acc);
     else return lb_ldg(p, base, n, acc);
 }
 

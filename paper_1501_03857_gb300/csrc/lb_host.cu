@@ -1093,10 +1093,16 @@ int batch_layout(lb_batch* b) {
             mine[top.second].push_back(o.second);
             std::push_heap(heap.begin(), heap.end(), cmp);
         }
+        // blocks in the order of their first tile (for one tile per block,
+        // the order of the per-step launch), so that the costly tiles LPT
+        // dealt out first do not sit on consecutive blocks
+        for (auto& m : mine) std::sort(m.begin(), m.end());  // tile ids are ordered by (instance, tile)
+        std::sort(mine.begin(), mine.end(), [](const std::vector<int>& x, const std::vector<int>& y) {
+            return x.front() < y.front();
+        });
         b->h_tiles.clear();
         b->h_tile_off.assign(1, 0);
         for (int g = 0; g < G; ++g) {
-            std::sort(mine[g].begin(), mine[g].end());  // tile ids are ordered by (instance, tile)
             for (int t : mine[g]) b->h_tiles.push_back(tiles[t]);
             b->h_tile_off.push_back((int)b->h_tiles.size());
         }

@@ -759,9 +759,10 @@ __global__ void __launch_bounds__(BD, MINB) lb_step_batch_k(const StepParams K, 
 // `wait_limit` polls (with a short sleep between them); a block that gives
 // up sets ERR_TIMEOUT in its instance's fault flags and leaves the kernel,
 // which lets every block waiting on it give up in turn, so the launch always
-// ends. The step's input state is loaded at L2 (other SMs rewrite it during
-// the launch), and every tile runs the same step body as the per-step
-// kernel, so results are bit-identical to it.
+// ends. The step's input state is read with plain loads, which after the
+// acquiring wait and the barrier see the other SMs' writes (the read-only
+// path could serve copies cached before them), and every tile runs the same
+// step body as the per-step kernel, so results are bit-identical to it.
 // ---------------------------------------------------------------------------
 
 // Poll *p until it reaches `target`, at most `limit` times; true if reached.
@@ -775,33 +776,96 @@ __device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned target
     }
 }
 
+// The most tiles one block of the persistent batch schedules by readiness
+// (more than this many are taken in order).
+constexpr int PERSIST_MAX_TILES = 64;
+
 template <int BD, int MINB, bool SK>
 __global__ void __launch_bounds__(BD, MINB) lb_batch_persist(const StepParams K, const PersistArgs A) {
     __shared__ StepParams sP;
-    __shared__ bool s_go;
+    __shared__ int s_next[PERSIST_MAX_TILES];  // next step of each of the block's tiles
+    __shared__ int s_pick;
     const int t0 = A.tile_off[blockIdx.x], t1 = A.tile_off[blockIdx.x + 1];
-    for (int k = 0; k < A.nsteps; ++k) {
-        for (int t = t0; t < t1; ++t) {
-            const int2 tl = A.tiles[t];
-            const int inst = tl.x;
-            if (threadIdx.x == 0) {
-                s_go = k == 0 || wait_at_least(A.arrive + inst, (unsigned)k * (unsigned)A.ntiles[inst], A.wait_limit);
-                if (!s_go) atomicOr(&A.table[inst].acc->err, ERR_TIMEOUT);
+    const int m = t1 - t0;
+    const bool by_ready = m <= PERSIST_MAX_TILES;
+    for (int j = threadIdx.x; j < PERSIST_MAX_TILES; j += BD) s_next[j] = 0;
+    __syncthreads();
+    // whether tile j may run its next step: every tile of its instance has
+    // finished the previous one
+    auto ready = [&](int j, int k) {
+        const int inst = A.tiles[t0 + j].x;
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(A.arrive + inst) : "memory");
+        return k == 0 || v >= (unsigned)k * (unsigned)A.ntiles[inst];
+    };
+    int last = m - 1, done_in_order = 0;
+    for (;;) {
+        // thread 0 picks the next tile: with few tiles per block the first
+        // ready one after the last tile run (round robin), so a block never
+        // idles while one of its tiles can go on; otherwise the tiles in
+        // order, step after step. -2: all done; -3: a wait ran out.
+        if (threadIdx.x == 0) {
+            int pick = -2;
+            if (by_ready) {
+                unsigned long long polls = 0;
+                for (;;) {
+                    bool left = false;
+                    pick = -1;
+                    for (int d = 1; d <= m; ++d) {
+                        const int j = (last + d) % m;
+                        if (s_next[j] >= A.nsteps) continue;
+                        left = true;
+                        if (ready(j, s_next[j])) {
+                            pick = j;
+                            break;
+                        }
+                    }
+                    if (!left) {
+                        pick = -2;
+                        break;
+                    }
+                    if (pick >= 0) break;
+                    if (polls++ >= A.wait_limit) {
+                        pick = -3;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            } else if (done_in_order < m * A.nsteps) {
+                const int j = done_in_order % m, k = done_in_order / m;
+                pick = wait_at_least(A.arrive + A.tiles[t0 + j].x, (unsigned)k * (unsigned)A.ntiles[A.tiles[t0 + j].x],
+                                     k == 0 ? 0ull : A.wait_limit) || k == 0 ? j : -3;
+                if (pick >= 0) s_next[0] = k;  // the step to run
             }
-            constexpr int NW = (int)(sizeof(StepParams) / sizeof(int));
-            __syncthreads();
-            if (!s_go) return;
-            const StepParams* src = A.table + (k & 1) * A.n + inst;
-            for (int w = threadIdx.x; w < NW; w += BD)
-                reinterpret_cast<int*>(&sP)[w] = __ldg(reinterpret_cast<const int*>(src) + w);
-            __syncthreads();
-            step_body<BD, P2, false, true>(sP, SK ? K : sP, tl.y);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(A.arrive + inst, 1u);
+            if (pick == -3) {  // latch the timeout on an unfinished tile's instance
+                for (int j = 0; j < m; ++j)
+                    if (!by_ready || s_next[j] < A.nsteps) {
+                        atomicOr(&A.table[A.tiles[t0 + j].x].acc->err, ERR_TIMEOUT);
+                        break;
+                    }
             }
+            s_pick = pick;
         }
+        __syncthreads();
+        const int pick = s_pick;
+        if (pick < 0) return;  // all done, or given up
+        const int k = by_ready ? s_next[pick] : s_next[0];
+        const int2 tl = A.tiles[t0 + pick];
+        const StepParams* src = A.table + (k & 1) * A.n + tl.x;
+        constexpr int NW = (int)(sizeof(StepParams) / sizeof(int));
+        for (int w = threadIdx.x; w < NW; w += BD)
+            reinterpret_cast<int*>(&sP)[w] = __ldg(reinterpret_cast<const int*>(src) + w);
+        __syncthreads();
+        step_body<BD, P2, false, true>(sP, SK ? K : sP, tl.y);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(A.arrive + tl.x, 1u);
+            if (by_ready) ++s_next[pick];
+            else ++done_in_order;
+            last = pick;
+        }
+        __syncthreads();
     }
 }
 

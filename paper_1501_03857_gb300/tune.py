@@ -17,7 +17,7 @@ _CACHE: Dict[tuple, tuple] = {}
 SIM_CANDIDATES = tuple((bx, seg) for bx in (64, 128, 256) for seg in (0, 32, 64, 128, 256))
 # (block_x, seg_rows, tiles per block of the persistent launch; 0: one launch per step)
 BATCH_CANDIDATES = (tuple((bx, seg, 0) for bx in (64, 128) for seg in (0, 16, 32, 64, 128))
-                    + tuple((bx, 0, tpb) for bx in (64, 128) for tpb in (1, 2, 3, 4)))
+                    + tuple((bx, 0, tpb) for bx in (64, 128) for tpb in (1, 2)))
 
 
 def _time(torch, stream, fn, steps: int) -> float:
