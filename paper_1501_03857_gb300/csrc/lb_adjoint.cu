@@ -6,12 +6,13 @@
 // Forward intermediates of step n are recomputed from the stored state
 // (f*^n, theta^n): on large domains by the fused step itself in its
 // recompute mode (lb_step3.cu, RecomputeOut), on small ones by field kernels
-// (one thread per cell) that follow its formulas. The reverse passes (field
-// kernels) then transpose each part of the step in the opposite order:
+// (one thread per cell) that follow its formulas. The reverse passes then
+// transpose each part of the step in the opposite order:
 //
 //   RK4 of Eq. 18 (stage 4 .. 1)   -> lambda_theta, lambda of the per-cell
-//                                     coefficients (ax, ay, cA, cB)
-//   coefficients                   -> lambda_rho, lambda_v (grad rho, div v)
+//   and the coefficients              coefficients (ax, ay, cA, cB), then
+//   (rev_thermal_fused: one           lambda_rho, lambda_v through grad rho
+//   column-marching launch)           and div v
 //   MRT collision (Eqs. 2, 5, 8), v (Eq. 6), forces (Eqs. 7, 9, 22)
 //                                  -> lambda_f, lambda_rho, lambda_psi, lambda_F_m
 //   F_m neighbour sums (Eq. 7), psi (Eq. 21), q_w, rho = sum f
@@ -21,8 +22,10 @@
 //
 // A stencil applied forward as out(x) = sum_d c_d in(x + d) is transposed as
 // a gather lambda_in(y) += sum_d c_d lambda_out(y - d). Fields are pitched
-// [Ly][pitch] FP32; gradients are accumulated in FP64. Supported: walls or
-// periodic in y, no ghost layer (the host checks).
+// [Ly][pitch] FP32; gradients are accumulated in FP64. Supported: walls in
+// y, no ghost layer (the host checks).
+#include <algorithm>
+
 #include "lb_internal.h"
 
 namespace lbgpu {
@@ -92,7 +95,7 @@ struct AdjFields {
     float* lt_out;       // lambda of theta^n
     float* lf;           // lambda of the pulled populations, 9 planes
     float *lrho, *lpsi, *lFmx, *lFmy, *lvx, *lvy, *lth;
-    float *lax, *lay, *lcA, *lcB, *mu, *mu_next, *ldrx, *ldry, *ldivv;
+    float *ldrx, *ldry, *ldivv;
     double* dTb;   // [Lx] dJ/d theta_b accumulators
     double* dGwx;  // [Lx] dJ/dG_w contributions of each column's first fluid row
     double* dGw;   // dJ/dG_w (sum of dGwx, formed at the end)
@@ -262,14 +265,14 @@ __global__ void fwd_stage(const StepParams P, AdjFields A, const float* u_in, fl
 
 // coefficients -> lambda of grad rho, div v (local) and the local parts of
 // lambda_rho, lambda_v, for cell i (after the last stage's accumulation)
-__device__ __forceinline__ void rev_coef_cell(const StepParams& P, const AdjFields& A, int i, bool wall) {
+__device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFields& A, int i, bool wall, float lax,
+                                              float lay, float lcA, float lcB) {
     if (wall) {
         A.ldrx[i] = A.ldry[i] = A.ldivv[i] = 0.f;
         A.lrho[i] = A.lvx[i] = A.lvy[i] = 0.f;
         return;
     }
     const float rho = A.rho[i], irho = rcp_a(rho);
-    const float lax = A.lax[i], lay = A.lay[i], lcA = A.lcA[i], lcB = A.lcB[i];
     const float br = P.b * rho;
     const float i1 = rcp_a(1.f - br);
     const float D = 1.f + 2.f * br - br * br, iD = rcp_a(D);
@@ -284,86 +287,205 @@ __device__ __forceinline__ void rev_coef_cell(const StepParams& P, const AdjFiel
     A.lvy[i] = -lay;
 }
 
-// Transpose of one RK stage h = mask K(u): from mu (= mask lambda_h) compute
-// lambda_u (transposed stencils + the diagonal source term), accumulate the
-// coefficient adjoints and lambda_theta (u = theta + ...), and form the next
-// stage's mu = mask (a lambda-bar + b lambda_u). The first (stage 4) starts
-// the sweep: its mu is lambda-bar / 6 with lambda-bar the incoming
-// lambda_theta on fluid rows, the accumulators start from lambda-bar
-// (identity part of theta' = theta + ...) and 0, and the incoming lambda of
-// the new bottom wall row (its Dirichlet value) goes to dJ/d theta_b.
-__global__ void rev_stage(const StepParams P, AdjFields A, const float* u, float a_bar, float b_u, int first,
-                          int last) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    const bool wall = g.wall(y);
-    auto mu_at = [&](int j, int yj) {
-        return first ? (g.wall(yj) ? 0.f : A.lt_in[j] * (1.f / 6.f)) : A.mu[j];
+// ---- the four RK stages transposed in one column-marching launch ------------
+//
+// Each RK stage of Eq. 18 (stage 4 .. 1) transposed and then the
+// coefficients (rev_coef_vals), cell by cell, in one pass over the domain: a
+// block of RT_BD threads owns RT_BD - 2 RT_HALO output columns and a segment
+// of rows and marches up the segment one row per iteration, each thread one
+// column:
+//
+//   S  row L    : mu4 = lambda_theta'/6 (fluid rows) and its products with
+//                 ax, ay into shared rings; u4, u3 (row L), u2 (row L - 2),
+//                 theta (row L - 3); ax, ay, cA, cB, lambda-bar (own column)
+//   R4 row L-1  : stage 4 transposed (rows L-2..L) -> mu3 and its products
+//   R3 row L-2  : stage 3 transposed -> mu2
+//   R2 row L-3  : stage 2 transposed -> mu1
+//   R1 row L-4  : stage 1 transposed; the cell's coefficient adjoints are
+//                 complete: lambda of grad rho, div v, rho, v, theta out
+//
+// A stage's lambda_u at x gathers c_d(x - d) mu(x - d) over the 9 cells
+// around x, with c_d(s) = ax(s) wx(d) + ay(s) wy(d) + chi wl(d) the
+// isotropic stencils of Sec. 2. With the products PX = ax mu and PY = ay mu
+// stored at the source cell, and the first-derivative weights odd in d,
+// that is lambda_u = -Dx[PX] - Dy[PY] + chi Lap[mu]: the forward stencils
+// applied to the products. Each stage reaches one column further out: 4
+// halo columns per side. The per-cell accumulators (coefficient adjoints,
+// lambda_theta) ride along with their row in registers. Walls in y only
+// (the adjoint's supported case). (Measured: this scalar form with 4 warps
+// per block runs 1.5 x faster than a paired-FP32 form over two strips,
+// whose shared rings allowed only 10 warps per SM.)
+constexpr int RT_BD = 128, RT_HALO = 4, RT_W = RT_BD + 2, RT_R = 4;  // ring rows
+
+__global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, AdjFields A, int seg_h) {
+    extern __shared__ float rt_sm[];
+    float* const sPX = rt_sm;                   // per stage (4, 3, 2, 1 -> 0..3): [4][RT_R][RT_W]
+    float* const sPY = sPX + 4 * RT_R * RT_W;
+    float* const sMU = sPY + 4 * RT_R * RT_W;
+    float* const sU = sMU + 4 * RT_R * RT_W;    // u4, u3, u2, theta: [4][RT_R][RT_W]
+    float* const sOWN = sU + 4 * RT_R * RT_W;   // ax, ay, cA, cB, lambda-bar: [5][RT_R][RT_BD]
+    constexpr int SMN = 16 * RT_R * RT_W + 5 * RT_R * RT_BD;
+    for (int i = threadIdx.x; i < SMN; i += RT_BD) rt_sm[i] = 0.f;
+
+    const int Lx = P.Lx, Ly = P.Ly, pitch = P.pitch;
+    const int nout = RT_BD - 2 * RT_HALO;
+    const int nstrips = (Lx + nout - 1) / nout;
+    const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+    const int lc = threadIdx.x, s = lc + 1;
+    int x = (strip * nout - RT_HALO + lc) % Lx;
+    if (x < 0) x += Lx;
+    const bool out = lc >= RT_HALO && lc < RT_HALO + nout && strip * nout + lc - RT_HALO < Lx;
+    const int ys = seg * seg_h, ye = min(ys + seg_h, Ly);
+    const int lo = max(ys - RT_HALO, 0), hi = min(ye + RT_HALO - 1, Ly - 1);  // rows loaded
+    const float chi = P.chi;
+    auto own = [&](int f, int r) -> float& { return sOWN[(f * RT_R + (r & (RT_R - 1))) * RT_BD + lc]; };
+    auto ring = [&](float* base, int k, int r) { return base + (k * RT_R + (r & (RT_R - 1))) * RT_W + s; };
+    float acc_ax[4], acc_ay[4], acc_cA[4], acc_cB[4], acc_th[4];  // index k: the row stage k worked on
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc_ax[k] = acc_ay[k] = acc_cA[k] = acc_cB[k] = acc_th[k] = 0.f;
+    __syncthreads();
+
+    // stage k (0: stage 4 .. 3: stage 1) at row r
+    auto stage = [&](const int k, const int r) {
+        const bool wall = r == 0 || r == Ly - 1;
+        // rows beyond the walls hold no cell: their products are 0
+        const bool hm = r - 1 >= 0, hp = r + 1 < Ly;
+        const float* xm = ring(sPX, k, r - 1);
+        const float* xc = ring(sPX, k, r);
+        const float* xp = ring(sPX, k, r + 1);
+        const float* ym = ring(sPY, k, r - 1);
+        const float* yp = ring(sPY, k, r + 1);
+        const float* mm = ring(sMU, k, r - 1);
+        const float* mc = ring(sMU, k, r);
+        const float* mp = ring(sMU, k, r + 1);
+        // 12 Dx[PX], 12 Dy[PY], 6 Lap[mu] (unweighted sums of the stencils)
+        float dxp = 4.f * (xc[1] - xc[-1]), dyp = 0.f;
+        float lap = -20.f * mc[0] + 4.f * (mc[1] + mc[-1]);
+        if (hm) {
+            dxp += xm[1] - xm[-1];
+            dyp -= 4.f * ym[0] + ym[1] + ym[-1];
+            lap += 4.f * mm[0] + mm[1] + mm[-1];
+        }
+        if (hp) {
+            dxp += xp[1] - xp[-1];
+            dyp += 4.f * yp[0] + yp[1] + yp[-1];
+            lap += 4.f * mp[0] + mp[1] + mp[-1];
+        }
+        float lu = -(dxp + dyp) * (1.f / 12.f) + chi * (1.f / 6.f) * lap;
+        const float m = mc[0];
+        float lax = 0.f, lay = 0.f, lcA = 0.f, lcB = 0.f;
+        if (!wall && m != 0.f) {
+            const float* um = ring(sU, k, r - 1);
+            const float* uc = ring(sU, k, r);
+            const float* up = ring(sU, k, r + 1);
+            const float T = P.Ts + uc[0];
+            const float rsq = rsqrt_a(T);
+            const float dphi = P.k1k1 - P.k0k1 * rsq;
+            const float d2phi = 0.5f * P.k0k1 * (rsq * rsq * rsq);
+            const float cA = own(2, r), cB = own(3, r);
+            lu += (-(cA - cB * dphi) + T * cB * d2phi) * m;
+            const float ux = (uc[1] - uc[-1]) * (1.f / 3.f) + ((up[1] - um[-1]) + (um[1] - up[-1])) * (1.f / 12.f);
+            const float uy = (up[0] - um[0]) * (1.f / 3.f) + ((up[1] - um[-1]) + (up[-1] - um[1])) * (1.f / 12.f);
+            lax = ux * m;
+            lay = uy * m;
+            lcA = -T * m;
+            lcB = T * dphi * m;
+        }
+        if (k == 0) {
+            acc_ax[0] = lax;
+            acc_ay[0] = lay;
+            acc_cA[0] = lcA;
+            acc_cB[0] = lcB;
+            acc_th[0] = own(4, r) + lu;
+        } else {
+            acc_ax[k] += lax;
+            acc_ay[k] += lay;
+            acc_cA[k] += lcA;
+            acc_cB[k] += lcB;
+            acc_th[k] += lu;
+        }
+        if (k < 3) {  // the next stage's mu = a lambda-bar + b lambda_u on fluid rows, with its products
+            const float ab = k == 2 ? 1.f / 6.f : 1.f / 3.f, bb = k == 0 ? 1.f : 0.5f;
+            const float mn = wall ? 0.f : ab * own(4, r) + bb * lu;
+            *ring(sMU, k + 1, r) = mn;
+            *ring(sPX, k + 1, r) = own(0, r) * mn;
+            *ring(sPY, k + 1, r) = own(1, r) * mn;
+        }
     };
-    // the nine neighbours' mu first (issued together), then their
-    // coefficients only where mu is non-zero: lambda is zero away from the
-    // heated wall early in a reverse sweep, and those cells cost no traffic
-    float mj[9];
-    int jj[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        // source cell s = y - d with d = e_a contributes c_d(s) mu(s)
-        jj[a] = g.at(x, y, -EXd[a], -EYd[a]);
-        mj[a] = jj[a] < 0 ? 0.f : mu_at(jj[a], y - EYd[a]);
-    }
-    float lu = 0.f;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        if (mj[a] == 0.f) continue;
-        const int j = jj[a], dx = EXd[a], dy = EYd[a];
-        lu += (A.ax[j] * wdx(dx, dy) + A.ay[j] * wdy(dx, dy) + P.chi * wlap(dx, dy)) * mj[a];
-    }
-    const float m = mj[0];  // own cell (e_0 = 0)
-    float lax = 0.f, lay = 0.f, lcA = 0.f, lcB = 0.f;
-    if (!wall && m != 0.f) {
-        const float T = P.Ts + u[i];
-        const float rs = rsqrt_a(T);
-        const float dphi = P.k1k1 - P.k0k1 * rs;
-        const float d2phi = 0.5f * P.k0k1 * (rs * rs * rs);
-        lu += (-(A.cA[i] - A.cB[i] * dphi) + T * A.cB[i] * d2phi) * m;
-        float dx = 0.f, dy = 0.f;
-#pragma unroll
-        for (int a = 1; a < 9; ++a) {
-            const float un = u[g.at(x, y, EXd[a], EYd[a])];
-            dx += wdx(EXd[a], EYd[a]) * un;
-            dy += wdy(EXd[a], EYd[a]) * un;
+
+    // the inputs of iteration L, loaded one iteration ahead (their latency is
+    // hidden behind the stages): lambda_theta', ax, ay, u4, u3 of row L, cA,
+    // cB of row L - 1, u2 of row L - 2, theta of row L - 3
+    float n_lin = 0.f, n_ax = 0.f, n_ay = 0.f, n_u4 = 0.f, n_u3 = 0.f, n_cA = 0.f, n_cB = 0.f, n_u2 = 0.f, n_th = 0.f;
+    auto prefetch = [&](int L) {
+        if (L <= hi) {
+            const int i = L * pitch + x;
+            n_lin = A.lt_in[i];
+            n_ax = A.ax[i];
+            n_ay = A.ay[i];
+            n_u4 = A.u4[i];
+            n_u3 = A.u3[i];
         }
-        lax = dx * m;
-        lay = dy * m;
-        lcA = -T * m;
-        lcB = T * dphi * m;
-    }
-    if (first) {
-        const float lin = A.lt_in[i];
-        if (P.bc != BC_PERIODIC && y == 0) A.dTb[x] += (double)lin;
-        A.lax[i] = lax;
-        A.lay[i] = lay;
-        A.lcA[i] = lcA;
-        A.lcB[i] = lcB;
-        A.lth[i] = (wall ? 0.f : lin) + lu;
-    } else {
-        if (lax != 0.f || lay != 0.f || lcA != 0.f || lcB != 0.f) {
-            A.lax[i] += lax;
-            A.lay[i] += lay;
-            A.lcA[i] += lcA;
-            A.lcB[i] += lcB;
+        if (L - 1 >= lo && L - 1 <= hi) {
+            const int i = (L - 1) * pitch + x;
+            n_cA = A.cA[i];
+            n_cB = A.cB[i];
         }
-        A.lth[i] += lu;
-    }
-    if (!last) {
-        const float lin = A.lt_in[i];
-        const float lbar = wall ? 0.f : lin;
-        A.mu_next[i] = wall ? 0.f : (a_bar * lbar + b_u * lu);
-    } else {
-        rev_coef_cell(P, A, i, wall);
+        if (L - 2 >= lo && L - 2 <= hi) n_u2 = A.u2[(L - 2) * pitch + x];
+        if (L - 3 >= lo && L - 3 <= hi) n_th = A.theta[(L - 3) * pitch + x];
+    };
+    prefetch(lo);
+    for (int L = lo; L <= hi + RT_HALO; ++L) {
+        // ---- S: the prefetched row into the rings, then the next one's loads
+        if (L <= hi) {
+            const bool wall = L == 0 || L == Ly - 1;
+            const float mu = wall ? 0.f : n_lin * (1.f / 6.f);
+            *ring(sMU, 0, L) = mu;
+            *ring(sPX, 0, L) = n_ax * mu;
+            *ring(sPY, 0, L) = n_ay * mu;
+            own(0, L) = n_ax;
+            own(1, L) = n_ay;
+            own(4, L) = wall ? 0.f : n_lin;
+            *ring(sU, 0, L) = n_u4;
+            *ring(sU, 1, L) = n_u3;
+        }
+        if (L - 1 >= lo && L - 1 <= hi) {  // cA, cB of row L - 1 (stage 4 there next)
+            own(2, L - 1) = n_cA;
+            own(3, L - 1) = n_cB;
+        }
+        if (L - 2 >= lo && L - 2 <= hi) *ring(sU, 2, L - 2) = n_u2;
+        if (L - 3 >= lo && L - 3 <= hi) *ring(sU, 3, L - 3) = n_th;
+        prefetch(L + 1);
+        __syncthreads();
+        if (L - 1 >= lo && L - 1 <= hi) stage(0, L - 1);
+        __syncthreads();
+        if (L - 2 >= lo && L - 2 <= hi) stage(1, L - 2);
+        __syncthreads();
+        if (L - 3 >= lo && L - 3 <= hi) stage(2, L - 3);
+        __syncthreads();
+        const int r = L - 4;
+        if (r >= ys && r < ye) {
+            stage(3, r);
+            if (out) {
+                const int i = r * pitch + x;
+                A.lth[i] = acc_th[3];
+                rev_coef_vals(P, A, i, r == 0 || r == Ly - 1, acc_ax[3], acc_ay[3], acc_cA[3], acc_cB[3]);
+                if (r == 0) A.dTb[x] += (double)A.lt_in[i];
+            }
+        }
+#pragma unroll
+        for (int k = 3; k > 0; --k) {
+            acc_ax[k] = acc_ax[k - 1];
+            acc_ay[k] = acc_ay[k - 1];
+            acc_cA[k] = acc_cA[k - 1];
+            acc_cB[k] = acc_cB[k - 1];
+            acc_th[k] = acc_th[k - 1];
+        }
+        __syncthreads();
     }
 }
+
+constexpr size_t rt_smem_bytes() { return sizeof(float) * (16 * (size_t)RT_R * RT_W + 5 * (size_t)RT_R * RT_BD); }
 
 // MRT collision (additive form f* = f + M^-1 dm), velocity and the local
 // parts of the forces, transposed cell by cell; first the transposed
@@ -588,9 +710,9 @@ __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
 // launches take ~15 us, the fused step ~20 us).
 constexpr size_t kFusedRecomputeCells = 512 * 512;
 
-// Work-buffer layout: 45 field planes, then dJ/d theta_b [pitch doubles], the
+// Work-buffer layout: 39 field planes, then dJ/d theta_b [pitch doubles], the
 // per-column dJ/dG_w parts [pitch doubles] and dJ/dG_w.
-constexpr int kPlanes = 45;
+constexpr int kPlanes = 39;
 
 AdjFields fields_at(const StepParams& P, void* work) {
     float* w = (float*)work;
@@ -634,12 +756,6 @@ AdjFields fields_at(const StepParams& P, void* work) {
     A.lvx = next(1);
     A.lvy = next(1);
     A.lth = next(1);
-    A.lax = next(1);
-    A.lay = next(1);
-    A.lcA = next(1);
-    A.lcB = next(1);
-    A.mu = next(1);
-    A.mu_next = next(1);
     A.ldrx = next(1);
     A.ldry = next(1);
     A.ldivv = next(1);
@@ -727,14 +843,27 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
         fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u2, A.u3, 0.5f);
         fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u3, A.u4, 1.0f);
     }
-    const float* us[4] = {A.u4, A.u3, A.u2, theta};
-    const float abar[4] = {1.f / 3.f, 1.f / 3.f, 1.f / 6.f, 0.f};
-    const float bu[4] = {1.f, 0.5f, 0.5f, 0.f};
-    for (int k = 0; k < 4; ++k) {
-        rev_stage<<<grid, blk, 0, st>>>(P, A, us[k], abar[k], bu[k], k == 0, k == 3);
-        float* t = A.mu;
-        A.mu = A.mu_next;
-        A.mu_next = t;
+    // the four RK stages transposed: one column-marching launch, segments
+    // sized so that the blocks fill the GPU once
+    {
+        static int occ = 0, nsm = 0;
+        cudaError_t e = cudaSuccess;
+        if (!occ) {
+            int dev = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(rev_thermal_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                           (int)rt_smem_bytes());
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rev_thermal_fused, RT_BD, rt_smem_bytes());
+            if (e != cudaSuccess) return e;
+            occ = occ < 1 ? 1 : occ;
+        }
+        const int nstrips = (P.Lx + RT_BD - 2 * RT_HALO - 1) / (RT_BD - 2 * RT_HALO);
+        const int nseg = std::max(1, nsm * occ / nstrips);
+        const int seg_h = std::max(16, (P.Ly + nseg - 1) / nseg);
+        const int nb = nstrips * ((P.Ly + seg_h - 1) / seg_h);
+        rev_thermal_fused<<<nb, RT_BD, rt_smem_bytes(), st>>>(P, A, seg_h);
     }
     rev_collide<<<grid, blk, 0, st>>>(P, A);
     rev_psi<<<grid, blk, 0, st>>>(P, A, lq);

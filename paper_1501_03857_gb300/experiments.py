@@ -224,3 +224,52 @@ def boiling_curve(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, ba
                       "hc_max_superheat": best["superheat"], "hc_max": best["h_c"]}
     return {"t_switch": t_switch, "t_settle": t_settle, "t_avg": t_avg, "base_superheat": base_superheat,
             "seeds": seeds, "cases": out, "curves": curves, "ranks": world, "runs_on_this_rank": len(mine)}
+
+
+def boiling_history(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, base_superheat: float = 0.0137,
+                    t_switch: int = 20000, t_end: int = 140000, window: int = 5000, sample_every: int = 1000,
+                    seeds=(1, 2, 3), stream=None) -> dict:
+    """The time course behind the boiling curve: every (Delta T, G_w, seed)
+    run of boiling_curve's protocol continued to t_end, with the mean heat
+    flux q(t) of each window of `window` steps after the switch and the
+    lowest and mean wall vapour coverage of its samples (every
+    sample_every steps). Returns per case the window start times, the
+    seed-mean flux per window ("q"), each seed's series ("q_runs") and, per
+    window, how many seeds kept the heated wall under a film in every sample
+    ("film")."""
+    cfg = cfg or paper_config()
+    rv, rl = lb.coexistence(cfg)
+    cases = [(float(dT), float(gw)) for gw in Gw_values for dT in superheats]
+    runs = [(c, int(sd)) for c in cases for sd in seeds]
+    insts = [{"cfg": replace(cfg, seed=sd), "Gw": gw, "superheat": (base_superheat if dT > base_superheat else dT)}
+             for (dT, gw), sd in runs]
+    batch = lb.Batch(insts, stream=stream)
+    nwin = (t_end - t_switch) // window
+    q = np.zeros((len(runs), nwin))
+    cmin = np.zeros((len(runs), nwin))
+    try:
+        batch.step(t_switch)
+        for i, ((dT, gw), _) in enumerate(runs):
+            if dT > base_superheat:
+                batch.set_wall_temperature(i, dT)
+        for w in range(nwin):
+            batch.heat_flux(reset=True)
+            lo = np.ones(len(runs))
+            done = 0
+            while done < window:
+                n = min(sample_every, window - done)
+                batch.step(n)
+                done += n
+                for i in range(len(runs)):
+                    lo[i] = min(lo[i], wall_coverage(batch.fields(i, ("rho",))["rho"], rl, rv))
+            q[:, w] = batch.heat_flux()["q_mean"]
+            cmin[:, w] = lo
+    finally:
+        batch.close()
+    out = []
+    for c in cases:
+        idx = [i for i, (cc, _) in enumerate(runs) if cc == c]
+        out.append({"superheat": c[0], "Gw": c[1], "q": q[idx].mean(0).tolist(), "q_runs": q[idx].tolist(),
+                    "film": (cmin[idx] >= FILM_COVERAGE).sum(0).astype(int).tolist()})
+    return {"t_windows": [t_switch + w * window for w in range(nwin)], "window": window, "seeds": list(seeds),
+            "cases": out}
