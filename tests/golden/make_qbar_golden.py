@@ -15,8 +15,10 @@ density noise 1e-4, bottom-wall superheat Delta T = 0.02 (lattice units,
 nucleate boiling: the first bubbles appear after 2000-4000 steps), 30000
 steps; q_bar is the mean of q(t) over steps t = 10000 .. 29999.
 
-Usage: python tests/golden/make_qbar_golden.py [nseeds] [nprocs]
-(35 seeds on 7 single-threaded processes take about 50 minutes.)
+Usage: python tests/golden/make_qbar_golden.py [first_seed last_seed] [nprocs]
+runs the seeds first_seed..last_seed (default 1..70) and merges them with
+the runs already in the file (35 seeds on 7 single-threaded processes take
+about 55 minutes).
 """
 
 import multiprocessing as mp
@@ -51,24 +53,34 @@ def run_seed(seed):
 
 
 def main():
-    nseeds = int(sys.argv[1]) if len(sys.argv) > 1 else 35
-    nprocs = int(sys.argv[2]) if len(sys.argv) > 2 else 7
+    first = int(sys.argv[1]) if len(sys.argv) > 2 else 1
+    last = int(sys.argv[2]) if len(sys.argv) > 2 else 70
+    nprocs = int(sys.argv[3]) if len(sys.argv) > 3 else 7
+    runs = {}
+    if os.path.exists(OUT):
+        for line in open(OUT):
+            p = line.split()
+            if p and p[0] == "seed":
+                runs[int(p[1])] = float(p[2])
+    todo = [sd for sd in range(first, last + 1) if sd not in runs]
     t0 = time.time()
-    with mp.get_context("spawn").Pool(nprocs) as pool:
-        res = sorted(pool.map(run_seed, range(1, nseeds + 1), chunksize=1))
+    if todo:
+        with mp.get_context("spawn").Pool(nprocs) as pool:
+            for sd, qb, _ in pool.map(run_seed, todo, chunksize=1):
+                runs[sd] = qb
     import numpy as np
-    q = np.array([r[1] for r in res])
+    q = np.array([runs[k] for k in sorted(runs)])
     mean, sem = q.mean(), q.std(ddof=1) / np.sqrt(len(q))
     with open(OUT, "w") as fh:
         fh.write("# Time-averaged bottom-wall heat flux q_bar (Sec. 3.2) of a boiling pool, FP64 oracle,\n")
         fh.write("# one run per seed of the initial density noise; written by make_qbar_golden.py\n")
         fh.write(f"# Lx {LX} Ly {LY} walls, paper EOS and transport (Sec. 3.1), pool_height {POOL}, "
                  f"noise_amp {NOISE}, superheat {SUPERHEAT}\n")
-        fh.write(f"# steps {STEPS}, q_bar over steps {T0}..{STEPS - 1}; "
-                 f"wall time {time.time() - t0:.0f} s on {nprocs} processes\n")
+        fh.write(f"# steps {STEPS}, q_bar over steps {T0}..{STEPS - 1}; single-threaded runs of about 10 minutes "
+                 f"each (the last {len(todo)} in {time.time() - t0:.0f} s on {nprocs} processes)\n")
         fh.write(f"mean {mean:.9e}\nsem {sem:.9e}\nseeds {len(q)}\n")
-        for sd, qb, qe in res:
-            fh.write(f"seed {sd} {qb:.9e}\n")
+        for sd in sorted(runs):
+            fh.write(f"seed {sd} {runs[sd]:.9e}\n")
     print(f"q_bar mean {mean:.6e} sem {sem:.3e} ({100 * sem / mean:.2f} %) over {len(q)} seeds")
 
 

@@ -7,9 +7,18 @@ bottom-wall heat flux q(t) (Sec. 3.2), of a small boiling pool is averaged
 over an ensemble of seeds of the initial density noise on both sides: the
 FP64 oracle's ensemble is stored in tests/golden/qbar_boiling_200x100.txt
 (written by make_qbar_golden.py beside it, which calls only the oracle),
-the GPU runs its own larger ensemble as the instances of one batch. The two
-ensemble means must agree within 2 %; the combined standard error of the
-difference is printed with them.
+the GPU runs its own larger ensemble as the instances of one batch.
+
+The ensemble has a long low tail. Most runs boil in the nucleate regime
+(q_bar 1.13e-3 to 1.36e-3 in the oracle's first 35 runs); about one in six
+stays for part of the window under the vapour blanket that the first burst
+of bubbles spreads over the wall (q_bar down to 0.59e-3). The all-run mean
+therefore carries the binomial noise of how many runs fall in the tail
+(17 % run-to-run spread against 5.5 % within the nucleate runs). So the
+comparison is: the mean q_bar of the runs above Q_GAP (the nucleate runs)
+within 2 % (the scope's bound), and the fraction of runs below it within
+three standard errors of the difference of two binomial fractions. The
+all-run means and their standard errors are printed beside them.
 """
 
 import os
@@ -49,12 +58,14 @@ def lb():
     return lbmod
 
 
+Q_GAP = 1.0e-3  # below the nucleate runs of the oracle's ensemble (its lowest: 1.13e-3)
+
+
 @pytest.mark.parametrize("tpb", [0, 1])
 def test_time_averaged_heat_flux_matches_oracle_ensemble(lb, tpb):
     """200 x 100 pool, liquid below y = 60, superheat 0.02 (nucleate
-    boiling), q_bar over steps 10000-29999: the mean over 512 GPU runs
-    (one launch per step, and the persistent launch) against the mean over
-    the oracle's runs, within 2 %."""
+    boiling), q_bar over steps 10000-29999 of 512 GPU runs (one launch per
+    step, and the persistent launch) against the oracle's runs."""
     g = read_golden()
     cfg = lb.Config(Lx=200, Ly=100, bc_y=lb.BC_WALLS, pool_height=60.0, noise_amp=1e-4)
     rv, rl = lb.coexistence(cfg)
@@ -69,14 +80,20 @@ def test_time_averaged_heat_flux_matches_oracle_ensemble(lb, tpb):
     q = batch.heat_flux()
     batch.close()
     assert (q["n"] == 20000).all()
-    qg = q["q_mean"]
-    mg, sg = float(qg.mean()), float(qg.std(ddof=1) / np.sqrt(len(qg)))
-    mo, so = g["mean"], g["sem"]
-    rel = mg / mo - 1.0
-    comb = float(np.hypot(sg, so)) / mo
+    qg = np.asarray(q["q_mean"])
+    qo = np.array([g["runs"][k] for k in sorted(g["runs"])])
+    sem = lambda v: float(v.std(ddof=1) / np.sqrt(len(v)))
+    hg, ho = qg[qg > Q_GAP], qo[qo > Q_GAP]
+    fg, fo = 1 - len(hg) / len(qg), 1 - len(ho) / len(qo)
+    rel = hg.mean() / ho.mean() - 1.0
+    comb = float(np.hypot(sem(hg), sem(ho))) / ho.mean()
+    fp = (fg * len(qg) + fo * len(qo)) / (len(qg) + len(qo))
+    fsd = float(np.sqrt(fp * (1 - fp) * (1 / len(qg) + 1 / len(qo))))
     same = sorted(g["runs"])
-    mg_same = float(np.mean([qg[s - 1] for s in same]))
-    print(f"q_bar GPU {mg:.5e} +- {sg:.1e} ({len(qg)} runs), oracle {mo:.5e} +- {so:.1e} ({len(same)} runs): "
-          f"difference {100 * rel:+.2f} % (combined standard error {100 * comb:.2f} %); "
-          f"GPU mean over the oracle's seeds {mg_same:.5e} ({100 * (mg_same / mo - 1):+.2f} %)")
+    print(f"all runs: GPU {qg.mean():.5e} +- {sem(qg):.1e} ({len(qg)}), oracle {qo.mean():.5e} +- {sem(qo):.1e} "
+          f"({len(qo)}); nucleate runs: GPU {hg.mean():.5e}, oracle {ho.mean():.5e}, difference {100 * rel:+.2f} % "
+          f"(combined standard error {100 * comb:.2f} %); blanketed fraction GPU {fg:.3f}, oracle {fo:.3f} "
+          f"(sd of the difference {fsd:.3f}); in the gap: GPU {int(((qg > 0.85e-3) & (qg < 1.1e-3)).sum())}; "
+          f"same seeds, GPU mean {np.mean([qg[s - 1] for s in same]):.5e}")
     assert abs(rel) <= 0.02
+    assert abs(fg - fo) <= 3 * fsd
