@@ -234,11 +234,13 @@ int lb_batch_workspace_bytes(const lb_batch_desc* d, int n, size_t* bytes);
 int lb_batch_init(lb_batch** b, const lb_batch_desc* d, int n, void* dev_workspace,
                   size_t workspace_bytes, void* stream);
 
-/* Advance every instance by nsteps: one launch of the fused step covers all
- * instances (each block belongs to one instance); runs of 32 steps are
- * replayed from a captured CUDA graph on a private stream ordered after and
- * before `stream`. Asynchronous. Results per instance are identical to
- * stepping the instance alone with the same launch shape. */
+/* Advance every instance by nsteps. By default one launch of the fused step
+ * per step covers all instances (each block belongs to one instance); in
+ * the persistent mode (lb_batch_set_persistent) one launch covers all
+ * instances for 32 steps. Runs of 32 steps are replayed from a captured
+ * CUDA graph on a private stream ordered after and before `stream`.
+ * Asynchronous. Results per instance are identical to stepping the instance
+ * alone with the same block size. */
 int lb_batch_step(lb_batch* b, int nsteps);
 
 /* Launch shape shared by all instances: block_x 64 or 128; seg_rows 0 gives
@@ -264,7 +266,7 @@ int lb_batch_set_launch(lb_batch* b, int block_x, int seg_rows);
 int lb_batch_set_persistent(lb_batch* b, int tiles_per_block, long long wait_limit);
 
 /* Per-instance heat-flux statistics into arrays of n entries (any may be
- * NULL); see lb_heat_flux. Synchronises. */
+ * NULL); see lb_heat_flux. Synchronises; reports faults as lb_batch_sync. */
 int lb_batch_heat_flux(lb_batch* b, double* q_inst, double* q_mean, double* q_std,
                        int64_t* nsamples, int reset);
 
@@ -281,7 +283,8 @@ int lb_batch_set_wettability(lb_batch* b, int i, double Gw);
  * persistent mode). */
 int lb_batch_info(lb_batch* b, int64_t* steps, int* block_x, int* nblocks);
 
-/* Wait and report latched device faults of any instance. */
+/* Wait and report latched device faults of any instance: every instance's
+ * flags are read and cleared, and the first fault found is returned. */
 int lb_batch_sync(lb_batch* b);
 
 /* Release the batch (the workspace stays the caller's). */
