@@ -313,11 +313,14 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     check against central differences of the same FP32 forward (uniform T_b
     mode and G_w, h = 1e-4). The timed adjoint call follows an untimed one, so
     graph capture and scratch allocation are not in it."""
+    from paper_1501_03857_gb300 import inputs
     cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
     Tc = lb.critical_temperature(cfg)
     sh, Gw = 0.1 * Tc, 0.065
+    rv, rl = lb.coexistence(cfg)
+    rho0 = inputs.pool_density(L, L, rl, rv, 0.4 * L, noise_amp=1e-4, seed=5)
     st = torch.cuda.current_stream()
-    sim = lb.Simulation(cfg, superheat=sh, Gw=Gw, stream=st)
+    sim = lb.Simulation(cfg, superheat=sh, Gw=Gw, rho0=rho0, stream=st)
     sim.step(200)  # leave the initial transient
     blob = sim.save()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -351,7 +354,22 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     fd_tb = (forward_J(dtb=h) - forward_J(dtb=-h)) / (2 * h)
     fd_gw = (forward_J(dgw=h) - forward_J(dgw=-h)) / (2 * h)
     sim.close()
-    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "J": J,
+    # the FP64 reference gradients of this window (tests/golden, written from
+    # the oracle by central differences with Richardson extrapolation)
+    ref = {}
+    gp = os.path.join(ROOT, "tests", "golden", "adjoint_256_gradients.txt")
+    if L == 256 and nsteps == 2000 and os.path.exists(gp):
+        for line in open(gp):
+            p = line.split("#")[0].split()
+            if len(p) == 2:
+                ref[p[0]] = float(p[1])
+    fp64 = None
+    if ref:
+        fp64 = {"J": ref["J"], "dJ_dGw": ref["dGw"], "dJ_dTb_uniform": ref["dTb_uniform"],
+                "rel_err_J": abs(J / ref["J"] - 1), "rel_err_Gw": abs(dGw / ref["dGw"] - 1),
+                "rel_err_uniform": abs(float(dTb.sum()) / ref["dTb_uniform"] - 1),
+                "what": "FP64 oracle central differences, h = 2e-4 and 1e-4, Richardson-extrapolated"}
+    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "J": J, "vs_fp64_reference": fp64,
             "ms_forward": t_fwd, "ms_adjoint_total": t_adj, "cost_ratio": t_adj / t_fwd,
             "mlups_adjoint": L * L * nsteps / (t_adj * 1e-3) / 1e6,
             "mlups_forward": L * L * nsteps / (t_fwd * 1e-3) / 1e6,

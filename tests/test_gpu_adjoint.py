@@ -154,3 +154,37 @@ def test_gradient_direction_at_bench_scale(lb, L):
     across = (J_of(h * o) - J_of(-h * o)) / (2 * h)
     assert abs(across - float(g @ o)) < 1e-3 * norm, (across, float(g @ o), norm)
     sim.close()
+
+
+def test_adjoint_256_window_against_fp64_reference(lb):
+    """The gradient of the benchmark window (256 x 256 boiling domain, 200
+    steps from the pool, then a 2000-step window, checkpoint every 100)
+    against FP64 reference gradients of the oracle (central differences
+    at h = 2e-4 and 1e-4, Richardson-extrapolated; tests/golden/
+    adjoint_256_gradients.txt, written from the oracle alone): dJ/dG_w and
+    the uniform T_b mode within 1e-3, J within 1e-5."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "adjoint_256_gradients.txt")
+    ref = {}
+    for line in open(path):
+        p = line.split("#")[0].split()
+        if len(p) == 2:
+            ref[p[0]] = float(p[1])
+    L = 256
+    cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
+    sh = 0.1 * lb.critical_temperature(cfg)
+    rv, rl = lb.coexistence(cfg)
+    rho0 = inputs.pool_density(L, L, rl, rv, 0.4 * L, noise_amp=1e-4, seed=5)
+    P = oracle_params(cfg, rho0, superheat=sh, Gw=0.065)
+    f0, th0 = oracle_initial_fp32(rho0, P)
+    sim = lb.Simulation(cfg, superheat=sh, Gw=0.065, rho0=rho0)
+    sim.set_state(f0, th0)
+    sim.step(200)
+    J, dTb, dGw = sim.adjoint(2000, 100)
+    sim.close()
+    eJ, eG, eT = abs(J / ref["J"] - 1), abs(dGw / ref["dGw"] - 1), abs(float(dTb.sum()) / ref["dTb_uniform"] - 1)
+    print(f"256^2 window: J rel {eJ:.2e}, dJ/dG_w rel {eG:.2e}, uniform dJ/dT_b rel {eT:.2e} "
+          f"(Richardson vs h = 1e-4 alone: {abs(ref['dGw'] / ref['dGw_h1e-4'] - 1):.1e}, "
+          f"{abs(ref['dTb_uniform'] / ref['dTb_uniform_h1e-4'] - 1):.1e})")
+    assert eJ < 1e-5
+    assert eG < 1e-3 and eT < 1e-3
