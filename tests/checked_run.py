@@ -26,7 +26,7 @@ def run(case):
     return f, th
 
 
-def run_batch(shapes, block_x=64, seg=0, vary=False):
+def run_batch(shapes, block_x=64, seg=0, vary=False, tpb=0):
     insts = []
     for i, (Lx, Ly, bc) in enumerate(shapes):
         # vary: instances differ in sigma, so the step reads every constant
@@ -36,6 +36,7 @@ def run_batch(shapes, block_x=64, seg=0, vary=False):
         insts.append({"cfg": cfg, "superheat": 0.01, "Gw": 0.05 * (i % 3)})
     b = lb.Batch(insts)
     b.set_launch(block_x, seg)
+    b.set_persistent(tpb)  # 0: one launch per step; >= 1: the persistent launch
     b.step(37)
     b.sync()
     out = [b.get_state(i) for i in range(b.n)]
@@ -53,10 +54,13 @@ if __name__ == "__main__":
     res = {}
     for k, c in enumerate(cases):
         res[f"f{k}"], res[f"t{k}"] = run(c)
-    batches = [(((40, 30, 0), (57, 23, 1), (33, 48, 2)), 64, 0, False), (random_batch(), 128, 0, False),
-               (random_batch(12, 9), 64, 5, False), (random_batch(13, 7), 64, 0, True),
-               (random_batch(14, 5), 128, 7, True)]
-    for j, (shapes, bx, seg, vary) in enumerate(batches):
-        for k, (f, t) in enumerate(run_batch(shapes, bx, seg, vary)):
+    batches = [(((40, 30, 0), (57, 23, 1), (33, 48, 2)), 64, 0, False, 0), (random_batch(), 128, 0, False, 0),
+               (random_batch(12, 9), 64, 5, False, 0), (random_batch(13, 7), 64, 0, True, 0),
+               (random_batch(14, 5), 128, 7, True, 0),
+               # the persistent launch: one and several tiles per block
+               (random_batch(15, 10), 64, 0, False, 1), (random_batch(16, 8), 128, 6, False, 2),
+               (random_batch(17, 6), 64, 0, True, 1), (random_batch(18, 4), 64, 3, False, 3)]
+    for j, (shapes, bx, seg, vary, tpb) in enumerate(batches):
+        for k, (f, t) in enumerate(run_batch(shapes, bx, seg, vary, tpb)):
             res[f"b{j}f{k}"], res[f"b{j}t{k}"] = f, t
     np.savez(sys.argv[2], **res)

@@ -1,9 +1,9 @@
 """The checked build (liblbboil_checked.so, compiled with -DLB_CHECKED): its
 fused step checks every global and shared-memory address against its buffer
 and flags a miss as LB_E_BOUNDS instead of faulting. On grids with odd
-sizes, every boundary treatment, several launch shapes and a batch of uneven
-instances it flags nothing and produces exactly the states of the normal
-build."""
+sizes, every boundary treatment, several launch shapes and batches of uneven
+instances (one launch per step and the persistent launch) it flags nothing
+and produces exactly the states of the normal build."""
 
 import json
 import os
