@@ -203,7 +203,8 @@ int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* b
  * steps (the simulation advances; its heat-flux accumulators are not
  * touched) storing a checkpoint every ckpt_every steps, then sweeps back
  * recomputing each segment from its checkpoint. J (host) receives the value.
- * Wall-bounded runs without ghost layer only. Synchronises. */
+ * Walls or the outflow top in y, no ghost layer, thermal runs only.
+ * Synchronises. */
 int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes,
                double* J, double* dJ_dTb, double* dJ_dGw);
 

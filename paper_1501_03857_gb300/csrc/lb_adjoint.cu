@@ -23,7 +23,7 @@
 // A stencil applied forward as out(x) = sum_d c_d in(x + d) is transposed as
 // a gather lambda_in(y) += sum_d c_d lambda_out(y - d). Fields are pitched
 // [Ly][pitch] FP32; gradients are accumulated in FP64. Supported: walls in
-// y, no ghost layer (the host checks).
+// y or the outflow top, no ghost layer (the host checks).
 #include <algorithm>
 
 #include "lb_internal.h"
@@ -146,6 +146,8 @@ __device__ __forceinline__ void pull_cell(const StepParams& P, const float* __re
             if (yy < 0) yy += P.Ly;
             if (yy >= P.Ly) yy -= P.Ly;
         } else {
+            // the outflow top pulls its unknowns from the top row itself
+            if (P.bc == BC_TOP_OUTFLOW && yy == P.Ly) yy = P.Ly - 1;
             ok = yy >= 0 && yy < P.Ly;
         }
         int xx = x - EXd[a];
@@ -701,7 +703,31 @@ __global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
         if (t >= 0) A.lf_out[a * pl + t] = lf[a];
         if (g.at(x, y, EXd[a], EYd[a]) < 0) A.lf_out[a * pl + i] = 0.f;
     }
+    // the outflow top pulled populations 4, 7, 8 from its own row, whose
+    // f* already has a consumer one row down: this second adjoint is kept in
+    // the cell's own lf slot and added by outflow_push after this kernel
+    if (P.bc == BC_TOP_OUTFLOW && y == P.Ly - 1) {
+        A.lf[4 * pl + i] = lf[4];
+        A.lf[7 * pl + i] = lf[7];
+        A.lf[8 * pl + i] = lf[8];
+    }
     A.lt_out[i] = lth;
+}
+
+// The outflow top's second consumer of f*_a(x - e_a, Ly - 1), a = 4, 7, 8.
+__global__ void outflow_push(const StepParams P, AdjFields A) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= P.Lx) return;
+    const int pl = P.plane, row = (P.Ly - 1) * P.pitch;
+    const int a4[3] = {4, 7, 8};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int a = a4[k];
+        int xs = x - EXd[a];
+        if (xs < 0) xs += P.Lx;
+        if (xs >= P.Lx) xs -= P.Lx;
+        A.lf_out[a * pl + row + xs] += A.lf[a * pl + row + x];
+    }
 }
 
 // Domains of at least this many cells recompute with the fused step (one
@@ -867,6 +893,7 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
     }
     rev_collide<<<grid, blk, 0, st>>>(P, A);
     rev_psi<<<grid, blk, 0, st>>>(P, A, lq);
+    if (P.bc == BC_TOP_OUTFLOW) outflow_push<<<(P.Lx + 127) / 128, 128, 0, st>>>(P, A);
     return cudaGetLastError();
 }
 

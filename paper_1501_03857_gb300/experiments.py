@@ -40,7 +40,7 @@ from dataclasses import replace
 
 import numpy as np
 
-from . import diagnostics, lb
+from . import diagnostics, lb, tune
 
 FILM_COVERAGE = 0.95  # wall coverage in every sample: a continuous vapour film
 
@@ -151,6 +151,8 @@ def run_cases(runs, cfg: lb.Config, rho_v: float, rho_l: float, base_superheat: 
     insts = [{"cfg": replace(cfg, seed=sd), "Gw": gw, "superheat": (base_superheat if dT > base_superheat else dT)}
              for (dT, gw), sd in runs]
     batch = lb.Batch(insts, stream=stream)
+    tune.tune_batch(batch)  # launch form and shape; the states are restored
+    batch.heat_flux(reset=True)
     cov = [[] for _ in runs]
     nbub = [[] for _ in runs]
     try:
@@ -244,6 +246,7 @@ def boiling_history(superheats, Gw_values=(0.0,), cfg: lb.Config | None = None, 
     insts = [{"cfg": replace(cfg, seed=sd), "Gw": gw, "superheat": (base_superheat if dT > base_superheat else dT)}
              for (dT, gw), sd in runs]
     batch = lb.Batch(insts, stream=stream)
+    tune.tune_batch(batch)  # launch form and shape; the states are restored
     nwin = (t_end - t_switch) // window
     q = np.zeros((len(runs), nwin))
     cmin = np.zeros((len(runs), nwin))

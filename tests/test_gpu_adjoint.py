@@ -22,8 +22,8 @@ def lb():
     return lbmod
 
 
-def setup(lb, Lx=24, Ly=16, superheat=0.012, Gw=0.05, seed=3):
-    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_WALLS, pool_height=0.45 * Ly)
+def setup(lb, Lx=24, Ly=16, superheat=0.012, Gw=0.05, seed=3, bc=None):
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_WALLS if bc is None else bc, pool_height=0.45 * Ly)
     rv, rl = lb.coexistence(cfg)
     rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.45 * Ly, noise_amp=1e-2, seed=seed)
     prof = superheat + 0.003 * np.sin(2 * np.pi * np.arange(Lx) / Lx)
@@ -56,9 +56,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def test_adjoint_matches_oracle_autograd(lb):
+@pytest.mark.parametrize("outflow", [False, True])
+def test_adjoint_matches_oracle_autograd(lb, outflow):
+    """Walls, and the outflow top (whose top row pulls populations 4, 7, 8
+    from itself, so their f* has two consumers)."""
     n = 12
-    cfg, rho0, prof, P, f0, th0 = setup(lb)
+    cfg, rho0, prof, P, f0, th0 = setup(lb, bc=lb.BC_TOP_OUTFLOW if outflow else None)
     tb = torch.tensor(prof, dtype=F64, requires_grad=True)
     gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
     Jo = oracle_J(P, f0, th0, tb, gw, n)
