@@ -454,6 +454,36 @@ def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
                          "what": "reverse sweep incl. forward recomputation, per step"}}
 
 
+def summary(line):
+    """The key figures of the line's blocks, compact."""
+    r = {"mlups": round(line["value"]), "hbm_frac": round(line["roofline"]["frac"], 4),
+         "e2e_mlups": round(line["e2e"]["value"])}
+    b = line.get("batched")
+    if b:
+        r["batched"] = {"speedup_vs_sequential": round(b["speedup"], 2), "ms_per_step": round(b["ms_per_step_batched"], 4),
+                        "sims_per_hour": round(b["sims_per_hour_batched"]), "mode": b["launch"]["mode"].split(":")[0],
+                        "hbm_frac": round(b["mlups_batched"] * 80e6 / 1e9 / line["roofline"]["peak"], 3)}
+    a = line.get("adjoint")
+    if a:
+        r["adjoint"] = {"cost_vs_forward_256": round(a["cost_ratio"], 2), "rel_err_Gw_vs_fd32": round(a["rel_err_Gw"], 6)}
+        if a.get("vs_fp64_reference"):
+            f = a["vs_fp64_reference"]
+            r["adjoint"].update(rel_err_Gw_vs_fp64=float("%.2e" % f["rel_err_Gw"]),
+                                rel_err_Tb_vs_fp64=float("%.2e" % f["rel_err_uniform"]))
+        if a.get("large"):
+            g = a["large"]
+            r["adjoint"].update(reverse_ms_2048=round(g["ms_reverse_per_step"], 4), reverse_hbm_frac_2048=round(g["roofline"]["frac"], 3),
+                                cost_vs_forward_2048=round(1 + g["ms_reverse_per_step"] / g["ms_forward_per_step"], 2))
+    e = line.get("experiments")
+    if e:
+        r["experiments"] = {"sims_per_hour": round(e["sims_per_hour"]),
+                            "chf_superheat": {k: v["chf_superheat"] for k, v in e["curves"].items()}}
+    c = line.get("cpu_baseline")
+    if c:
+        r["oracle_mlups"] = round(c["value"], 2)
+    return r
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -594,6 +624,7 @@ def run_ours(args):
             line["adjoint"]["large"] = adjoint_roofline(torch, lb)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        line["summary"] = summary(line)  # last, so that the end of the line carries the key figures
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
