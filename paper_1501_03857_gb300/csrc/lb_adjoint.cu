@@ -11,14 +11,17 @@
 //
 //   RK4 of Eq. 18 (stage 4 .. 1)   -> lambda_theta, lambda of the per-cell
 //   and the coefficients              coefficients (ax, ay, cA, cB), then
-//   (rev_thermal_fused: one           lambda_rho, lambda_v through grad rho
-//   column-marching launch)           and div v
-//   MRT collision (Eqs. 2, 5, 8), v (Eq. 6), forces (Eqs. 7, 9, 22)
-//                                  -> lambda_f, lambda_rho, lambda_psi, lambda_F_m
+//   (rev_thermal_fused: one           lambda of grad rho and div v, and the
+//   column-marching launch)           local parts of lambda_rho, lambda_v
+//   MRT collision (Eqs. 2, 5, 8), v (Eq. 6), forces (Eqs. 7, 9, 22),
+//   pull-streaming (Eq. 3)         -> lambda_f*^n without the lambda_rho
+//   (rev_flow_fused, stage C)         share, lambda_psi, lambda_F_m
 //   F_m neighbour sums (Eq. 7), psi (Eq. 21), q_w, rho = sum f
-//                                  -> lambda_f, lambda_theta
-//   Zou-He fill, pull-streaming (Eq. 3)
-//                                  -> lambda_f*^n
+//   (rev_flow_fused, stage P)      -> lambda_rho (shared by all nine pulled
+//                                     populations: carried to the next
+//                                     reverse step as one plane), lambda_theta;
+//                                     on the wall rows the Zou-He fill and the
+//                                     pull transposed with it
 //
 // A stencil applied forward as out(x) = sum_d c_d in(x + d) is transposed as
 // a gather lambda_in(y) += sum_d c_d lambda_out(y - d). Fields are pitched
@@ -61,40 +64,51 @@ __device__ __forceinline__ float wlap(int dx, int dy) {
     return (dx == 0 && dy == 0) ? (-20.f / 6.f) : ((dx == 0 || dy == 0) ? (4.f / 6.f) : (1.f / 6.f));
 }
 
-struct Grid {
-    int Lx, Ly, pitch, bc;
-    // index of (x + dx, y + dy) or -1 outside a wall-bounded domain
-    __device__ __forceinline__ int at(int x, int y, int dx, int dy) const {
-        int xx = x + dx;
-        if (xx < 0) xx += Lx;
-        if (xx >= Lx) xx -= Lx;
-        int yy = y + dy;
-        if (bc == BC_PERIODIC) {
-            if (yy < 0) yy += Ly;
-            if (yy >= Ly) yy -= Ly;
-        } else if (yy < 0 || yy >= Ly) {
-            return -1;
-        }
-        return yy * pitch + xx;
+// The 3 x 3 neighbourhood of one cell (x, y): its wrapped columns and the
+// offsets of its rows, -1 for a row beyond a wall; at(dx, dy) is the index
+// of (x + dx, y + dy) or -1. Formed once per cell, so each neighbour costs
+// one select and one add.
+struct Nbr {
+    int col[3], row[3];
+    bool wall;  // (x, y) on a wall row (or the outflow top)
+    __device__ __forceinline__ int at(int dx, int dy) const {
+        const int r = row[dy + 1];
+        return r < 0 ? -1 : r + col[dx + 1];
     }
-    __device__ __forceinline__ bool wall(int y) const { return bc != BC_PERIODIC && (y == 0 || y == Ly - 1); }
 };
+
+__device__ __forceinline__ Nbr nbr_of(const StepParams& P, int x, int y) {
+    Nbr n;
+    n.col[0] = x == 0 ? P.Lx - 1 : x - 1;
+    n.col[1] = x;
+    n.col[2] = x == P.Lx - 1 ? 0 : x + 1;
+    const bool per = P.bc == BC_PERIODIC;
+    n.row[0] = y > 0 ? (y - 1) * P.pitch : (per ? (P.Ly - 1) * P.pitch : -1);
+    n.row[1] = y * P.pitch;
+    n.row[2] = y + 1 < P.Ly ? (y + 1) * P.pitch : (per ? 0 : -1);
+    n.wall = !per && (y == 0 || y == P.Ly - 1);
+    return n;
+}
 
 // All the field planes one adjoint step works on.
 struct AdjFields {
-    // forward intermediates of the step being reversed
+    // forward intermediates of the step being reversed (jx, jy, vx, vy only
+    // in the field-kernel recompute, as its own scratch)
     const float* fstar;  // f*^n, 9 planes
     const float* theta;  // theta^n
-    float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *Fx, *Fy, *vx, *vy;
+    float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *vx, *vy;
     float *drx, *dry, *divv, *ax, *ay, *cA, *cB;
     float *u2, *u3, *u4;
-    // adjoints
-    const float* lf_in;  // lambda of f*^{n+1}, 9 planes
+    // adjoints; lambda of f* is carried as lf[a](t) + lr(t + e_a) (see
+    // adjoint_reverse_step in lb_internal.h)
+    const float* lf_in;  // lf part of lambda of f*^{n+1}, 9 planes
     const float* lt_in;  // lambda of theta^{n+1}
-    float* lf_out;       // lambda of f*^n, 9 planes
+    const float* lr_in;  // lr part of lambda of f*^{n+1}
+    float* lf_out;       // lf part of lambda of f*^n, 9 planes
     float* lt_out;       // lambda of theta^n
-    float* lf;           // lambda of the pulled populations, 9 planes
-    float *lrho, *lpsi, *lFmx, *lFmy, *lvx, *lvy, *lth;
+    float* lr_out;       // lr part of lambda of f*^n
+    float* sb;           // lambda of the pulled populations of the two wall rows: [9][2][pitch]
+    float *lrho, *lvx, *lvy, *lth;  // the thermal pass's parts
     float *ldrx, *ldry, *ldivv;
     double* dTb;   // [Lx] dJ/d theta_b accumulators
     double* dGwx;  // [Lx] dJ/dG_w contributions of each column's first fluid row
@@ -108,7 +122,6 @@ __device__ __forceinline__ bool cell(const StepParams& P, int& x, int& y, int& i
     return x < P.Lx && y < P.Ly;
 }
 
-__device__ __forceinline__ Grid grid_of(const StepParams& P) { return Grid{P.Lx, P.Ly, P.pitch, P.bc}; }
 
 // p_EOS and its partial derivatives (Eq. 21), FP32.
 struct Eos {
@@ -136,24 +149,15 @@ __device__ __forceinline__ Eos eos(float rho, float T, const StepParams& P) {
 
 // Pulled and wall-filled populations of cell (x, y) from f* (Eq. 3, Zou-He
 // on the wall rows), as the step computes them.
-__device__ __forceinline__ void pull_cell(const StepParams& P, const float* __restrict__ fstar, int x, int y,
+__device__ __forceinline__ void pull_cell(const StepParams& P, const Nbr& g, const float* __restrict__ fstar, int y,
                                           float (&f)[9]) {
+    // the outflow top pulls its unknowns from the top row itself
+    const int rp = (g.row[2] < 0 && P.bc == BC_TOP_OUTFLOW) ? g.row[1] : g.row[2];
+    const int rows[3] = {g.row[0], g.row[1], rp};
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        int yy = y - EYd[a];
-        bool ok = true;
-        if (P.bc == BC_PERIODIC) {
-            if (yy < 0) yy += P.Ly;
-            if (yy >= P.Ly) yy -= P.Ly;
-        } else {
-            // the outflow top pulls its unknowns from the top row itself
-            if (P.bc == BC_TOP_OUTFLOW && yy == P.Ly) yy = P.Ly - 1;
-            ok = yy >= 0 && yy < P.Ly;
-        }
-        int xx = x - EXd[a];
-        if (xx < 0) xx += P.Lx;
-        if (xx >= P.Lx) xx -= P.Lx;
-        f[a] = ok ? fstar[a * P.plane + yy * P.pitch + xx] : 0.f;
+        const int r = rows[1 - EYd[a]];
+        f[a] = r < 0 ? 0.f : fstar[a * P.plane + r + g.col[1 - EXd[a]]];
     }
     wall_fill(P, y, f);
 }
@@ -168,9 +172,9 @@ __device__ __forceinline__ void pull_cell(const StepParams& P, const float* __re
 __global__ void fwd_pull(const StepParams P, AdjFields A) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
+    const Nbr g = nbr_of(P, x, y);
     float f[9];
-    pull_cell(P, A.fstar, x, y, f);
+    pull_cell(P, g, A.fstar, y, f);
     float rho = 0.f;
     for (int a = 0; a < 9; ++a) rho += f[a];
     A.rho[i] = rho;
@@ -179,19 +183,18 @@ __global__ void fwd_pull(const StepParams P, AdjFields A) {
     const float T = P.Ts + A.theta[i];
     const float arg = P.two_over_G * (eos(rho, T, P).p - rho * (1.f / 3.f));
     A.psi[i] = arg > 0.f ? sqrtf(arg) : 0.f;
-    (void)g;
 }
 
 __global__ void fwd_force(const StepParams P, AdjFields A) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    const bool wall = g.wall(y);
+    const Nbr g = nbr_of(P, x, y);
+    const bool wall = g.wall;
     float Fmx = 0.f, Fmy = 0.f;
     if (!wall) {
         float sx = 0.f, sy = 0.f;
         for (int a = 1; a < 9; ++a) {
-            const float pn = A.psi[g.at(x, y, EXd[a], EYd[a])];
+            const float pn = A.psi[g.at(EXd[a], EYd[a])];
             sx += wdx(EXd[a], EYd[a]) * pn;
             sy += wdy(EXd[a], EYd[a]) * pn;
         }
@@ -205,8 +208,6 @@ __global__ void fwd_force(const StepParams P, AdjFields A) {
     }
     A.Fmx[i] = Fmx;
     A.Fmy[i] = Fmy;
-    A.Fx[i] = Fx;
-    A.Fy[i] = Fy;
     A.vx[i] = (A.jx[i] + 0.5f * Fx) / A.rho[i];
     A.vy[i] = (A.jy[i] + 0.5f * Fy) / A.rho[i];
 }
@@ -214,14 +215,14 @@ __global__ void fwd_force(const StepParams P, AdjFields A) {
 __global__ void fwd_coef(const StepParams P, AdjFields A) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    if (g.wall(y)) {
+    const Nbr g = nbr_of(P, x, y);
+    if (g.wall) {
         A.drx[i] = A.dry[i] = A.divv[i] = A.ax[i] = A.ay[i] = A.cA[i] = A.cB[i] = 0.f;
         return;
     }
     float drx = 0.f, dry = 0.f, dvx = 0.f, dvy = 0.f;
     for (int a = 1; a < 9; ++a) {
-        const int j = g.at(x, y, EXd[a], EYd[a]);
+        const int j = g.at(EXd[a], EYd[a]);
         const float cx = wdx(EXd[a], EYd[a]), cy = wdy(EXd[a], EYd[a]);
         drx += cx * A.rho[j];
         dry += cy * A.rho[j];
@@ -244,15 +245,15 @@ __global__ void fwd_coef(const StepParams P, AdjFields A) {
 __global__ void fwd_stage(const StepParams P, AdjFields A, const float* u_in, float* u_out, float c) {
     int x, y, i;
     if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    const bool wall = g.wall(y);
+    const Nbr g = nbr_of(P, x, y);
+    const bool wall = g.wall;
     if (wall) {
         u_out[i] = A.theta[i];
         return;
     }
     float dx = 0.f, dy = 0.f, lap = wlap(0, 0) * u_in[i];
     for (int a = 1; a < 9; ++a) {
-        const float un = u_in[g.at(x, y, EXd[a], EYd[a])];
+        const float un = u_in[g.at(EXd[a], EYd[a])];
         dx += wdx(EXd[a], EYd[a]) * un;
         dy += wdy(EXd[a], EYd[a]) * un;
         lap += wlap(EXd[a], EYd[a]) * un;
@@ -267,23 +268,24 @@ __global__ void fwd_stage(const StepParams P, AdjFields A, const float* u_in, fl
 
 // coefficients -> lambda of grad rho, div v (local) and the local parts of
 // lambda_rho, lambda_v, for cell i (after the last stage's accumulation)
+// (rho, divv, drx, dry: the cell's forward values)
 __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFields& A, int i, bool wall, float lax,
-                                              float lay, float lcA, float lcB) {
+                                              float lay, float lcA, float lcB, float rho, float divv, float drx,
+                                              float dry) {
     if (wall) {
         A.ldrx[i] = A.ldry[i] = A.ldivv[i] = 0.f;
         A.lrho[i] = A.lvx[i] = A.lvy[i] = 0.f;
         return;
     }
-    const float rho = A.rho[i], irho = rcp_a(rho);
+    const float irho = rcp_a(rho);
     const float br = P.b * rho;
     const float i1 = rcp_a(1.f - br);
     const float D = 1.f + 2.f * br - br * br, iD = rcp_a(D);
     const float dD = 2.f * P.b - 2.f * P.b * br;
-    const float divv = A.divv[i];
     A.ldrx[i] = P.chi * lax * irho;
     A.ldry[i] = P.chi * lay * irho;
     A.ldivv[i] = lcA * P.R * P.inv_cv * i1 + lcB * P.a * rho * P.inv_cv * iD;
-    A.lrho[i] = -P.chi * (A.drx[i] * lax + A.dry[i] * lay) * irho * irho + lcA * divv * P.R * P.inv_cv * P.b * i1 * i1 +
+    A.lrho[i] = -P.chi * (drx * lax + dry * lay) * irho * irho + lcA * divv * P.R * P.inv_cv * P.b * i1 * i1 +
                 lcB * divv * P.a * P.inv_cv * (D - rho * dD) * iD * iD;
     A.lvx[i] = -lax;
     A.lvy[i] = -lay;
@@ -417,8 +419,10 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
 
     // the inputs of iteration L, loaded one iteration ahead (their latency is
     // hidden behind the stages): lambda_theta', ax, ay, u4, u3 of row L, cA,
-    // cB of row L - 1, u2 of row L - 2, theta of row L - 3
+    // cB of row L - 1, u2 of row L - 2, theta of row L - 3, and rho, div v,
+    // grad rho of row L - 4 (the output row)
     float n_lin = 0.f, n_ax = 0.f, n_ay = 0.f, n_u4 = 0.f, n_u3 = 0.f, n_cA = 0.f, n_cB = 0.f, n_u2 = 0.f, n_th = 0.f;
+    float n_rho = 0.f, n_dv = 0.f, n_drx = 0.f, n_dry = 0.f;
     auto prefetch = [&](int L) {
         if (L <= hi) {
             const int i = L * pitch + x;
@@ -435,6 +439,13 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
         }
         if (L - 2 >= lo && L - 2 <= hi) n_u2 = A.u2[(L - 2) * pitch + x];
         if (L - 3 >= lo && L - 3 <= hi) n_th = A.theta[(L - 3) * pitch + x];
+        if (L - 4 >= ys && L - 4 < ye && out) {
+            const int i = (L - 4) * pitch + x;
+            n_rho = A.rho[i];
+            n_dv = A.divv[i];
+            n_drx = A.drx[i];
+            n_dry = A.dry[i];
+        }
     };
     prefetch(lo);
     for (int L = lo; L <= hi + RT_HALO; ++L) {
@@ -457,6 +468,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
         }
         if (L - 2 >= lo && L - 2 <= hi) *ring(sU, 2, L - 2) = n_u2;
         if (L - 3 >= lo && L - 3 <= hi) *ring(sU, 3, L - 3) = n_th;
+        const float o_rho = n_rho, o_dv = n_dv, o_drx = n_drx, o_dry = n_dry;  // row L - 4
         prefetch(L + 1);
         __syncthreads();
         if (L - 1 >= lo && L - 1 <= hi) stage(0, L - 1);
@@ -471,7 +483,8 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             if (out) {
                 const int i = r * pitch + x;
                 A.lth[i] = acc_th[3];
-                rev_coef_vals(P, A, i, r == 0 || r == Ly - 1, acc_ax[3], acc_ay[3], acc_cA[3], acc_cB[3]);
+                rev_coef_vals(P, A, i, r == 0 || r == Ly - 1, acc_ax[3], acc_ay[3], acc_cA[3], acc_cB[3], o_rho, o_dv,
+                              o_drx, o_dry);
                 if (r == 0) A.dTb[x] += (double)A.lt_in[i];
             }
         }
@@ -489,244 +502,363 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
 
 constexpr size_t rt_smem_bytes() { return sizeof(float) * (16 * (size_t)RT_R * RT_W + 5 * (size_t)RT_R * RT_BD); }
 
-// MRT collision (additive form f* = f + M^-1 dm), velocity and the local
-// parts of the forces, transposed cell by cell; first the transposed
-// gradients of the RK coefficients (lambda_rho += Dx^T ldrx + Dy^T ldry,
-// lambda_v += D^T ldivv), which complete this cell's lambda_rho and lambda_v.
-__global__ void rev_collide(const StepParams P, AdjFields A) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    const bool wall = g.wall(y);
-    float lr_c = 0.f, lvx_c = 0.f, lvy_c = 0.f;
-    for (int a = 1; a < 9; ++a) {
-        const int j = g.at(x, y, -EXd[a], -EYd[a]);
-        if (j < 0) continue;
-        const float cx = wdx(EXd[a], EYd[a]), cy = wdy(EXd[a], EYd[a]);
-        lr_c += cx * A.ldrx[j] + cy * A.ldry[j];
-        lvx_c += cx * A.ldivv[j];
-        lvy_c += cy * A.ldivv[j];
-    }
-    const int pl = P.plane;
-    float f[9], lo[9];
-    pull_cell(P, A.fstar, x, y, f);  // pulled again from f*: cheaper than a stored copy
-    for (int a = 0; a < 9; ++a) lo[a] = A.lf_in[a * pl + i];
-    const float rho = A.rho[i], vx = A.vx[i], vy = A.vy[i];
-    const float Fx = A.Fx[i], Fy = A.Fy[i], Fmx = A.Fmx[i], Fmy = A.Fmy[i], psi = A.psi[i];
-    // lambda_dm = diag(1/9, 1/36, ...) M lambda_f*
-    const float Ml1 = -4.f * lo[0] - (lo[1] + lo[2] + lo[3] + lo[4]) + 2.f * (lo[5] + lo[6] + lo[7] + lo[8]);
-    const float Ml2 = 4.f * lo[0] - 2.f * (lo[1] + lo[2] + lo[3] + lo[4]) + (lo[5] + lo[6] + lo[7] + lo[8]);
-    const float Ml3 = lo[1] - lo[3] + lo[5] - lo[6] - lo[7] + lo[8];
-    const float Ml4 = -2.f * lo[1] + 2.f * lo[3] + lo[5] - lo[6] - lo[7] + lo[8];
-    const float Ml5 = lo[2] - lo[4] + lo[5] + lo[6] - lo[7] - lo[8];
-    const float Ml6 = -2.f * lo[2] + 2.f * lo[4] + lo[5] + lo[6] - lo[7] - lo[8];
-    const float Ml7 = lo[1] - lo[2] + lo[3] - lo[4];
-    const float Ml8 = lo[5] - lo[6] + lo[7] - lo[8];
-    const float ldm1 = Ml1 * (1.f / 36.f), ldm2 = Ml2 * (1.f / 36.f), ldm3 = Ml3 * (1.f / 6.f);
-    const float ldm4 = Ml4 * (1.f / 12.f), ldm5 = Ml5 * (1.f / 6.f), ldm6 = Ml6 * (1.f / 12.f);
-    const float ldm7 = Ml7 * 0.25f, ldm8 = Ml8 * 0.25f;
-    // forward quantities of dm
-    const float v2 = vx * vx + vy * vy;
-    const float m7 = f[1] - f[2] + f[3] - f[4];
-    const float m8 = f[5] - f[6] + f[7] - f[8];
-    const float ne7 = m7 - rho * (vx * vx - vy * vy);
-    const float ne8 = m8 - rho * vx * vy;
-    const float psi2 = psi * psi;
-    const float ipsi2 = psi2 > 0.f ? rcp_a(psi2) : 0.f;
-    const float R = (Fmx * Fmx + Fmy * Fmy) * ipsi2;
-    const float S7 = 2.f * (vx * Fx - vy * Fy), S8 = vx * Fy + vy * Fx;
-    const float s = (rho - P.rho_v) * P.inv_drho;
-    const float sfr = fminf(fmaxf(s, 0.f), 1.f);
-    const float snu = rcp_a(P.tau_v + P.dtau * sfr);
-    // dm = -Lambda (m - meq) + (I - Lambda/2) S, momentum rows dm_j = F
-    const float lne1 = -P.s_e * ldm1, lS1 = (1.f - 0.5f * P.s_e) * ldm1;
-    const float lne2 = -P.s_z * ldm2, lS2 = (1.f - 0.5f * P.s_z) * ldm2;
-    const float lne4 = -P.s_q * ldm4, lne6 = -P.s_q * ldm6;
-    float lFx = ldm3 - (1.f - 0.5f * P.s_q) * ldm4;
-    float lFy = ldm5 - (1.f - 0.5f * P.s_q) * ldm6;
-    const float lne7 = -snu * ldm7, lS7 = (1.f - 0.5f * snu) * ldm7;
-    const float lne8 = -snu * ldm8, lS8 = (1.f - 0.5f * snu) * ldm8;
-    const float lsnu = -(ne7 + 0.5f * S7) * ldm7 - (ne8 + 0.5f * S8) * ldm8;
-    // ne_k = m_k(f) - meq_k(rho, v): m part -> lambda_f = M^T lambda_m
-    float lf[9];
-    {
-        const float l1 = lne1, l2 = lne2, l4 = lne4, l6 = lne6, l7 = lne7, l8 = lne8;
-        lf[0] = -4.f * l1 + 4.f * l2;
-        lf[1] = -l1 - 2.f * l2 - 2.f * l4 + l7;
-        lf[2] = -l1 - 2.f * l2 - 2.f * l6 - l7;
-        lf[3] = -l1 - 2.f * l2 + 2.f * l4 + l7;
-        lf[4] = -l1 - 2.f * l2 + 2.f * l6 - l7;
-        lf[5] = 2.f * l1 + l2 + l4 + l6 + l8;
-        lf[6] = 2.f * l1 + l2 - l4 + l6 - l8;
-        lf[7] = 2.f * l1 + l2 - l4 - l6 + l8;
-        lf[8] = 2.f * l1 + l2 + l4 - l6 - l8;
-    }
-    // meq part (lambda_meq = -lambda_ne): meq1 = rho(-2 + 3v^2), meq2 = rho(1 - 3v^2),
-    // meq4 = -rho vx, meq6 = -rho vy, meq7 = rho(vx^2 - vy^2), meq8 = rho vx vy
-    const float q1 = -lne1, q2 = -lne2, q4 = -lne4, q6 = -lne6, q7 = -lne7, q8 = -lne8;
-    float lrho = q1 * (-2.f + 3.f * v2) + q2 * (1.f - 3.f * v2) - q4 * vx - q6 * vy + q7 * (vx * vx - vy * vy) +
-                 q8 * vx * vy;
-    float lvx = q1 * 6.f * rho * vx - q2 * 6.f * rho * vx - q4 * rho + q7 * 2.f * rho * vx + q8 * rho * vy;
-    float lvy = q1 * 6.f * rho * vy - q2 * 6.f * rho * vy - q6 * rho - q7 * 2.f * rho * vy + q8 * rho * vx;
-    // S (Eq. 8): S1 = 6 vF + sig_e R, S2 = -6 vF - sig_z R, S7, S8
-    const float lvF = 6.f * lS1 - 6.f * lS2;
-    const float lR = P.sig_e * lS1 - P.sig_z * lS2;
-    lvx += lvF * Fx + 2.f * lS7 * Fx + lS8 * Fy;
-    lvy += lvF * Fy - 2.f * lS7 * Fy + lS8 * Fx;
-    lFx += lvF * vx + 2.f * lS7 * vx + lS8 * vy;
-    lFy += lvF * vy - 2.f * lS7 * vy + lS8 * vx;
-    float lFmx = 0.f, lFmy = 0.f, lpsi = 0.f;
-    if (psi2 > 0.f) {
-        lFmx += 2.f * Fmx * lR * ipsi2;
-        lFmy += 2.f * Fmy * lR * ipsi2;
-        lpsi += -2.f * R * lR * psi * ipsi2;
-    }
-    // snu(rho)
-    if (s > 0.f && s < 1.f) lrho += lsnu * (-snu * snu * P.dtau * P.inv_drho);
-    // identity part of f* = f + ...
-    for (int a = 0; a < 9; ++a) lf[a] += lo[a];
-    // velocity v = (j + F/2) / rho with the thermal path's lambda_v added
-    lvx += A.lvx[i] + lvx_c;
-    lvy += A.lvy[i] + lvy_c;
-    lrho += lr_c;
-    const float irho = rcp_a(rho);
-    const float ljx = lvx * irho, ljy = lvy * irho;
-    lFx += 0.5f * ljx;
-    lFy += 0.5f * ljy;
-    lrho += -(lvx * vx + lvy * vy) * irho;
-    for (int a = 0; a < 9; ++a) lf[a] += EXd[a] * ljx + EYd[a] * ljy;
-    // forces: F = F_m + F_ads + F_b on fluid rows, 0 on wall rows
-    if (!wall) {
-        lFmx += lFx;
-        lFmy += lFy;
-        lrho += -P.g * lFy;  // F_b (Eq. 9)
-        if (P.bc != BC_PERIODIC && y == 1) {  // F_ads (Eq. 22) on the first fluid row
-            lpsi += 2.f * P.gw6 * psi * lFy;
-            A.dGwx[x] += (double)(psi2 * (1.f / 6.f) * lFy);  // one cell per x on this row
-        }
-    } else {
-        lFmx = lFmy = 0.f;  // no force is applied on wall rows
-    }
-    for (int a = 0; a < 9; ++a) A.lf[a * pl + i] = lf[a];
-    A.lrho[i] += lrho;
-    A.lpsi[i] = lpsi;
-    A.lFmx[i] = lFmx;
-    A.lFmy[i] = lFmy;
+// ---- collision, forces, psi and the pull transposed in one column-marching launch
+//
+// A block of RF_BD threads owns RF_BD - 2 RF_HALO output columns and a
+// segment of rows and marches up it, each thread one column, two stages per
+// row iteration L:
+//
+//   C  row L    : the gathers of the RK-coefficient gradients (lambda_rho +=
+//                 -(Dx[ldrx] + Dy[ldry]), lambda_v += -D[ldivv]), the MRT
+//                 collision (additive form f* = f + M^-1 dm), velocity and the
+//                 local force terms transposed, cell by cell. rho, j and v
+//                 are formed again from the pulled populations (as the step
+//                 forms them), F from F_m, psi and rho. The cell's lambda of
+//                 the pulled populations, without the lambda_rho share, goes
+//                 straight through the transposed pull into lf_out (wall
+//                 rows: into sb for stage P); psi lambda_F_m goes to a ring.
+//   P  row L-1  : F_m's neighbour sums transposed (Eq. 7): with Q = psi
+//                 lambda_F_m at the source cell and the first-derivative
+//                 weights odd, lambda_psi += G (Dx[Qx] + Dy[Qy]); then psi
+//                 (Eq. 21), q(t) (Sec. 3.2) and rho = sum f transposed:
+//                 lambda_rho of the cell, shared by all nine pulled
+//                 populations, goes to lr_out (read by the next reverse step
+//                 where it reads lf); on the wall rows it is added to the
+//                 populations in sb, the Zou-He fill is transposed and the
+//                 result is pulled back into lf_out. lambda_theta out.
+//
+// The stencil inputs (ldrx, ldry, ldivv and lr_in of rows L-1..L+1 for C,
+// Q of rows L-2..L for P) sit in shared rings; every other input of row L+1
+// is loaded into registers during row L. C reaches one column further out
+// than its own and P one more: 2 halo columns per side. The owner's own
+// share of F_m(x) = -G psi(x) sum_a w_a psi(x + e_a) e_a is (F_m . lambda_F_m)
+// / psi; where psi = 0 (outside the EOS domain, which the forward step flags)
+// it is taken as 0.
+constexpr int RF_BD = 128, RF_HALO = 2, RF_W = RF_BD + 2, RF_R = 4;
+
+// 12 Dx[v], 12 Dy[v] of a shared ring around lane pointer c (rows m, c, p)
+__device__ __forceinline__ void grad12(const float* m, const float* c, const float* p, float& dx, float& dy) {
+    dx = 4.f * (c[1] - c[-1]) + (p[1] - p[-1]) + (m[1] - m[-1]);
+    dy = 4.f * (p[0] - m[0]) + (p[1] - m[1]) + (p[-1] - m[-1]);
 }
 
-// F_m neighbour sums (Eq. 7) and psi (Eq. 21) transposed, the heat flux
-// q(t) (in the window), rho = sum f; then the Zou-He fill transposed on the
-// wall rows and the pull-streaming transposed. Writes lambda of f*^n and of
-// theta^n.
-__global__ void rev_psi(const StepParams P, AdjFields A, float lq) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Grid g = grid_of(P);
-    const bool wall = g.wall(y);
-    const int pl = P.plane;
-    const float psi = A.psi[i];
-    float lpsi = A.lpsi[i];
-    if (!wall) {  // own factor psi(x) of F_m(x) = -G psi(x) sum_a w_a psi(x + e_a) e_a
-        float sx = 0.f, sy = 0.f;
-        for (int a = 1; a < 9; ++a) {
-            const float pn = A.psi[g.at(x, y, EXd[a], EYd[a])];
-            sx += wdx(EXd[a], EYd[a]) * pn;
-            sy += wdy(EXd[a], EYd[a]) * pn;
-        }
-        lpsi += -P.G * (sx * A.lFmx[i] + sy * A.lFmy[i]);
-    }
-    // neighbour factor: psi(y) appears in F_m(y - e_a); the eight lambda_F_m
-    // pairs first (issued together), psi only where they are non-zero
-    float lfx[9], lfy[9];
-    int jj[9];
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-        jj[a] = g.at(x, y, -EXd[a], -EYd[a]);
-        lfx[a] = jj[a] < 0 ? 0.f : A.lFmx[jj[a]];
-        lfy[a] = jj[a] < 0 ? 0.f : A.lFmy[jj[a]];
-    }
-#pragma unroll
-    for (int a = 1; a < 9; ++a) {
-        if (lfx[a] == 0.f && lfy[a] == 0.f) continue;
-        lpsi += -P.G * A.psi[jj[a]] * (wdx(EXd[a], EYd[a]) * lfx[a] + wdy(EXd[a], EYd[a]) * lfy[a]);
-    }
-    float lrho = A.lrho[i];
-    float lth = A.lth[i];
-    if (psi > 0.f) {
-        const float rho = A.rho[i];
-        const float T = P.Ts + A.theta[i];
-        const Eos e = eos(rho, T, P);
-        const float k = lpsi * rcp_a(P.G * psi);  // d psi = (dp - d rho / 3) / (G psi)
-        lrho += k * (e.p_rho - 1.f / 3.f);
-        lth += k * e.p_T;
-    }
-    // q(t) = (1/Lx) sum_x -cvchi rho(x,0) (-3 th0 + 4 th1 - th2) / 2 (Sec. 3.2)
-    if (lq != 0.f && P.bc != BC_PERIODIC && y <= 2) {
-        const float c = lq / (float)P.Lx * (-P.cvchi);
-        const int i0 = x, i1 = P.pitch + x, i2 = 2 * P.pitch + x;
-        const float rho0 = A.rho[i0];
-        if (y == 0) {
-            lrho += c * 0.5f * (-3.f * A.theta[i0] + 4.f * A.theta[i1] - A.theta[i2]);
-            lth += c * rho0 * (-1.5f);
-        } else if (y == 1) {
-            lth += c * rho0 * 2.f;
+__global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjFields A, float lq, int seg_h) {
+    // rings: 0 ldrx, 1 ldry, 2 ldivv, 3 lr_in (rows of stage C), 4 Qx, 5 Qy (stage P)
+    __shared__ float sm[6 * RF_R * RF_W];
+    for (int k = threadIdx.x; k < 6 * RF_R * RF_W; k += RF_BD) sm[k] = 0.f;
+    const int Lx = P.Lx, Ly = P.Ly, pitch = P.pitch, pl = P.plane;
+    const int nout = RF_BD - 2 * RF_HALO;
+    const int nstrips = (Lx + nout - 1) / nout;
+    const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+    const int lc = threadIdx.x, s = lc + 1;
+    int x = (strip * nout - RF_HALO + lc) % Lx;
+    if (x < 0) x += Lx;
+    const bool own = lc >= RF_HALO && lc < RF_HALO + nout && strip * nout + lc - RF_HALO < Lx;
+    const int cols[3] = {x == 0 ? Lx - 1 : x - 1, x, x == Lx - 1 ? 0 : x + 1};
+    // segment rows [ys, ye); the top two rows always share one (the outflow
+    // top adds to what row Ly - 2 stored, see stage P)
+    const int ys = seg * seg_h;
+    int ye = min(ys + seg_h, Ly);
+    if (ye == Ly - 1) ye = Ly;
+    if (ys >= Ly || (ys == Ly - 1 && ys > 0)) return;  // (the whole block: no barrier yet)
+    const int cl = max(ys - 1, 0), ch = min(ye, Ly - 1);  // rows of stage C
+    auto ring = [&](int f, int r) { return sm + (f * RF_R + (r & (RF_R - 1))) * RF_W + s; };
+    const float G = P.G;
+
+    float nr[4];  // ring inputs of one row (0 beyond the walls)
+    auto load_ring = [&](int r) {
+        if (r >= 0 && r < Ly) {
+            const int i = r * pitch + x;
+            nr[0] = A.ldrx[i];
+            nr[1] = A.ldry[i];
+            nr[2] = A.ldivv[i];
+            nr[3] = A.lr_in[i];
         } else {
-            lth += c * rho0 * (-0.5f);
+            nr[0] = nr[1] = nr[2] = nr[3] = 0.f;
         }
-    }
-    float lf[9];
-    for (int a = 0; a < 9; ++a) lf[a] = A.lf[a * pl + i] + lrho;
-    // Zou-He fill transposed: the filled populations pass their adjoint to
-    // the known ones they were built from
-    if (P.bc != BC_PERIODIC && y == 0) {
-        lf[4] += lf[2];
-        lf[7] += lf[5];
-        lf[1] += -0.5f * lf[5] + 0.5f * lf[6];
-        lf[3] += 0.5f * lf[5] - 0.5f * lf[6];
-        lf[8] += lf[6];
-        lf[2] = lf[5] = lf[6] = 0.f;
-    }
-    if (P.bc == BC_WALLS && y == P.Ly - 1) {
-        lf[2] += lf[4];
-        lf[5] += lf[7];
-        lf[1] += 0.5f * lf[7] - 0.5f * lf[8];
-        lf[3] += -0.5f * lf[7] + 0.5f * lf[8];
-        lf[6] += lf[8];
-        lf[4] = lf[7] = lf[8] = 0.f;
-    }
-    // pull-streaming transposed (f_a(y) = f*_a(y - e_a)) as a scatter:
-    // lambda_f*_a(y - e_a) = lambda_f_a(y); a cell whose y + e_a lies beyond a
-    // wall receives nothing and is set to 0 here
+    };
+    auto store_ring = [&](int r) {
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int t = g.at(x, y, -EXd[a], -EYd[a]);
-        if (t >= 0) A.lf_out[a * pl + t] = lf[a];
-        if (g.at(x, y, EXd[a], EYd[a]) < 0) A.lf_out[a * pl + i] = 0.f;
-    }
-    // the outflow top pulled populations 4, 7, 8 from its own row, whose
-    // f* already has a consumer one row down: this second adjoint is kept in
-    // the cell's own lf slot and added by outflow_push after this kernel
-    if (P.bc == BC_TOP_OUTFLOW && y == P.Ly - 1) {
-        A.lf[4 * pl + i] = lf[4];
-        A.lf[7 * pl + i] = lf[7];
-        A.lf[8 * pl + i] = lf[8];
-    }
-    A.lt_out[i] = lth;
-}
+        for (int k = 0; k < 4; ++k) *ring(k, r) = nr[k];
+    };
+    // stage C's per-cell inputs of one row: pulled populations (Eq. 3; the
+    // outflow top pulls 4, 7, 8 from its own row), lf part of lambda_f*^{n+1},
+    // the step's F_m, psi, theta, and the thermal pass's lambda_v, lambda_rho,
+    // lambda_theta
+    float nf[9], nl[9], nFmx, nFmy, npsi, nlvx, nlvy, nlrho, nth, nlth;
+    auto load_in = [&](int r) {
+        const int rc = r * pitch;
+        const int rows[3] = {r > 0 ? rc - pitch : -1, rc,
+                             r + 1 < Ly ? rc + pitch : (P.bc == BC_TOP_OUTFLOW ? rc : -1)};
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            const int rr = rows[1 - EYd[a]];
+            nf[a] = rr < 0 ? 0.f : A.fstar[a * pl + rr + cols[1 - EXd[a]]];
+        }
+        const int i = rc + x;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) nl[a] = A.lf_in[a * pl + i];
+        nFmx = A.Fmx[i];
+        nFmy = A.Fmy[i];
+        npsi = A.psi[i];
+        nlvx = A.lvx[i];
+        nlvy = A.lvy[i];
+        nlrho = A.lrho[i];
+        nth = A.theta[i];
+        nlth = A.lth[i];
+    };
+    // stage C's results for stage P, carried one iteration (row L - 1)
+    float c_lrho = 0.f, c_lpsi = 0.f, c_psi = 0.f, c_rho = 0.f, c_th = 0.f, c_lth = 0.f;
 
-// The outflow top's second consumer of f*_a(x - e_a, Ly - 1), a = 4, 7, 8.
-__global__ void outflow_push(const StepParams P, AdjFields A) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= P.Lx) return;
-    const int pl = P.plane, row = (P.Ly - 1) * P.pitch;
-    const int a4[3] = {4, 7, 8};
+    load_ring(cl - 1);
+    store_ring(cl - 1);
+    load_ring(cl);
+    store_ring(cl);
+    load_ring(cl + 1);
+    load_in(cl);
+    for (int L = cl; L <= ch + 1; ++L) {
+        // ---- ring row L + 1 and this row's inputs; then row L + 1's loads
+        float f[9], lo[9];
+        const float Fmx = nFmx, Fmy = nFmy, psi = npsi, lvx_t = nlvx, lvy_t = nlvy, lrho_t = nlrho, th = nth;
+        const float lth_t = nlth;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int a = a4[k];
-        int xs = x - EXd[a];
-        if (xs < 0) xs += P.Lx;
-        if (xs >= P.Lx) xs -= P.Lx;
-        A.lf_out[a * pl + row + xs] += A.lf[a * pl + row + x];
+        for (int a = 0; a < 9; ++a) {
+            f[a] = nf[a];
+            lo[a] = nl[a];
+        }
+        if (L <= ch) store_ring(L + 1);
+        if (L + 1 <= ch) {
+            load_in(L + 1);
+            load_ring(L + 2);
+        }
+        __syncthreads();
+
+        // ---- C: row L
+        float n_lrho = 0.f, n_lpsi = 0.f, n_rho = 0.f;
+        if (L <= ch) {
+            const int y = L;
+            const bool wall = y == 0 || y == Ly - 1;
+            wall_fill(P, y, f);
+            float gx, gy, hx, hy, dvx, dvy;  // 12 D of ldrx, ldry, ldivv (gy, hx unused)
+            grad12(ring(0, y - 1), ring(0, y), ring(0, y + 1), gx, gy);
+            grad12(ring(1, y - 1), ring(1, y), ring(1, y + 1), hx, hy);
+            grad12(ring(2, y - 1), ring(2, y), ring(2, y + 1), dvx, dvy);
+            // lambda of f*^{n+1} here: lf part + lr of the cell that pulled it
+#pragma unroll
+            for (int a = 0; a < 9; ++a) lo[a] += ring(3, y + EYd[a])[EXd[a]];
+            const float lr_c = -(gx + hy) * (1.f / 12.f);
+            const float lvx_c = -dvx * (1.f / 12.f), lvy_c = -dvy * (1.f / 12.f);
+            // rho, j, F, v of the step (Eqs. 6, 9, 22)
+            const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            const float jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+            const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+            const float Fx = Fmx;
+            float Fy = Fmy;
+            if (!wall) {
+                if (y == 1) Fy += P.gw6 * psi * psi;
+                Fy -= P.g * (rho - P.rho_ave);
+            }
+            const float irho = rcp_a(rho);
+            const float vx = (jx + 0.5f * Fx) * irho, vy = (jy + 0.5f * Fy) * irho;
+            // lambda_dm = diag(1/9, 1/36, ...) M lambda_f*
+            const float Ml1 = -4.f * lo[0] - (lo[1] + lo[2] + lo[3] + lo[4]) + 2.f * (lo[5] + lo[6] + lo[7] + lo[8]);
+            const float Ml2 = 4.f * lo[0] - 2.f * (lo[1] + lo[2] + lo[3] + lo[4]) + (lo[5] + lo[6] + lo[7] + lo[8]);
+            const float Ml3 = lo[1] - lo[3] + lo[5] - lo[6] - lo[7] + lo[8];
+            const float Ml4 = -2.f * lo[1] + 2.f * lo[3] + lo[5] - lo[6] - lo[7] + lo[8];
+            const float Ml5 = lo[2] - lo[4] + lo[5] + lo[6] - lo[7] - lo[8];
+            const float Ml6 = -2.f * lo[2] + 2.f * lo[4] + lo[5] + lo[6] - lo[7] - lo[8];
+            const float Ml7 = lo[1] - lo[2] + lo[3] - lo[4];
+            const float Ml8 = lo[5] - lo[6] + lo[7] - lo[8];
+            const float ldm1 = Ml1 * (1.f / 36.f), ldm2 = Ml2 * (1.f / 36.f), ldm3 = Ml3 * (1.f / 6.f);
+            const float ldm4 = Ml4 * (1.f / 12.f), ldm5 = Ml5 * (1.f / 6.f), ldm6 = Ml6 * (1.f / 12.f);
+            const float ldm7 = Ml7 * 0.25f, ldm8 = Ml8 * 0.25f;
+            // forward quantities of dm
+            const float v2 = vx * vx + vy * vy;
+            const float m7 = f[1] - f[2] + f[3] - f[4];
+            const float m8 = f[5] - f[6] + f[7] - f[8];
+            const float ne7 = m7 - rho * (vx * vx - vy * vy);
+            const float ne8 = m8 - rho * vx * vy;
+            const float psi2 = psi * psi;
+            const float ipsi2 = psi2 > 0.f ? rcp_a(psi2) : 0.f;
+            const float R = (Fmx * Fmx + Fmy * Fmy) * ipsi2;
+            const float S7 = 2.f * (vx * Fx - vy * Fy), S8 = vx * Fy + vy * Fx;
+            const float sr = (rho - P.rho_v) * P.inv_drho;
+            const float sfr = fminf(fmaxf(sr, 0.f), 1.f);
+            const float snu = rcp_a(P.tau_v + P.dtau * sfr);
+            // dm = -Lambda (m - meq) + (I - Lambda/2) S, momentum rows dm_j = F
+            const float lne1 = -P.s_e * ldm1, lS1 = (1.f - 0.5f * P.s_e) * ldm1;
+            const float lne2 = -P.s_z * ldm2, lS2 = (1.f - 0.5f * P.s_z) * ldm2;
+            const float lne4 = -P.s_q * ldm4, lne6 = -P.s_q * ldm6;
+            float lFx = ldm3 - (1.f - 0.5f * P.s_q) * ldm4;
+            float lFy = ldm5 - (1.f - 0.5f * P.s_q) * ldm6;
+            const float lne7 = -snu * ldm7, lS7 = (1.f - 0.5f * snu) * ldm7;
+            const float lne8 = -snu * ldm8, lS8 = (1.f - 0.5f * snu) * ldm8;
+            const float lsnu = -(ne7 + 0.5f * S7) * ldm7 - (ne8 + 0.5f * S8) * ldm8;
+            // ne_k = m_k(f) - meq_k(rho, v): m part -> lambda_f = M^T lambda_m, plus
+            // the identity part of f* = f + ...
+            float lf[9];
+            lf[0] = lo[0] - 4.f * lne1 + 4.f * lne2;
+            lf[1] = lo[1] - lne1 - 2.f * lne2 - 2.f * lne4 + lne7;
+            lf[2] = lo[2] - lne1 - 2.f * lne2 - 2.f * lne6 - lne7;
+            lf[3] = lo[3] - lne1 - 2.f * lne2 + 2.f * lne4 + lne7;
+            lf[4] = lo[4] - lne1 - 2.f * lne2 + 2.f * lne6 - lne7;
+            lf[5] = lo[5] + 2.f * lne1 + lne2 + lne4 + lne6 + lne8;
+            lf[6] = lo[6] + 2.f * lne1 + lne2 - lne4 + lne6 - lne8;
+            lf[7] = lo[7] + 2.f * lne1 + lne2 - lne4 - lne6 + lne8;
+            lf[8] = lo[8] + 2.f * lne1 + lne2 + lne4 - lne6 - lne8;
+            // meq part (lambda_meq = -lambda_ne): meq1 = rho(-2 + 3v^2), meq2 = rho(1 - 3v^2),
+            // meq4 = -rho vx, meq6 = -rho vy, meq7 = rho(vx^2 - vy^2), meq8 = rho vx vy
+            const float q1 = -lne1, q2 = -lne2, q4 = -lne4, q6 = -lne6, q7 = -lne7, q8 = -lne8;
+            float lrho = q1 * (-2.f + 3.f * v2) + q2 * (1.f - 3.f * v2) - q4 * vx - q6 * vy + q7 * (vx * vx - vy * vy) +
+                         q8 * vx * vy;
+            float lvx = q1 * 6.f * rho * vx - q2 * 6.f * rho * vx - q4 * rho + q7 * 2.f * rho * vx + q8 * rho * vy;
+            float lvy = q1 * 6.f * rho * vy - q2 * 6.f * rho * vy - q6 * rho - q7 * 2.f * rho * vy + q8 * rho * vx;
+            // S (Eq. 8): S1 = 6 vF + sig_e R, S2 = -6 vF - sig_z R, S7, S8
+            const float lvF = 6.f * lS1 - 6.f * lS2;
+            const float lR = P.sig_e * lS1 - P.sig_z * lS2;
+            lvx += lvF * Fx + 2.f * lS7 * Fx + lS8 * Fy;
+            lvy += lvF * Fy - 2.f * lS7 * Fy + lS8 * Fx;
+            lFx += lvF * vx + 2.f * lS7 * vx + lS8 * vy;
+            lFy += lvF * vy - 2.f * lS7 * vy + lS8 * vx;
+            float lFmx = 0.f, lFmy = 0.f, lpsi = 0.f;
+            if (psi2 > 0.f) {
+                lFmx += 2.f * Fmx * lR * ipsi2;
+                lFmy += 2.f * Fmy * lR * ipsi2;
+                lpsi += -2.f * R * lR * psi * ipsi2;
+            }
+            // snu(rho)
+            if (sr > 0.f && sr < 1.f) lrho += lsnu * (-snu * snu * P.dtau * P.inv_drho);
+            // velocity v = (j + F/2) / rho with the thermal pass's lambda_v added
+            lvx += lvx_t + lvx_c;
+            lvy += lvy_t + lvy_c;
+            lrho += lrho_t + lr_c;
+            const float ljx = lvx * irho, ljy = lvy * irho;
+            lFx += 0.5f * ljx;
+            lFy += 0.5f * ljy;
+            lrho += -(lvx * vx + lvy * vy) * irho;
+#pragma unroll
+            for (int a = 0; a < 9; ++a) lf[a] += EXd[a] * ljx + EYd[a] * ljy;
+            // forces: F = F_m + F_ads + F_b on fluid rows, 0 on wall rows
+            const bool mine = own && y >= ys && y < ye;
+            if (!wall) {
+                lFmx += lFx;
+                lFmy += lFy;
+                lrho += -P.g * lFy;  // F_b (Eq. 9)
+                if (y == 1) {        // F_ads (Eq. 22) on the first fluid row
+                    lpsi += 2.f * P.gw6 * psi * lFy;
+                    if (mine) A.dGwx[x] += (double)(psi2 * (1.f / 6.f) * lFy);  // one cell per x on this row
+                }
+                if (psi > 0.f) lpsi += (Fmx * lFmx + Fmy * lFmy) * rcp_a(psi);  // own factor of F_m
+            } else {
+                lFmx = lFmy = 0.f;  // no force is applied on wall rows
+            }
+            *ring(4, y) = psi * lFmx;
+            *ring(5, y) = psi * lFmy;
+            if (mine) {
+                if (wall) {  // the wall row's lambda, completed by stage P
+                    float* sb = A.sb + (y == 0 ? 0 : pitch) + x;
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) sb[2 * a * pitch] = lf[a];
+                } else {  // pull-streaming transposed: lambda of f*_a(y - e_a) (always inside)
+#pragma unroll
+                    for (int a = 0; a < 9; ++a) A.lf_out[a * pl + (y - EYd[a]) * pitch + cols[1 - EXd[a]]] = lf[a];
+                }
+            }
+            n_lrho = lrho;
+            n_lpsi = lpsi;
+            n_rho = rho;
+        }
+        __syncthreads();
+
+        // ---- P: row L - 1
+        const int r = L - 1;
+        if (r >= ys && r < ye && own) {
+            const bool wall = r == 0 || r == Ly - 1;
+            const int i = r * pitch + x;
+            // F_m's neighbour sums transposed: lambda_psi += G (Dx[Qx] + Dy[Qy]);
+            // rows beyond the walls hold no cell
+            const float* xm = ring(4, r - 1);
+            const float* xc = ring(4, r);
+            const float* xp = ring(4, r + 1);
+            const float* ym = ring(5, r - 1);
+            const float* yp = ring(5, r + 1);
+            float dq = 4.f * (xc[1] - xc[-1]);
+            if (r > 0) dq += (xm[1] - xm[-1]) - (4.f * ym[0] + ym[1] + ym[-1]);
+            if (r + 1 < Ly) dq += (xp[1] - xp[-1]) + (4.f * yp[0] + yp[1] + yp[-1]);
+            const float lpsi = c_lpsi + G * (1.f / 12.f) * dq;
+            float lrho = c_lrho, lth = c_lth;
+            if (c_psi > 0.f) {  // psi^2 = 2 (p_EOS - rho/3) / G (Eq. 21)
+                const Eos e = eos(c_rho, P.Ts + c_th, P);
+                const float k = lpsi * rcp_a(G * c_psi);
+                lrho += k * (e.p_rho - 1.f / 3.f);
+                lth += k * e.p_T;
+            }
+            // q(t) = (1/Lx) sum_x -cvchi rho(x,0) (-3 th0 + 4 th1 - th2) / 2 (Sec. 3.2)
+            if (lq != 0.f && r <= 2) {
+                const float c = lq / (float)Lx * (-P.cvchi);
+                const float rho0 = r == 0 ? c_rho : A.rho[x];
+                if (r == 0) {
+                    lrho += c * 0.5f * (-3.f * c_th + 4.f * A.theta[pitch + x] - A.theta[2 * pitch + x]);
+                    lth += c * rho0 * (-1.5f);
+                } else if (r == 1) {
+                    lth += c * rho0 * 2.f;
+                } else {
+                    lth += c * rho0 * (-0.5f);
+                }
+            }
+            A.lt_out[i] = lth;
+            if (!wall) {
+                A.lr_out[i] = lrho;
+            } else {
+                A.lr_out[i] = 0.f;
+                float lf[9];
+                const float* sb = A.sb + (r == 0 ? 0 : pitch) + x;
+#pragma unroll
+                for (int a = 0; a < 9; ++a) lf[a] = sb[2 * a * pitch] + lrho;
+                // Zou-He fill transposed: the filled populations pass their
+                // adjoint to the known ones they were built from
+                if (r == 0) {
+                    lf[4] += lf[2];
+                    lf[7] += lf[5];
+                    lf[1] += -0.5f * lf[5] + 0.5f * lf[6];
+                    lf[3] += 0.5f * lf[5] - 0.5f * lf[6];
+                    lf[8] += lf[6];
+                    lf[2] = lf[5] = lf[6] = 0.f;
+                } else if (P.bc == BC_WALLS) {
+                    lf[2] += lf[4];
+                    lf[5] += lf[7];
+                    lf[1] += 0.5f * lf[7] - 0.5f * lf[8];
+                    lf[3] += -0.5f * lf[7] + 0.5f * lf[8];
+                    lf[6] += lf[8];
+                    lf[4] = lf[7] = lf[8] = 0.f;
+                }
+                // pull-streaming transposed as a scatter; where y + e_a lies
+                // beyond the wall f*_a of this cell has no consumer: 0
+#pragma unroll
+                for (int a = 0; a < 9; ++a) {
+                    const int t = r - EYd[a];
+                    if (t >= 0 && t < Ly) A.lf_out[a * pl + t * pitch + cols[1 - EXd[a]]] = lf[a];
+                    const int u = r + EYd[a];
+                    if (u < 0 || u >= Ly) A.lf_out[a * pl + i] = 0.f;
+                }
+                // the outflow top pulled populations 4, 7, 8 from its own row:
+                // f*_a(x - e_a, Ly - 1) has this second consumer besides the
+                // cell one row down, which is this thread's column too and
+                // stored its share in stage C two rows ago
+                if (P.bc == BC_TOP_OUTFLOW && r == Ly - 1) {
+                    const int row = r * pitch;
+                    A.lf_out[4 * pl + row + x] += lf[4];
+                    A.lf_out[7 * pl + row + cols[2]] += lf[7];
+                    A.lf_out[8 * pl + row + cols[0]] += lf[8];
+                }
+            }
+        }
+        c_lrho = n_lrho;
+        c_lpsi = n_lpsi;
+        c_rho = n_rho;
+        c_psi = psi;
+        c_th = th;
+        c_lth = lth_t;
     }
 }
 
@@ -736,9 +868,11 @@ __global__ void outflow_push(const StepParams P, AdjFields A) {
 // launches take ~15 us, the fused step ~20 us).
 constexpr size_t kFusedRecomputeCells = 512 * 512;
 
-// Work-buffer layout: 39 field planes, then dJ/d theta_b [pitch doubles], the
+// Work-buffer layout: 25 field planes, the wall rows' lambda of the pulled
+// populations [9][2][pitch], then dJ/d theta_b [pitch doubles], the
 // per-column dJ/dG_w parts [pitch doubles] and dJ/dG_w.
-constexpr int kPlanes = 39;
+constexpr int kPlanes = 25;
+inline size_t sb_floats(const StepParams& P) { return 18 * (size_t)P.pitch; }
 
 AdjFields fields_at(const StepParams& P, void* work) {
     float* w = (float*)work;
@@ -752,16 +886,14 @@ AdjFields fields_at(const StepParams& P, void* work) {
     AdjFields A;
     A.fstar = nullptr;
     A.theta = nullptr;
-    A.lf_in = A.lt_in = nullptr;
-    A.lf_out = A.lt_out = nullptr;
+    A.lf_in = A.lt_in = A.lr_in = nullptr;
+    A.lf_out = A.lt_out = A.lr_out = nullptr;
     A.rho = next(1);
     A.psi = next(1);
     A.jx = next(1);
     A.jy = next(1);
     A.Fmx = next(1);
     A.Fmy = next(1);
-    A.Fx = next(1);
-    A.Fy = next(1);
     A.vx = next(1);
     A.vy = next(1);
     A.drx = next(1);
@@ -774,18 +906,15 @@ AdjFields fields_at(const StepParams& P, void* work) {
     A.u2 = next(1);
     A.u3 = next(1);
     A.u4 = next(1);
-    A.lf = next(9);
     A.lrho = next(1);
-    A.lpsi = next(1);
-    A.lFmx = next(1);
-    A.lFmy = next(1);
     A.lvx = next(1);
     A.lvy = next(1);
     A.lth = next(1);
     A.ldrx = next(1);
     A.ldry = next(1);
     A.ldivv = next(1);
-    A.dTb = (double*)(w + kPlanes * pl);
+    A.sb = w + kPlanes * pl;
+    A.dTb = (double*)(A.sb + sb_floats(P));
     A.dGwx = A.dTb + P.pitch;
     A.dGw = A.dGwx + P.pitch;
     return A;
@@ -813,7 +942,8 @@ __global__ void add_wall_row(const StepParams P, const float* lt, double* dTb) {
 }  // namespace
 
 size_t adjoint_work_bytes(const StepParams& P) {
-    return sizeof(float) * (size_t)kPlanes * (size_t)P.plane + sizeof(double) * (2 * (size_t)P.pitch + 2);
+    return sizeof(float) * ((size_t)kPlanes * (size_t)P.plane + sb_floats(P)) +
+           sizeof(double) * (2 * (size_t)P.pitch + 2);
 }
 
 cudaError_t adjoint_grads_reset(const StepParams& P, void* work, cudaStream_t st) {
@@ -834,18 +964,21 @@ cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* l
 }
 
 // One reverse step: state (fstar, theta) of level n, lambda of level n+1 in
-// (lf_in, lt_in), lambda of level n out; lq = dJ/dq(t_n). L is a dual-strip
+// (lf_in with lr_in, lt_in), lambda of level n out (lf_out with lr_out,
+// lt_out); lq = dJ/dq(t_n). L is a dual-strip
 // launch shape matching P (nout, nstrips, seg_h) for the recompute.
 cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* work, const float* fstar,
-                                 const float* theta, const float* lf_in, const float* lt_in, float* lf_out,
-                                 float* lt_out, float lq, cudaStream_t st) {
+                                 const float* theta, const float* lf_in, const float* lt_in, const float* lr_in,
+                                 float* lf_out, float* lt_out, float* lr_out, float lq, cudaStream_t st) {
     AdjFields A = fields_at(P, work);
     A.fstar = fstar;
     A.theta = theta;
     A.lf_in = lf_in;
     A.lt_in = lt_in;
+    A.lr_in = lr_in;
     A.lf_out = lf_out;
     A.lt_out = lt_out;
+    A.lr_out = lr_out;
     // 32 x 8 tiles: the vertical neighbours of a warp's cells are read by the
     // warps above and below it in the same block, so they stay in L1
     const dim3 blk(32, 8), grid((P.Lx + 31) / 32, (P.Ly + 7) / 8);
@@ -856,8 +989,7 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
     Q.th_in = theta;
     Q.f_out = nullptr;
     Q.th_out = nullptr;
-    const RecomputeOut R{A.rho, A.psi, A.jx, A.jy, A.Fmx, A.Fmy, A.Fx, A.Fy, A.vx, A.vy,
-                         A.drx, A.dry, A.divv, A.ax, A.ay, A.cA, A.cB, A.u2, A.u3, A.u4};
+    const RecomputeOut R{A.rho, A.psi, A.Fmx, A.Fmy, A.drx, A.dry, A.divv, A.ax, A.ay, A.cA, A.cB, A.u2, A.u3, A.u4};
     if ((size_t)P.Lx * P.Ly >= kFusedRecomputeCells) {
         cudaError_t e = dual_recompute(Q, R, L, st);
         if (e != cudaSuccess) return e;
@@ -869,31 +1001,35 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
         fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u2, A.u3, 0.5f);
         fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u3, A.u4, 1.0f);
     }
-    // the four RK stages transposed: one column-marching launch, segments
-    // sized so that the blocks fill the GPU once
-    {
-        static int occ = 0, nsm = 0;
-        cudaError_t e = cudaSuccess;
-        if (!occ) {
-            int dev = 0;
-            e = cudaGetDevice(&dev);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(rev_thermal_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                           (int)rt_smem_bytes());
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rev_thermal_fused, RT_BD, rt_smem_bytes());
-            if (e != cudaSuccess) return e;
-            occ = occ < 1 ? 1 : occ;
-        }
-        const int nstrips = (P.Lx + RT_BD - 2 * RT_HALO - 1) / (RT_BD - 2 * RT_HALO);
-        const int nseg = std::max(1, nsm * occ / nstrips);
-        const int seg_h = std::max(16, (P.Ly + nseg - 1) / nseg);
-        const int nb = nstrips * ((P.Ly + seg_h - 1) / seg_h);
-        rev_thermal_fused<<<nb, RT_BD, rt_smem_bytes(), st>>>(P, A, seg_h);
+    // the four RK stages transposed, then the collision, forces, psi and the
+    // pull: two column-marching launches, segments sized so that the blocks
+    // fill the GPU once
+    static int nsm = 0, occ_t = 0, occ_f = 0;
+    if (!nsm) {
+        int dev = 0, n = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(rev_thermal_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rt_smem_bytes());
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, rev_thermal_fused, RT_BD, rt_smem_bytes());
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, rev_flow_fused, RF_BD, 0);
+        if (e != cudaSuccess) return e;
+        occ_t = std::max(occ_t, 1);
+        occ_f = std::max(occ_f, 1);
+        nsm = n;
     }
-    rev_collide<<<grid, blk, 0, st>>>(P, A);
-    rev_psi<<<grid, blk, 0, st>>>(P, A, lq);
-    if (P.bc == BC_TOP_OUTFLOW) outflow_push<<<(P.Lx + 127) / 128, 128, 0, st>>>(P, A);
+    auto shape = [&](int nout, int occ, int& seg_h) {  // -> number of blocks
+        const int nstrips = (P.Lx + nout - 1) / nout;
+        const int nseg = std::max(1, nsm * occ / nstrips);
+        seg_h = std::max(16, (P.Ly + nseg - 1) / nseg);
+        return nstrips * ((P.Ly + seg_h - 1) / seg_h);
+    };
+    int seg_t = 0, seg_f = 0;
+    const int nb_t = shape(RT_BD - 2 * RT_HALO, occ_t, seg_t);
+    rev_thermal_fused<<<nb_t, RT_BD, rt_smem_bytes(), st>>>(P, A, seg_t);
+    const int nb_f = shape(RF_BD - 2 * RF_HALO, occ_f, seg_f);
+    rev_flow_fused<<<nb_f, RF_BD, 0, st>>>(P, A, lq, seg_f);
     return cudaGetLastError();
 }
 

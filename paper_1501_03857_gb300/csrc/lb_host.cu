@@ -1459,7 +1459,7 @@ AdjLayout adj_layout(const lb_handle* h, const StepParams& P, int nsteps, int C)
     L.work = 0;
     L.acc = align256(L.work + adjoint_work_bytes(P));
     L.lam = align256(L.acc + sizeof(Acc));
-    L.ckpt = L.lam + 2 * state;
+    L.ckpt = L.lam + 2 * align256(sizeof(float) * 11 * (size_t)P.plane);  // lambda: lf, theta, lr
     L.seg = L.ckpt + (size_t)L.nck * state;
     L.total = L.seg + 2 * (size_t)C * state;  // two segment buffers
     (void)h;
@@ -1502,7 +1502,9 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
     void* work = s + L.work;
     Acc* acc = (Acc*)(s + L.acc);
     auto sf = [&](size_t off, int k) { return (float*)(s + off + (size_t)k * state); };
-    float* lam[2] = {sf(L.lam, 0), sf(L.lam, 1)};
+    // adjoint state, twice: lf (9 planes), lambda_theta, lr (lb_internal.h)
+    const size_t lam_state = align256(sizeof(float) * 11 * pl);
+    float* lam[2] = {(float*)(s + L.lam), (float*)(s + L.lam + lam_state)};
     cudaStream_t st = h->st;
 
     // forward: nsteps steps from the current state, J = mean q(t), checkpoints
@@ -1537,7 +1539,7 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
     // k is recomputed from its checkpoint into one of two buffers on one
     // private stream while the reverse sweep of segment k + 1 runs on another;
     // both are captured CUDA graphs.
-    LB_CUDA(cudaMemsetAsync(lam[0], 0, state, st), "clear lambda");
+    LB_CUDA(cudaMemsetAsync(lam[0], 0, lam_state, st), "clear lambda");
     LB_CUDA(adjoint_grads_reset(base, work, st), "clear gradients");
     if ((rc = aux_stream(h))) return rc;
     if (!h->adj_stream2) {
@@ -1573,8 +1575,8 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         int c = c0;
         for (int j = len - 1; j >= 0; --j) {
             const float* fs = seg_state(buf, j);
-            LB_CUDA(adjoint_reverse_step(RB, RL, work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl, lam[1 - c],
-                                         lam[1 - c] + 9 * pl, lq, q),
+            LB_CUDA(adjoint_reverse_step(RB, RL, work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl, lam[c] + 10 * pl,
+                                         lam[1 - c], lam[1 - c] + 9 * pl, lam[1 - c] + 10 * pl, lq, q),
                     "adjoint reverse step");
             c ^= 1;
         }

@@ -30,7 +30,7 @@ cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
 // wall rows). The step itself (f*, theta of the next level, heat flux) is
 // not written in this mode.
 struct RecomputeOut {
-    float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *Fx, *Fy, *vx, *vy;
+    float *rho, *psi, *Fmx, *Fmy;
     float *drx, *dry, *divv, *ax, *ay, *cA, *cB, *u2, *u3, *u4;
 };
 cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Launch& L, cudaStream_t st);
@@ -80,9 +80,14 @@ cudaError_t launch_macro(const StepParams& P, float* scratch, float* rho, float*
 // (which adds the initial wall row's lambda_theta to dJ/d theta_b).
 size_t adjoint_work_bytes(const StepParams& P);
 cudaError_t adjoint_grads_reset(const StepParams& P, void* work, cudaStream_t st);
+// The adjoint of f* travels between reverse steps in two parts: lambda of
+// f*_a at cell t is lf[a](t) + lr(t + e_a), where lr is one plane (lambda of
+// rho = sum f at the cell that pulls f*_a(t); 0 outside the domain and on
+// the wall rows and the outflow top, whose share is already in lf). Zero lf
+// and lr are a zero adjoint. The in and out planes are distinct buffers.
 cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* work, const float* fstar,
-                                 const float* theta, const float* lf_in, const float* lt_in, float* lf_out,
-                                 float* lt_out, float lq, cudaStream_t st);
+                                 const float* theta, const float* lf_in, const float* lt_in, const float* lr_in,
+                                 float* lf_out, float* lt_out, float* lr_out, float lq, cudaStream_t st);
 cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* lt0, double* dTb_host,
                                  double* dGw_host, cudaStream_t st);
 

@@ -447,14 +447,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
                 const bool st = S || (r >= ys && r < ye);
                 if constexpr (REC) {
                     if (st) {
-                        put(R->jx, y, jxP);
-                        put(R->jy, y, jyP);
-                        put(R->Fmx, y, Fmx);
+                        put(R->Fmx, y, Fmx);  // F and v follow from these, psi, rho and f
                         put(R->Fmy, y, Fmy);
-                        put(R->Fx, y, Fx);
-                        put(R->Fy, y, Fy);
-                        put(R->vx, y, vx);
-                        put(R->vy, y, vy);
                     }
                 } else if (st && (outa || outb)) {
                     T o[9];
