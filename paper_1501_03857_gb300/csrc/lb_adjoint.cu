@@ -4,10 +4,10 @@
 // Eq. 22.
 //
 // Forward intermediates of step n are recomputed from the stored state
-// (f*^n, theta^n): on large domains by the fused step itself in its
-// recompute mode (lb_step3.cu, RecomputeOut), on small ones by field kernels
-// (one thread per cell) that follow its formulas. The reverse passes then
-// transpose each part of the step in the opposite order:
+// (f*^n, theta^n) by the fused step itself in its recompute mode
+// (lb_step3.cu, RecomputeOut), which the adjoint driver runs while it
+// replays a checkpoint segment. The reverse passes then transpose each part
+// of the step in the opposite order:
 //
 //   RK4 of Eq. 18 (stage 4 .. 1)   -> lambda_theta, lambda of the per-cell
 //   and the coefficients              coefficients (ax, ay, cA, cB), then
@@ -52,53 +52,14 @@ __device__ __forceinline__ float rsqrt_a(float a) {
 __device__ constexpr int EXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int EYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
-// stencil weights for offset (dx, dy): first derivatives (Lee and Lin) and
-// the Laplacian; the first-derivative weights are also Eq. 7's w_a e_a.
-__device__ __forceinline__ float wdx(int dx, int dy) {
-    return dx == 0 ? 0.f : (dy == 0 ? dx * (1.f / 3.f) : dx * (1.f / 12.f));
-}
-__device__ __forceinline__ float wdy(int dx, int dy) {
-    return dy == 0 ? 0.f : (dx == 0 ? dy * (1.f / 3.f) : dy * (1.f / 12.f));
-}
-__device__ __forceinline__ float wlap(int dx, int dy) {
-    return (dx == 0 && dy == 0) ? (-20.f / 6.f) : ((dx == 0 || dy == 0) ? (4.f / 6.f) : (1.f / 6.f));
-}
-
-// The 3 x 3 neighbourhood of one cell (x, y): its wrapped columns and the
-// offsets of its rows, -1 for a row beyond a wall; at(dx, dy) is the index
-// of (x + dx, y + dy) or -1. Formed once per cell, so each neighbour costs
-// one select and one add.
-struct Nbr {
-    int col[3], row[3];
-    bool wall;  // (x, y) on a wall row (or the outflow top)
-    __device__ __forceinline__ int at(int dx, int dy) const {
-        const int r = row[dy + 1];
-        return r < 0 ? -1 : r + col[dx + 1];
-    }
-};
-
-__device__ __forceinline__ Nbr nbr_of(const StepParams& P, int x, int y) {
-    Nbr n;
-    n.col[0] = x == 0 ? P.Lx - 1 : x - 1;
-    n.col[1] = x;
-    n.col[2] = x == P.Lx - 1 ? 0 : x + 1;
-    const bool per = P.bc == BC_PERIODIC;
-    n.row[0] = y > 0 ? (y - 1) * P.pitch : (per ? (P.Ly - 1) * P.pitch : -1);
-    n.row[1] = y * P.pitch;
-    n.row[2] = y + 1 < P.Ly ? (y + 1) * P.pitch : (per ? 0 : -1);
-    n.wall = !per && (y == 0 || y == P.Ly - 1);
-    return n;
-}
-
 // All the field planes one adjoint step works on.
 struct AdjFields {
-    // forward intermediates of the step being reversed (jx, jy, vx, vy only
-    // in the field-kernel recompute, as its own scratch)
+    // forward intermediates of the step being reversed (RecomputeOut)
     const float* fstar;  // f*^n, 9 planes
     const float* theta;  // theta^n
-    float *rho, *psi, *jx, *jy, *Fmx, *Fmy, *vx, *vy;
-    float *drx, *dry, *divv, *ax, *ay, *cA, *cB;
-    float *u2, *u3, *u4;
+    const float *rho, *psi, *Fmx, *Fmy;
+    const float *drx, *dry, *divv, *ax, *ay, *cA, *cB;
+    const float *u2, *u3, *u4;
     // adjoints; lambda of f* is carried as lf[a](t) + lr(t + e_a) (see
     // adjoint_reverse_step in lb_internal.h)
     const float* lf_in;  // lf part of lambda of f*^{n+1}, 9 planes
@@ -114,14 +75,6 @@ struct AdjFields {
     double* dGwx;  // [Lx] dJ/dG_w contributions of each column's first fluid row
     double* dGw;   // dJ/dG_w (sum of dGwx, formed at the end)
 };
-
-__device__ __forceinline__ bool cell(const StepParams& P, int& x, int& y, int& i) {
-    x = blockIdx.x * blockDim.x + threadIdx.x;
-    y = blockIdx.y * blockDim.y + threadIdx.y;
-    i = y * P.pitch + x;
-    return x < P.Lx && y < P.Ly;
-}
-
 
 // p_EOS and its partial derivatives (Eq. 21), FP32.
 struct Eos {
@@ -145,123 +98,6 @@ __device__ __forceinline__ Eos eos(float rho, float T, const StepParams& P) {
     e.phi = phi;
     e.dphi = dphi;
     return e;
-}
-
-// Pulled and wall-filled populations of cell (x, y) from f* (Eq. 3, Zou-He
-// on the wall rows), as the step computes them.
-__device__ __forceinline__ void pull_cell(const StepParams& P, const Nbr& g, const float* __restrict__ fstar, int y,
-                                          float (&f)[9]) {
-    // the outflow top pulls its unknowns from the top row itself
-    const int rp = (g.row[2] < 0 && P.bc == BC_TOP_OUTFLOW) ? g.row[1] : g.row[2];
-    const int rows[3] = {g.row[0], g.row[1], rp};
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int r = rows[1 - EYd[a]];
-        f[a] = r < 0 ? 0.f : fstar[a * P.plane + r + g.col[1 - EXd[a]]];
-    }
-    wall_fill(P, y, f);
-}
-
-// ---- forward recompute by field kernels ---------------------------------------
-//
-// For small domains, where the fused step's 5-row pipeline halo and its
-// sequential march dominate (a 256 x 256 step takes ~20 us in it), the
-// intermediates are recomputed by these one-thread-per-cell kernels, which
-// follow the fused step's formulas.
-
-__global__ void fwd_pull(const StepParams P, AdjFields A) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Nbr g = nbr_of(P, x, y);
-    float f[9];
-    pull_cell(P, g, A.fstar, y, f);
-    float rho = 0.f;
-    for (int a = 0; a < 9; ++a) rho += f[a];
-    A.rho[i] = rho;
-    A.jx[i] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    A.jy[i] = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const float T = P.Ts + A.theta[i];
-    const float arg = P.two_over_G * (eos(rho, T, P).p - rho * (1.f / 3.f));
-    A.psi[i] = arg > 0.f ? sqrtf(arg) : 0.f;
-}
-
-__global__ void fwd_force(const StepParams P, AdjFields A) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Nbr g = nbr_of(P, x, y);
-    const bool wall = g.wall;
-    float Fmx = 0.f, Fmy = 0.f;
-    if (!wall) {
-        float sx = 0.f, sy = 0.f;
-        for (int a = 1; a < 9; ++a) {
-            const float pn = A.psi[g.at(EXd[a], EYd[a])];
-            sx += wdx(EXd[a], EYd[a]) * pn;
-            sy += wdy(EXd[a], EYd[a]) * pn;
-        }
-        Fmx = -P.G * A.psi[i] * sx;
-        Fmy = -P.G * A.psi[i] * sy;
-    }
-    float Fx = Fmx, Fy = Fmy;
-    if (!wall) {
-        if (P.bc != BC_PERIODIC && y == 1) Fy += P.gw6 * A.psi[i] * A.psi[i];
-        Fy -= P.g * (A.rho[i] - P.rho_ave);
-    }
-    A.Fmx[i] = Fmx;
-    A.Fmy[i] = Fmy;
-    A.vx[i] = (A.jx[i] + 0.5f * Fx) / A.rho[i];
-    A.vy[i] = (A.jy[i] + 0.5f * Fy) / A.rho[i];
-}
-
-__global__ void fwd_coef(const StepParams P, AdjFields A) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Nbr g = nbr_of(P, x, y);
-    if (g.wall) {
-        A.drx[i] = A.dry[i] = A.divv[i] = A.ax[i] = A.ay[i] = A.cA[i] = A.cB[i] = 0.f;
-        return;
-    }
-    float drx = 0.f, dry = 0.f, dvx = 0.f, dvy = 0.f;
-    for (int a = 1; a < 9; ++a) {
-        const int j = g.at(EXd[a], EYd[a]);
-        const float cx = wdx(EXd[a], EYd[a]), cy = wdy(EXd[a], EYd[a]);
-        drx += cx * A.rho[j];
-        dry += cy * A.rho[j];
-        dvx += cx * A.vx[j];
-        dvy += cy * A.vy[j];
-    }
-    const float rho = A.rho[i];
-    const float divv = dvx + dvy;
-    const float br = P.b * rho;
-    A.drx[i] = drx;
-    A.dry[i] = dry;
-    A.divv[i] = divv;
-    A.ax[i] = -A.vx[i] + P.chi * drx / rho;
-    A.ay[i] = -A.vy[i] + P.chi * dry / rho;
-    A.cA[i] = divv * P.R * P.inv_cv / (1.f - br);
-    A.cB[i] = divv * P.a * rho * P.inv_cv / (1.f + 2.f * br - br * br);
-}
-
-// u_out = theta + c K(u_in) on fluid rows, theta on wall rows (Eqs. 18-20).
-__global__ void fwd_stage(const StepParams P, AdjFields A, const float* u_in, float* u_out, float c) {
-    int x, y, i;
-    if (!cell(P, x, y, i)) return;
-    const Nbr g = nbr_of(P, x, y);
-    const bool wall = g.wall;
-    if (wall) {
-        u_out[i] = A.theta[i];
-        return;
-    }
-    float dx = 0.f, dy = 0.f, lap = wlap(0, 0) * u_in[i];
-    for (int a = 1; a < 9; ++a) {
-        const float un = u_in[g.at(EXd[a], EYd[a])];
-        dx += wdx(EXd[a], EYd[a]) * un;
-        dy += wdy(EXd[a], EYd[a]) * un;
-        lap += wlap(EXd[a], EYd[a]) * un;
-    }
-    const float T = P.Ts + u_in[i];
-    const float dphi = P.k1k1 - P.k0k1 / sqrtf(T);
-    const float K = A.ax[i] * dx + A.ay[i] * dy + P.chi * lap - T * (A.cA[i] - A.cB[i] * dphi);
-    u_out[i] = A.theta[i] + c * K;
 }
 
 // ---- reverse -----------------------------------------------------------------
@@ -299,10 +135,10 @@ __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFiel
 // of rows and marches up the segment one row per iteration, each thread one
 // column:
 //
-//   S  row L    : mu4 = lambda_theta'/6 (fluid rows) and its products with
-//                 ax, ay into shared rings; u4, u3 (row L), u2 (row L - 2),
-//                 theta (row L - 3); ax, ay, cA, cB, lambda-bar (own column)
-//   R4 row L-1  : stage 4 transposed (rows L-2..L) -> mu3 and its products
+//   S  row L    : mu4 = lambda_theta'/6 (fluid rows), ax, ay into shared
+//                 rings; u4, u3 (row L), u2 (row L - 2), theta (row L - 3);
+//                 cA, cB, lambda-bar (own column)
+//   R4 row L-1  : stage 4 transposed (rows L-2..L) -> mu3
 //   R3 row L-2  : stage 3 transposed -> mu2
 //   R2 row L-3  : stage 2 transposed -> mu1
 //   R1 row L-4  : stage 1 transposed; the cell's coefficient adjoints are
@@ -310,25 +146,29 @@ __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFiel
 //
 // A stage's lambda_u at x gathers c_d(x - d) mu(x - d) over the 9 cells
 // around x, with c_d(s) = ax(s) wx(d) + ay(s) wy(d) + chi wl(d) the
-// isotropic stencils of Sec. 2. With the products PX = ax mu and PY = ay mu
-// stored at the source cell, and the first-derivative weights odd in d,
-// that is lambda_u = -Dx[PX] - Dy[PY] + chi Lap[mu]: the forward stencils
-// applied to the products. Each stage reaches one column further out: 4
+// isotropic stencils of Sec. 2. With the first-derivative weights odd in d
+// that is lambda_u = -Dx[ax mu] - Dy[ay mu] + chi Lap[mu]: the forward
+// stencils applied to the products, formed at each neighbour from the ax,
+// ay and mu rings (ax, ay are the same for all four stages, so two rings
+// serve them all). Each stage reaches one column further out: 4
 // halo columns per side. The per-cell accumulators (coefficient adjoints,
 // lambda_theta) ride along with their row in registers. Walls in y only
 // (the adjoint's supported case). (Measured: this scalar form with 4 warps
 // per block runs 1.5 x faster than a paired-FP32 form over two strips,
-// whose shared rings allowed only 10 warps per SM.)
-constexpr int RT_BD = 128, RT_HALO = 4, RT_W = RT_BD + 2, RT_R = 4;  // ring rows
+// whose shared rings allowed only 10 warps per SM; rings of the products
+// ax mu, ay mu per stage took 43.5 KB per block, 5 blocks per SM.)
+// ring rows: RT_R for mu and u (3 rows read, one written per iteration),
+// RT_RA for ax, ay (read by all four stages: rows L-5..L)
+constexpr int RT_BD = 128, RT_HALO = 4, RT_W = RT_BD + 2, RT_R = 4, RT_RA = 8;
+constexpr int RT_SMN = (8 * RT_R + 2 * RT_RA) * RT_W + 3 * RT_R * RT_BD;  // floats of shared memory
 
 __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, AdjFields A, int seg_h) {
     extern __shared__ float rt_sm[];
-    float* const sPX = rt_sm;                   // per stage (4, 3, 2, 1 -> 0..3): [4][RT_R][RT_W]
-    float* const sPY = sPX + 4 * RT_R * RT_W;
-    float* const sMU = sPY + 4 * RT_R * RT_W;
+    float* const sMU = rt_sm;                   // per stage (4, 3, 2, 1 -> 0..3): [4][RT_R][RT_W]
     float* const sU = sMU + 4 * RT_R * RT_W;    // u4, u3, u2, theta: [4][RT_R][RT_W]
-    float* const sOWN = sU + 4 * RT_R * RT_W;   // ax, ay, cA, cB, lambda-bar: [5][RT_R][RT_BD]
-    constexpr int SMN = 16 * RT_R * RT_W + 5 * RT_R * RT_BD;
+    float* const sAX = sU + 4 * RT_R * RT_W;    // ax, ay: [2][RT_RA][RT_W]
+    float* const sOWN = sAX + 2 * RT_RA * RT_W;  // cA, cB, lambda-bar: [3][RT_R][RT_BD]
+    constexpr int SMN = RT_SMN;
     for (int i = threadIdx.x; i < SMN; i += RT_BD) rt_sm[i] = 0.f;
 
     const int Lx = P.Lx, Ly = P.Ly, pitch = P.pitch;
@@ -344,6 +184,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     const float chi = P.chi;
     auto own = [&](int f, int r) -> float& { return sOWN[(f * RT_R + (r & (RT_R - 1))) * RT_BD + lc]; };
     auto ring = [&](float* base, int k, int r) { return base + (k * RT_R + (r & (RT_R - 1))) * RT_W + s; };
+    auto aring = [&](int k, int r) { return sAX + (k * RT_RA + (r & (RT_RA - 1))) * RT_W + s; };  // 0 ax, 1 ay
     float acc_ax[4], acc_ay[4], acc_cA[4], acc_cB[4], acc_th[4];  // index k: the row stage k worked on
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc_ax[k] = acc_ay[k] = acc_cA[k] = acc_cB[k] = acc_th[k] = 0.f;
@@ -354,25 +195,25 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
         const bool wall = r == 0 || r == Ly - 1;
         // rows beyond the walls hold no cell: their products are 0
         const bool hm = r - 1 >= 0, hp = r + 1 < Ly;
-        const float* xm = ring(sPX, k, r - 1);
-        const float* xc = ring(sPX, k, r);
-        const float* xp = ring(sPX, k, r + 1);
-        const float* ym = ring(sPY, k, r - 1);
-        const float* yp = ring(sPY, k, r + 1);
+        const float* xm = aring(0, r - 1);
+        const float* xc = aring(0, r);
+        const float* xp = aring(0, r + 1);
+        const float* ym = aring(1, r - 1);
+        const float* yp = aring(1, r + 1);
         const float* mm = ring(sMU, k, r - 1);
         const float* mc = ring(sMU, k, r);
         const float* mp = ring(sMU, k, r + 1);
-        // 12 Dx[PX], 12 Dy[PY], 6 Lap[mu] (unweighted sums of the stencils)
-        float dxp = 4.f * (xc[1] - xc[-1]), dyp = 0.f;
+        // 12 Dx[ax mu], 12 Dy[ay mu], 6 Lap[mu] (unweighted sums of the stencils)
+        float dxp = 4.f * (xc[1] * mc[1] - xc[-1] * mc[-1]), dyp = 0.f;
         float lap = -20.f * mc[0] + 4.f * (mc[1] + mc[-1]);
         if (hm) {
-            dxp += xm[1] - xm[-1];
-            dyp -= 4.f * ym[0] + ym[1] + ym[-1];
+            dxp += xm[1] * mm[1] - xm[-1] * mm[-1];
+            dyp -= 4.f * ym[0] * mm[0] + ym[1] * mm[1] + ym[-1] * mm[-1];
             lap += 4.f * mm[0] + mm[1] + mm[-1];
         }
         if (hp) {
-            dxp += xp[1] - xp[-1];
-            dyp += 4.f * yp[0] + yp[1] + yp[-1];
+            dxp += xp[1] * mp[1] - xp[-1] * mp[-1];
+            dyp += 4.f * yp[0] * mp[0] + yp[1] * mp[1] + yp[-1] * mp[-1];
             lap += 4.f * mp[0] + mp[1] + mp[-1];
         }
         float lu = -(dxp + dyp) * (1.f / 12.f) + chi * (1.f / 6.f) * lap;
@@ -386,7 +227,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             const float rsq = rsqrt_a(T);
             const float dphi = P.k1k1 - P.k0k1 * rsq;
             const float d2phi = 0.5f * P.k0k1 * (rsq * rsq * rsq);
-            const float cA = own(2, r), cB = own(3, r);
+            const float cA = own(0, r), cB = own(1, r);
             lu += (-(cA - cB * dphi) + T * cB * d2phi) * m;
             const float ux = (uc[1] - uc[-1]) * (1.f / 3.f) + ((up[1] - um[-1]) + (um[1] - up[-1])) * (1.f / 12.f);
             const float uy = (up[0] - um[0]) * (1.f / 3.f) + ((up[1] - um[-1]) + (up[-1] - um[1])) * (1.f / 12.f);
@@ -400,7 +241,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             acc_ay[0] = lay;
             acc_cA[0] = lcA;
             acc_cB[0] = lcB;
-            acc_th[0] = own(4, r) + lu;
+            acc_th[0] = own(2, r) + lu;
         } else {
             acc_ax[k] += lax;
             acc_ay[k] += lay;
@@ -408,12 +249,9 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             acc_cB[k] += lcB;
             acc_th[k] += lu;
         }
-        if (k < 3) {  // the next stage's mu = a lambda-bar + b lambda_u on fluid rows, with its products
+        if (k < 3) {  // the next stage's mu = a lambda-bar + b lambda_u on fluid rows
             const float ab = k == 2 ? 1.f / 6.f : 1.f / 3.f, bb = k == 0 ? 1.f : 0.5f;
-            const float mn = wall ? 0.f : ab * own(4, r) + bb * lu;
-            *ring(sMU, k + 1, r) = mn;
-            *ring(sPX, k + 1, r) = own(0, r) * mn;
-            *ring(sPY, k + 1, r) = own(1, r) * mn;
+            *ring(sMU, k + 1, r) = wall ? 0.f : ab * own(2, r) + bb * lu;
         }
     };
 
@@ -454,17 +292,15 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             const bool wall = L == 0 || L == Ly - 1;
             const float mu = wall ? 0.f : n_lin * (1.f / 6.f);
             *ring(sMU, 0, L) = mu;
-            *ring(sPX, 0, L) = n_ax * mu;
-            *ring(sPY, 0, L) = n_ay * mu;
-            own(0, L) = n_ax;
-            own(1, L) = n_ay;
-            own(4, L) = wall ? 0.f : n_lin;
+            *aring(0, L) = n_ax;
+            *aring(1, L) = n_ay;
+            own(2, L) = wall ? 0.f : n_lin;
             *ring(sU, 0, L) = n_u4;
             *ring(sU, 1, L) = n_u3;
         }
         if (L - 1 >= lo && L - 1 <= hi) {  // cA, cB of row L - 1 (stage 4 there next)
-            own(2, L - 1) = n_cA;
-            own(3, L - 1) = n_cB;
+            own(0, L - 1) = n_cA;
+            own(1, L - 1) = n_cB;
         }
         if (L - 2 >= lo && L - 2 <= hi) *ring(sU, 2, L - 2) = n_u2;
         if (L - 3 >= lo && L - 3 <= hi) *ring(sU, 3, L - 3) = n_th;
@@ -500,7 +336,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     }
 }
 
-constexpr size_t rt_smem_bytes() { return sizeof(float) * (16 * (size_t)RT_R * RT_W + 5 * (size_t)RT_R * RT_BD); }
+constexpr size_t rt_smem_bytes() { return sizeof(float) * (size_t)RT_SMN; }
 
 // ---- collision, forces, psi and the pull transposed in one column-marching launch
 //
@@ -862,16 +698,10 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
     }
 }
 
-// Domains of at least this many cells recompute with the fused step (one
-// launch instead of six; at 2048^2 the reverse step takes 0.83 ms instead of
-// 0.96 ms); smaller ones with the field kernels (at 256^2 the six small
-// launches take ~15 us, the fused step ~20 us).
-constexpr size_t kFusedRecomputeCells = 512 * 512;
-
-// Work-buffer layout: 25 field planes, the wall rows' lambda of the pulled
+// Work-buffer layout: 7 field planes, the wall rows' lambda of the pulled
 // populations [9][2][pitch], then dJ/d theta_b [pitch doubles], the
 // per-column dJ/dG_w parts [pitch doubles] and dJ/dG_w.
-constexpr int kPlanes = 25;
+constexpr int kPlanes = 7;
 inline size_t sb_floats(const StepParams& P) { return 18 * (size_t)P.pitch; }
 
 AdjFields fields_at(const StepParams& P, void* work) {
@@ -888,24 +718,8 @@ AdjFields fields_at(const StepParams& P, void* work) {
     A.theta = nullptr;
     A.lf_in = A.lt_in = A.lr_in = nullptr;
     A.lf_out = A.lt_out = A.lr_out = nullptr;
-    A.rho = next(1);
-    A.psi = next(1);
-    A.jx = next(1);
-    A.jy = next(1);
-    A.Fmx = next(1);
-    A.Fmy = next(1);
-    A.vx = next(1);
-    A.vy = next(1);
-    A.drx = next(1);
-    A.dry = next(1);
-    A.divv = next(1);
-    A.ax = next(1);
-    A.ay = next(1);
-    A.cA = next(1);
-    A.cB = next(1);
-    A.u2 = next(1);
-    A.u3 = next(1);
-    A.u4 = next(1);
+    A.rho = A.psi = A.Fmx = A.Fmy = nullptr;
+    A.drx = A.dry = A.divv = A.ax = A.ay = A.cA = A.cB = A.u2 = A.u3 = A.u4 = nullptr;
     A.lrho = next(1);
     A.lvx = next(1);
     A.lvy = next(1);
@@ -963,11 +777,11 @@ cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* l
     return e;
 }
 
-// One reverse step: state (fstar, theta) of level n, lambda of level n+1 in
-// (lf_in with lr_in, lt_in), lambda of level n out (lf_out with lr_out,
-// lt_out); lq = dJ/dq(t_n). L is a dual-strip
+// One reverse step: state (fstar, theta) of level n and the intermediates R
+// of the step from it, lambda of level n+1 in (lf_in with lr_in, lt_in),
+// lambda of level n out (lf_out with lr_out, lt_out); lq = dJ/dq(t_n). L is a dual-strip
 // launch shape matching P (nout, nstrips, seg_h) for the recompute.
-cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* work, const float* fstar,
+cudaError_t adjoint_reverse_step(const StepParams& P, const RecomputeOut& R, void* work, const float* fstar,
                                  const float* theta, const float* lf_in, const float* lt_in, const float* lr_in,
                                  float* lf_out, float* lt_out, float* lr_out, float lq, cudaStream_t st) {
     AdjFields A = fields_at(P, work);
@@ -979,28 +793,20 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* wor
     A.lf_out = lf_out;
     A.lt_out = lt_out;
     A.lr_out = lr_out;
-    // 32 x 8 tiles: the vertical neighbours of a warp's cells are read by the
-    // warps above and below it in the same block, so they stay in L1
-    const dim3 blk(32, 8), grid((P.Lx + 31) / 32, (P.Ly + 7) / 8);
-    // the step's intermediates from (f*^n, theta^n): written by the fused step
-    // on large domains, by the field kernels above on small ones
-    StepParams Q = P;
-    Q.f_in = fstar;
-    Q.th_in = theta;
-    Q.f_out = nullptr;
-    Q.th_out = nullptr;
-    const RecomputeOut R{A.rho, A.psi, A.Fmx, A.Fmy, A.drx, A.dry, A.divv, A.ax, A.ay, A.cA, A.cB, A.u2, A.u3, A.u4};
-    if ((size_t)P.Lx * P.Ly >= kFusedRecomputeCells) {
-        cudaError_t e = dual_recompute(Q, R, L, st);
-        if (e != cudaSuccess) return e;
-    } else {
-        fwd_pull<<<grid, blk, 0, st>>>(P, A);
-        fwd_force<<<grid, blk, 0, st>>>(P, A);
-        fwd_coef<<<grid, blk, 0, st>>>(P, A);
-        fwd_stage<<<grid, blk, 0, st>>>(P, A, theta, A.u2, 0.5f);
-        fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u2, A.u3, 0.5f);
-        fwd_stage<<<grid, blk, 0, st>>>(P, A, A.u3, A.u4, 1.0f);
-    }
+    A.rho = R.rho;
+    A.psi = R.psi;
+    A.Fmx = R.Fmx;
+    A.Fmy = R.Fmy;
+    A.drx = R.drx;
+    A.dry = R.dry;
+    A.divv = R.divv;
+    A.ax = R.ax;
+    A.ay = R.ay;
+    A.cA = R.cA;
+    A.cB = R.cB;
+    A.u2 = R.u2;
+    A.u3 = R.u3;
+    A.u4 = R.u4;
     // the four RK stages transposed, then the collision, forces, psi and the
     // pull: two column-marching launches, segments sized so that the blocks
     // fill the GPU once

@@ -1448,7 +1448,7 @@ int lb_batch_destroy(lb_batch* b) {
 namespace {
 
 struct AdjLayout {
-    size_t work, acc, lam, ckpt, seg, total;
+    size_t work, acc, lam, ckpt, seg, rec, total;
     int nck;
 };
 
@@ -1461,7 +1461,9 @@ AdjLayout adj_layout(const lb_handle* h, const StepParams& P, int nsteps, int C)
     L.lam = align256(L.acc + sizeof(Acc));
     L.ckpt = L.lam + 2 * align256(sizeof(float) * 11 * (size_t)P.plane);  // lambda: lf, theta, lr
     L.seg = L.ckpt + (size_t)L.nck * state;
-    L.total = L.seg + 2 * (size_t)C * state;  // two segment buffers
+    L.rec = L.seg + 2 * (size_t)C * state;  // two segment buffers of states
+    // and of the forward intermediates of each of their steps
+    L.total = L.rec + 2 * (size_t)C * align256(sizeof(float) * kRecomputePlanes * (size_t)P.plane);
     (void)h;
     return L;
 }
@@ -1555,28 +1557,37 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
     LB_CUDA(cudaStreamWaitEvent(rs, h->adj_in, 0), "cudaStreamWaitEvent");
     LB_CUDA(cudaStreamWaitEvent(cs, h->adj_in, 0), "cudaStreamWaitEvent");
     auto seg_state = [&](int buf, int j) { return sf(L.seg, buf * C + j); };
+    const size_t rec_stride = align256(sizeof(float) * kRecomputePlanes * pl);
+    auto seg_rec = [&](int buf, int j) {  // the intermediates of step j of segment buffer buf
+        float* r = (float*)(s + L.rec + (size_t)(buf * C + j) * rec_stride);
+        return RecomputeOut{r,           r + pl,      r + 2 * pl,  r + 3 * pl,  r + 4 * pl,
+                            r + 5 * pl,  r + 6 * pl,  r + 7 * pl,  r + 8 * pl,  r + 9 * pl,
+                            r + 10 * pl, r + 11 * pl, r + 12 * pl, r + 13 * pl};
+    };
+    // A segment is replayed from its checkpoint by the fused step in its
+    // recompute mode: each step writes the next state and its own forward
+    // intermediates (the last writes only the intermediates), so the reverse
+    // steps need no recomputation of their own.
     auto recompute = [&](int len, int buf, cudaStream_t q) -> int {
-        for (int j = 1; j < len; ++j) {
+        for (int j = 0; j < len; ++j) {
             StepParams P = base;
             P.acc = acc;
-            P.f_in = seg_state(buf, j - 1);
-            P.th_in = seg_state(buf, j - 1) + 9 * pl;
-            P.f_out = seg_state(buf, j);
-            P.th_out = seg_state(buf, j) + 9 * pl;
-            LB_CUDA(launch_step(P, h->launch, q), "adjoint recompute step");
+            P.f_in = seg_state(buf, j);
+            P.th_in = seg_state(buf, j) + 9 * pl;
+            const bool out = j + 1 < len;
+            P.f_out = out ? seg_state(buf, j + 1) : nullptr;
+            P.th_out = out ? seg_state(buf, j + 1) + 9 * pl : nullptr;
+            LB_CUDA(dual_recompute(P, seg_rec(buf, j), out, h->launch, q), "adjoint recompute step");
         }
         return LB_OK;
     };
-    // the reverse step recomputes the step's intermediates with the fused
-    // step in its write-out mode, in the current launch shape
-    const Launch RL = h->launch;
     const StepParams RB = base;
     auto sweep = [&](int len, int buf, int c0, cudaStream_t q) -> int {
         int c = c0;
         for (int j = len - 1; j >= 0; --j) {
             const float* fs = seg_state(buf, j);
-            LB_CUDA(adjoint_reverse_step(RB, RL, work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl, lam[c] + 10 * pl,
-                                         lam[1 - c], lam[1 - c] + 9 * pl, lam[1 - c] + 10 * pl, lq, q),
+            LB_CUDA(adjoint_reverse_step(RB, seg_rec(buf, j), work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl,
+                                         lam[c] + 10 * pl, lam[1 - c], lam[1 - c] + 9 * pl, lam[1 - c] + 10 * pl, lq, q),
                     "adjoint reverse step");
             c ^= 1;
         }
@@ -1619,7 +1630,7 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         LB_CUDA(cudaMemcpyAsync(seg_state(buf, 0), sf(L.ckpt, k), sizeof(float) * 10 * pl, cudaMemcpyDeviceToDevice,
                                 cs),
                 "checkpoint copy");
-        if (len > 1) {
+        {
             cudaGraphExec_t g = nullptr;
             int r = graph_of(0, len, buf, 0, cs, &g);
             if (r) return r;

@@ -27,13 +27,14 @@ cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
 // (lb_step3.cu) into pitched [Ly][pitch] planes. The gradients drx, dry and
 // div v carry the stencil weights; ax, ay, cA, cB are the coefficients of
 // K(T), Eq. 18 (0 on the wall rows); u2-u4 the RK stage inputs (theta on the
-// wall rows). The step itself (f*, theta of the next level, heat flux) is
-// not written in this mode.
+// wall rows). With out the step itself is written too (f*, theta of the
+// next level to P.f_out, P.th_out); the heat flux never is in this mode.
 struct RecomputeOut {
     float *rho, *psi, *Fmx, *Fmy;
     float *drx, *dry, *divv, *ax, *ay, *cA, *cB, *u2, *u3, *u4;
 };
-cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Launch& L, cudaStream_t st);
+constexpr int kRecomputePlanes = 14;  // the planes of RecomputeOut, in its order
+cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, const Launch& L, cudaStream_t st);
 
 // The same step over a table of independent instances in one launch
 // (paired FP32, block_x 64 or 128); instance i owns blocks
@@ -85,7 +86,9 @@ cudaError_t adjoint_grads_reset(const StepParams& P, void* work, cudaStream_t st
 // rho = sum f at the cell that pulls f*_a(t); 0 outside the domain and on
 // the wall rows and the outflow top, whose share is already in lf). Zero lf
 // and lr are a zero adjoint. The in and out planes are distinct buffers.
-cudaError_t adjoint_reverse_step(const StepParams& P, const Launch& L, void* work, const float* fstar,
+// R holds the forward intermediates of the step being reversed (written by
+// dual_recompute from the same state).
+cudaError_t adjoint_reverse_step(const StepParams& P, const RecomputeOut& R, void* work, const float* fstar,
                                  const float* theta, const float* lf_in, const float* lt_in, const float* lr_in,
                                  float* lf_out, float* lt_out, float* lr_out, float lq, cudaStream_t st);
 cudaError_t adjoint_grads_finish(const StepParams& P, void* work, const float* lt0, double* dTb_host,

@@ -257,10 +257,11 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
 // inv_drho, rho_v, cvchi): the same struct as P for one domain, or the
 // batch's shared constants in the parameter bank while P is an instance's
 // copy in shared memory. With REC (the adjoint's recompute mode) the block
-// writes the forward intermediates of its own cells to R instead of the
-// collided populations, theta^{t+1} and the heat flux (RecomputeOut,
-// lb_internal.h).
-template <int BD, class T, bool REC = false, bool CG = false>
+// writes the forward intermediates of its own cells to R (RecomputeOut,
+// lb_internal.h) and no heat flux; with OUT it writes the collided
+// populations and theta^{t+1} (the plain step: OUT without REC; the
+// adjoint's replay of a checkpoint segment: both).
+template <int BD, class T, bool REC = false, bool CG = false, bool OUT = !REC>
 __device__ __forceinline__ void step_body(const StepParams& P, const StepParams& K, const int block,
                                           const RecomputeOut* R = nullptr) {
     constexpr int W = BD + 2;
@@ -450,7 +451,8 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
                         put(R->Fmx, y, Fmx);  // F and v follow from these, psi, rho and f
                         put(R->Fmy, y, Fmy);
                     }
-                } else if (st && (outa || outb)) {
+                }
+                if (OUT && st && (outa || outb)) {
                     T o[9];
                     collide2(fP, rhoP, vx, vy, Fx, Fy, g2, K, o);
                     const int pl = P.plane;
@@ -576,7 +578,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
         // ---- F: RK stage 4 and theta^{t+1} of row L-5
         {
             const int r = L - 5;
-            if (!REC && (S || (r >= ys && r < ye)) && (outa || outb)) {
+            if (OUT && (S || (r >= ys && r < ye)) && (outa || outb)) {
                 const int y = periodic ? wrap_row(yL - 5, Ly) : r;
                 const T thr(*LB_SMP(sTH + (r & 7) * W + s));
                 T tnew = thr;
@@ -684,10 +686,11 @@ constexpr auto dual_kernel() {
     else return lb_step_dual<BD, MINB, T>;
 }
 
-// The forward intermediates of one step for the adjoint (paired FP32).
-template <int BD, int MINB>
+// The forward intermediates of one step for the adjoint (paired FP32); with
+// OUT also the step itself (f_out, th_out).
+template <int BD, int MINB, bool OUT>
 __global__ void __launch_bounds__(BD, MINB) lb_step_recompute(const StepParams P, const __grid_constant__ RecomputeOut R) {
-    step_body<BD, P2, true>(P, P, blockIdx.x, &R);
+    step_body<BD, P2, true, false, OUT>(P, P, blockIdx.x, &R);
 }
 
 // Many independent simulations in one launch (the boiling-curve batch): the
@@ -982,23 +985,27 @@ namespace {
 
 template <int BD, int MINB>
 cudaError_t recompute_prepare_t() {
-    return cudaFuncSetAttribute(lb_step_recompute<BD, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(lb_step_recompute<BD, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)DualKernel<BD, MINB, P2>::smem());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(lb_step_recompute<BD, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)DualKernel<BD, MINB, P2>::smem());
 }
 
 template <int BD, int MINB>
-cudaError_t recompute_t(const StepParams& P, const RecomputeOut& R, int nblocks, cudaStream_t st) {
-    lb_step_recompute<BD, MINB><<<nblocks, BD, DualKernel<BD, MINB, P2>::smem(), st>>>(P, R);
+cudaError_t recompute_t(const StepParams& P, const RecomputeOut& R, bool out, int nblocks, cudaStream_t st) {
+    if (out) lb_step_recompute<BD, MINB, true><<<nblocks, BD, DualKernel<BD, MINB, P2>::smem(), st>>>(P, R);
+    else lb_step_recompute<BD, MINB, false><<<nblocks, BD, DualKernel<BD, MINB, P2>::smem(), st>>>(P, R);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, const Launch& L, cudaStream_t st) {
+cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, const Launch& L, cudaStream_t st) {
     const int nb = L.nstrips * L.nseg;
-    if (L.block_x == 64) return recompute_t<64, 6>(P, R, nb, st);
-    if (L.block_x == 128) return recompute_t<128, 3>(P, R, nb, st);
-    if (L.block_x == 256) return recompute_t<256, 2>(P, R, nb, st);
+    if (L.block_x == 64) return recompute_t<64, 6>(P, R, out, nb, st);
+    if (L.block_x == 128) return recompute_t<128, 3>(P, R, out, nb, st);
+    if (L.block_x == 256) return recompute_t<256, 2>(P, R, out, nb, st);
     return cudaErrorInvalidValue;
 }
 
