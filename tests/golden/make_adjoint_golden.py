@@ -16,7 +16,7 @@ For p = G_w and for the uniform shift of T_b(x): D(h) = (J(p + h) -
 J(p - h)) / (2 h) at h = 2e-4 and 1e-4, and the extrapolated value
 (4 D(h/2) - D(h)) / 3, whose error is O(h^4).
 
-Usage: python tests/golden/make_adjoint_golden.py [threads]  (about 10
+Usage: python tests/golden/make_adjoint_golden.py [threads]  (about 40
 minutes on 8 threads)
 """
 
