@@ -56,12 +56,16 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("outflow", [False, True])
-def test_adjoint_matches_oracle_autograd(lb, outflow):
+@pytest.mark.parametrize("Lx,Ly,outflow", [(24, 16, False), (24, 16, True), (24, 17, False), (24, 17, True),
+                                           (130, 17, True)])
+def test_adjoint_matches_oracle_autograd(lb, Lx, Ly, outflow):
     """Walls, and the outflow top (whose top row pulls populations 4, 7, 8
-    from itself, so their f* has two consumers)."""
+    from itself, so their f* has two consumers). The reverse kernels march
+    segments of 4 rows here: with Ly = 17 the top row would be a segment of
+    its own and is joined to the one below; Lx = 130 takes two column strips
+    of each reverse kernel."""
     n = 12
-    cfg, rho0, prof, P, f0, th0 = setup(lb, bc=lb.BC_TOP_OUTFLOW if outflow else None)
+    cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=Lx, Ly=Ly, bc=lb.BC_TOP_OUTFLOW if outflow else None)
     tb = torch.tensor(prof, dtype=F64, requires_grad=True)
     gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
     Jo = oracle_J(P, f0, th0, tb, gw, n)
