@@ -182,27 +182,36 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     const int ys = seg * seg_h, ye = min(ys + seg_h, Ly);
     const int lo = max(ys - RT_HALO, 0), hi = min(ye + RT_HALO - 1, Ly - 1);  // rows loaded
     const float chi = P.chi;
-    auto own = [&](int f, int r) -> float& { return sOWN[(f * RT_R + (r & (RT_R - 1))) * RT_BD + lc]; };
-    auto ring = [&](float* base, int k, int r) { return base + (k * RT_R + (r & (RT_R - 1))) * RT_W + s; };
-    auto aring = [&](int k, int r) { return sAX + (k * RT_RA + (r & (RT_RA - 1))) * RT_W + s; };  // 0 ax, 1 ay
+    // this thread's slot of row L - j in the rings, j = 0..5, set at the
+    // start of iteration L; a ring field is a fixed offset from it, so every
+    // shared access is a register plus an immediate
+    float* p4[6];  // mu and u rings (RT_R slots)
+    float* p8[6];  // ax, ay rings (RT_RA slots)
+    float* q4[6];  // own-column values (RT_R slots)
+    auto own = [&](int f, int j) -> float& { return q4[j][f * RT_R * RT_BD]; };  // 0 cA, 1 cB, 2 lambda-bar
+    auto mu = [&](int k, int j) { return p4[j] + k * RT_R * RT_W; };
+    auto uu = [&](int k, int j) { return p4[j] + (4 + k) * RT_R * RT_W; };
+    auto aring = [&](int k, int j) { return p8[j] + k * RT_RA * RT_W; };  // 0 ax, 1 ay
     float acc_ax[4], acc_ay[4], acc_cA[4], acc_cB[4], acc_th[4];  // index k: the row stage k worked on
 #pragma unroll
     for (int k = 0; k < 4; ++k) acc_ax[k] = acc_ay[k] = acc_cA[k] = acc_cB[k] = acc_th[k] = 0.f;
     __syncthreads();
 
-    // stage k (0: stage 4 .. 3: stage 1) at row r
+    // stage k (0: stage 4 .. 3: stage 1) at row r = L - 1 - k (slot k + 1;
+    // its rows r - 1 and r + 1 are slots k + 2 and k)
     auto stage = [&](const int k, const int r) {
         const bool wall = r == 0 || r == Ly - 1;
         // rows beyond the walls hold no cell: their products are 0
         const bool hm = r - 1 >= 0, hp = r + 1 < Ly;
-        const float* xm = aring(0, r - 1);
-        const float* xc = aring(0, r);
-        const float* xp = aring(0, r + 1);
-        const float* ym = aring(1, r - 1);
-        const float* yp = aring(1, r + 1);
-        const float* mm = ring(sMU, k, r - 1);
-        const float* mc = ring(sMU, k, r);
-        const float* mp = ring(sMU, k, r + 1);
+        const int jm = k + 2, jc = k + 1, jp = k;
+        const float* xm = aring(0, jm);
+        const float* xc = aring(0, jc);
+        const float* xp = aring(0, jp);
+        const float* ym = aring(1, jm);
+        const float* yp = aring(1, jp);
+        const float* mm = mu(k, jm);
+        const float* mc = mu(k, jc);
+        const float* mp = mu(k, jp);
         // 12 Dx[ax mu], 12 Dy[ay mu], 6 Lap[mu] (unweighted sums of the stencils)
         float dxp = 4.f * (xc[1] * mc[1] - xc[-1] * mc[-1]), dyp = 0.f;
         float lap = -20.f * mc[0] + 4.f * (mc[1] + mc[-1]);
@@ -220,14 +229,14 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
         const float m = mc[0];
         float lax = 0.f, lay = 0.f, lcA = 0.f, lcB = 0.f;
         if (!wall && m != 0.f) {
-            const float* um = ring(sU, k, r - 1);
-            const float* uc = ring(sU, k, r);
-            const float* up = ring(sU, k, r + 1);
+            const float* um = uu(k, jm);
+            const float* uc = uu(k, jc);
+            const float* up = uu(k, jp);
             const float T = P.Ts + uc[0];
             const float rsq = rsqrt_a(T);
             const float dphi = P.k1k1 - P.k0k1 * rsq;
             const float d2phi = 0.5f * P.k0k1 * (rsq * rsq * rsq);
-            const float cA = own(0, r), cB = own(1, r);
+            const float cA = own(0, jc), cB = own(1, jc);
             lu += (-(cA - cB * dphi) + T * cB * d2phi) * m;
             const float ux = (uc[1] - uc[-1]) * (1.f / 3.f) + ((up[1] - um[-1]) + (um[1] - up[-1])) * (1.f / 12.f);
             const float uy = (up[0] - um[0]) * (1.f / 3.f) + ((up[1] - um[-1]) + (up[-1] - um[1])) * (1.f / 12.f);
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             acc_ay[0] = lay;
             acc_cA[0] = lcA;
             acc_cB[0] = lcB;
-            acc_th[0] = own(2, r) + lu;
+            acc_th[0] = own(2, jc) + lu;
         } else {
             acc_ax[k] += lax;
             acc_ay[k] += lay;
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
         }
         if (k < 3) {  // the next stage's mu = a lambda-bar + b lambda_u on fluid rows
             const float ab = k == 2 ? 1.f / 6.f : 1.f / 3.f, bb = k == 0 ? 1.f : 0.5f;
-            *ring(sMU, k + 1, r) = wall ? 0.f : ab * own(2, r) + bb * lu;
+            *mu(k + 1, jc) = wall ? 0.f : ab * own(2, jc) + bb * lu;
         }
     };
 
@@ -287,23 +296,28 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     };
     prefetch(lo);
     for (int L = lo; L <= hi + RT_HALO; ++L) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            p4[j] = rt_sm + ((L - j) & (RT_R - 1)) * RT_W + s;
+            p8[j] = sAX + ((L - j) & (RT_RA - 1)) * RT_W + s;
+            q4[j] = sOWN + ((L - j) & (RT_R - 1)) * RT_BD + lc;
+        }
         // ---- S: the prefetched row into the rings, then the next one's loads
         if (L <= hi) {
             const bool wall = L == 0 || L == Ly - 1;
-            const float mu = wall ? 0.f : n_lin * (1.f / 6.f);
-            *ring(sMU, 0, L) = mu;
-            *aring(0, L) = n_ax;
-            *aring(1, L) = n_ay;
-            own(2, L) = wall ? 0.f : n_lin;
-            *ring(sU, 0, L) = n_u4;
-            *ring(sU, 1, L) = n_u3;
+            *mu(0, 0) = wall ? 0.f : n_lin * (1.f / 6.f);
+            *aring(0, 0) = n_ax;
+            *aring(1, 0) = n_ay;
+            own(2, 0) = wall ? 0.f : n_lin;
+            *uu(0, 0) = n_u4;
+            *uu(1, 0) = n_u3;
         }
         if (L - 1 >= lo && L - 1 <= hi) {  // cA, cB of row L - 1 (stage 4 there next)
-            own(0, L - 1) = n_cA;
-            own(1, L - 1) = n_cB;
+            own(0, 1) = n_cA;
+            own(1, 1) = n_cB;
         }
-        if (L - 2 >= lo && L - 2 <= hi) *ring(sU, 2, L - 2) = n_u2;
-        if (L - 3 >= lo && L - 3 <= hi) *ring(sU, 3, L - 3) = n_th;
+        if (L - 2 >= lo && L - 2 <= hi) *uu(2, 2) = n_u2;
+        if (L - 3 >= lo && L - 3 <= hi) *uu(3, 3) = n_th;
         const float o_rho = n_rho, o_dv = n_dv, o_drx = n_drx, o_dry = n_dry;  // row L - 4
         prefetch(L + 1);
         __syncthreads();
