@@ -1024,17 +1024,37 @@ int batch_layout(lb_batch* b) {
     if (occ < 1) return fail(LB_E_INVAL, "batch block_x %d does not fit on an SM", b->block_x);
     const int waves = std::max(1, b->tpb);
     const int nout = b->block_x - 2 * HALO;
-    long long cells = 0;
-    for (lb_handle* h : b->inst) cells += (long long)h->grid.Lx * h->grid.Ly;
+    // Without a requested height every tile gets about the same number of
+    // rows: a block costs its rows (plus the pipeline's halo) whatever share
+    // of its columns the instance fills, and the step lasts as long as its
+    // longest tile. S is the smallest height at which the tiles still fit in
+    // `waves` waves; an instance splits its rows into ceil(Ly / S) equal
+    // segments.
+    auto nstrips_of = [&](const lb_handle* h) { return (h->grid.Lx + 2 * nout - 1) / (2 * nout); };
+    int S = 8;
+    if (b->seg_req <= 0) {
+        const long long cap = (long long)nsm * occ * waves;
+        auto tiles_at = [&](int height) {
+            long long t = 0;
+            for (lb_handle* h : b->inst) t += (long long)nstrips_of(h) * ((h->grid.Ly + height - 1) / height);
+            return t;
+        };
+        int hi = 8;
+        for (lb_handle* h : b->inst) hi = std::max(hi, h->grid.Ly);
+        while (S < hi) {  // the smallest height whose tiles fit (tiles_at falls as the height grows)
+            const int mid = S + (hi - S) / 2;
+            if (tiles_at(mid) <= cap) hi = mid;
+            else S = mid + 1;
+        }
+    }
     b->h_off.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
         lb_handle* h = b->inst[i];
-        const int nstrips = (h->grid.Lx + 2 * nout - 1) / (2 * nout);
+        const int nstrips = nstrips_of(h);
         int seg = b->seg_req;
         if (seg <= 0) {
-            const double share = (double)h->grid.Lx * h->grid.Ly / (double)cells;
-            const int nseg = std::max(1, (int)(share * nsm * occ * waves / nstrips));
-            seg = std::max(8, (h->grid.Ly + nseg - 1) / nseg);
+            const int nseg = (h->grid.Ly + S - 1) / S;
+            seg = (h->grid.Ly + nseg - 1) / nseg;
         }
         h->launch.block_x = b->block_x;
         h->launch.seg_rows = seg;
