@@ -868,8 +868,12 @@ __global__ void __launch_bounds__(BD, MINB) lb_batch_persist(const StepParams K,
 
 namespace {
 
-// blocks per SM the shared-constant batch kernel is compiled for
-constexpr int BATCH_K_MINB64 = 8, BATCH_K_MINB128 = 4;
+// blocks per SM the batch kernels (per-step and persistent) are compiled for:
+// at 64 threads the single-domain step's 6 (up to 168 registers, and shared
+// memory left to L1 for the pulled rows) measured faster than 8 (128
+// registers) on the 48-instance curve batch: 0.177 against 0.185 ms per
+// batched step, both launch forms
+constexpr int BATCH_MINB64 = 6, BATCH_MINB128 = 4;
 
 template <int BD, int MINB, class T>
 struct DualKernel {
@@ -953,14 +957,14 @@ cudaError_t dual_prepare_t() {
 }
 
 cudaError_t batch_prepare_t() {
-    cudaError_t e = DualKernel<64, 8, P2>::prepare_batch();
-    if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_batch();
-    if (e == cudaSuccess) e = DualKernel<64, BATCH_K_MINB64, P2>::prepare_batch_k();
-    if (e == cudaSuccess) e = DualKernel<128, BATCH_K_MINB128, P2>::prepare_batch_k();
-    if (e == cudaSuccess) e = DualKernel<64, 8, P2>::prepare_persist<true>();
-    if (e == cudaSuccess) e = DualKernel<64, 8, P2>::prepare_persist<false>();
-    if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_persist<true>();
-    if (e == cudaSuccess) e = DualKernel<128, 4, P2>::prepare_persist<false>();
+    cudaError_t e = DualKernel<64, BATCH_MINB64, P2>::prepare_batch();
+    if (e == cudaSuccess) e = DualKernel<128, BATCH_MINB128, P2>::prepare_batch();
+    if (e == cudaSuccess) e = DualKernel<64, BATCH_MINB64, P2>::prepare_batch_k();
+    if (e == cudaSuccess) e = DualKernel<128, BATCH_MINB128, P2>::prepare_batch_k();
+    if (e == cudaSuccess) e = DualKernel<64, BATCH_MINB64, P2>::prepare_persist<true>();
+    if (e == cudaSuccess) e = DualKernel<64, BATCH_MINB64, P2>::prepare_persist<false>();
+    if (e == cudaSuccess) e = DualKernel<128, BATCH_MINB128, P2>::prepare_persist<true>();
+    if (e == cudaSuccess) e = DualKernel<128, BATCH_MINB128, P2>::prepare_persist<false>();
     return e;
 }
 
@@ -1027,33 +1031,33 @@ cudaError_t batch_prepare() { return batch_prepare_t(); }
 
 cudaError_t batch_occupancy(int block_x, bool shared_k, int* n) {
     if (shared_k)
-        return block_x == 64 ? DualKernel<64, BATCH_K_MINB64, P2>::occupancy_batch_k(n)
-                             : DualKernel<128, BATCH_K_MINB128, P2>::occupancy_batch_k(n);
-    return block_x == 64 ? DualKernel<64, 8, P2>::occupancy_batch(n) : DualKernel<128, 4, P2>::occupancy_batch(n);
+        return block_x == 64 ? DualKernel<64, BATCH_MINB64, P2>::occupancy_batch_k(n)
+                             : DualKernel<128, BATCH_MINB128, P2>::occupancy_batch_k(n);
+    return block_x == 64 ? DualKernel<64, BATCH_MINB64, P2>::occupancy_batch(n) : DualKernel<128, BATCH_MINB128, P2>::occupancy_batch(n);
 }
 
 cudaError_t persist_occupancy(int block_x, bool shared_k, int* n) {
     if (block_x == 64)
-        return shared_k ? DualKernel<64, 8, P2>::occupancy_persist<true>(n) : DualKernel<64, 8, P2>::occupancy_persist<false>(n);
-    return shared_k ? DualKernel<128, 4, P2>::occupancy_persist<true>(n) : DualKernel<128, 4, P2>::occupancy_persist<false>(n);
+        return shared_k ? DualKernel<64, BATCH_MINB64, P2>::occupancy_persist<true>(n) : DualKernel<64, BATCH_MINB64, P2>::occupancy_persist<false>(n);
+    return shared_k ? DualKernel<128, BATCH_MINB128, P2>::occupancy_persist<true>(n) : DualKernel<128, BATCH_MINB128, P2>::occupancy_persist<false>(n);
 }
 
 cudaError_t persist_launch(int block_x, const StepParams* K, const PersistArgs& A, int nblocks, cudaStream_t st) {
     const StepParams k0 = K ? *K : StepParams{};
     if (block_x == 64)
-        return K ? DualKernel<64, 8, P2>::launch_persist<true>(k0, A, nblocks, st)
-                 : DualKernel<64, 8, P2>::launch_persist<false>(k0, A, nblocks, st);
-    return K ? DualKernel<128, 4, P2>::launch_persist<true>(k0, A, nblocks, st)
-             : DualKernel<128, 4, P2>::launch_persist<false>(k0, A, nblocks, st);
+        return K ? DualKernel<64, BATCH_MINB64, P2>::launch_persist<true>(k0, A, nblocks, st)
+                 : DualKernel<64, BATCH_MINB64, P2>::launch_persist<false>(k0, A, nblocks, st);
+    return K ? DualKernel<128, BATCH_MINB128, P2>::launch_persist<true>(k0, A, nblocks, st)
+             : DualKernel<128, BATCH_MINB128, P2>::launch_persist<false>(k0, A, nblocks, st);
 }
 
 cudaError_t batch_launch(int block_x, const StepParams* table, const int* block_off, int n, int nblocks,
                          const StepParams* K, cudaStream_t st) {
     if (K)
-        return block_x == 64 ? DualKernel<64, BATCH_K_MINB64, P2>::launch_batch_k(*K, table, block_off, n, nblocks, st)
-                             : DualKernel<128, BATCH_K_MINB128, P2>::launch_batch_k(*K, table, block_off, n, nblocks, st);
-    return block_x == 64 ? DualKernel<64, 8, P2>::launch_batch(table, block_off, n, nblocks, st)
-                         : DualKernel<128, 4, P2>::launch_batch(table, block_off, n, nblocks, st);
+        return block_x == 64 ? DualKernel<64, BATCH_MINB64, P2>::launch_batch_k(*K, table, block_off, n, nblocks, st)
+                             : DualKernel<128, BATCH_MINB128, P2>::launch_batch_k(*K, table, block_off, n, nblocks, st);
+    return block_x == 64 ? DualKernel<64, BATCH_MINB64, P2>::launch_batch(table, block_off, n, nblocks, st)
+                         : DualKernel<128, BATCH_MINB128, P2>::launch_batch(table, block_off, n, nblocks, st);
 }
 
 }  // namespace lbgpu
