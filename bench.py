@@ -350,6 +350,18 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     t0 = time.perf_counter()
     J, dTb, dGw = sim.adjoint(nsteps, ckpt)
     t_adj = (time.perf_counter() - t0) * 1e3
+    # the same window with every step stored (checkpoint every step: no
+    # replay, about 24 planes of scratch per step), timed the same way
+    sim.load(blob)
+    sim.adjoint(nsteps, 1)
+    sim.load(blob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J1, dTb1, dGw1 = sim.adjoint(nsteps, 1)
+    t_all = (time.perf_counter() - t0) * 1e3
+    store_all = {"ckpt_every": 1, "ms_adjoint_total": t_all, "cost_ratio": t_all / t_fwd,
+                 "scratch_gb": sim.adjoint_scratch_bytes(nsteps, 1) / 1e9,
+                 "same_gradients": bool(J1 == J and np.array_equal(dTb1, dTb) and dGw1 == dGw)}
     h = 1e-4
     fd_tb = (forward_J(dtb=h) - forward_J(dtb=-h)) / (2 * h)
     fd_gw = (forward_J(dgw=h) - forward_J(dgw=-h)) / (2 * h)
@@ -371,6 +383,7 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
                 "what": "FP64 oracle central differences, h = 2e-4 and 1e-4, Richardson-extrapolated"}
     return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "J": J, "vs_fp64_reference": fp64,
             "ms_forward": t_fwd, "ms_adjoint_total": t_adj, "cost_ratio": t_adj / t_fwd,
+            "store_every_step": store_all,
             "mlups_adjoint": L * L * nsteps / (t_adj * 1e-3) / 1e6,
             "mlups_forward": L * L * nsteps / (t_fwd * 1e-3) / 1e6,
             "dJ_dTb_uniform": float(dTb.sum()), "fd_uniform": fd_tb,
@@ -441,9 +454,19 @@ def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
     t0 = time.perf_counter()
     sim.adjoint(nsteps, ckpt)
     t_adj = (time.perf_counter() - t0) * 1e3
+    # every step stored (checkpoint every step: no replay)
+    sim.load(blob)
+    sim.adjoint(nsteps, 1)
+    sim.load(blob)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.adjoint(nsteps, 1)
+    t_all = (time.perf_counter() - t0) * 1e3
+    scratch_all = sim.adjoint_scratch_bytes(nsteps, 1)
     sim.close()
     cells = L * L
     rev_ms = (t_adj - t_fwd) / nsteps
+    rev_all = (t_all - t_fwd) / nsteps
     peak, _ = measured_peaks()
     achieved = ADJ_BYTES_PER_LU * cells / (rev_ms * 1e-3) / 1e9
     return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "ms_forward_per_step": t_fwd / nsteps,
@@ -451,7 +474,9 @@ def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
             "mlups_adjoint": cells * nsteps / (t_adj * 1e-3) / 1e6,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "bytes_per_lu": ADJ_BYTES_PER_LU,
-                         "what": "reverse sweep incl. forward recomputation, per step"}}
+                         "what": "reverse sweep incl. forward recomputation, per step"},
+            "store_every_step": {"ckpt_every": 1, "ms_reverse_per_step": rev_all,
+                                 "cost_ratio": 1 + rev_all / (t_fwd / nsteps), "scratch_gb": scratch_all / 1e9}}
 
 
 def summary(line):
@@ -474,6 +499,10 @@ def summary(line):
             g = a["large"]
             r["adjoint"].update(reverse_ms_2048=round(g["ms_reverse_per_step"], 4), reverse_hbm_frac_2048=round(g["roofline"]["frac"], 3),
                                 cost_vs_forward_2048=round(1 + g["ms_reverse_per_step"] / g["ms_forward_per_step"], 2))
+            if g.get("store_every_step"):
+                r["adjoint"]["cost_vs_forward_2048_every_step_stored"] = round(g["store_every_step"]["cost_ratio"], 2)
+        if a.get("store_every_step"):
+            r["adjoint"]["cost_vs_forward_256_every_step_stored"] = round(a["store_every_step"]["cost_ratio"], 2)
     e = line.get("experiments")
     if e:
         r["experiments"] = {"sims_per_hour": round(e["sims_per_hour"]),

@@ -191,7 +191,10 @@ int lb_destroy(lb_handle* h);
 /* ---- gradients (discrete adjoint) ----------------------------------------- */
 
 /* Device scratch lb_adjoint needs for nsteps steps with a checkpoint every
- * ckpt_every steps (work fields, checkpoints, one recomputed segment). */
+ * ckpt_every steps (work fields, checkpoints, two replayed segments with the
+ * forward intermediates of their steps: about 10 nsteps / ckpt_every + 48
+ * ckpt_every planes of Lx * Ly floats; with ckpt_every = 1, every step's
+ * state and intermediates: about 24 nsteps planes). */
 int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* bytes);
 
 /* Gradient of the window-averaged bottom-wall heat flux
@@ -201,8 +204,11 @@ int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* b
  * adjoint (reverse mode) of the step. The state at the window start is held
  * fixed except its bottom wall row, which is T_b. Runs the nsteps forward
  * steps (the simulation advances; its heat-flux accumulators are not
- * touched) storing a checkpoint every ckpt_every steps, then sweeps back
- * recomputing each segment from its checkpoint. J (host) receives the value.
+ * touched) storing a checkpoint every ckpt_every steps, then sweeps back,
+ * replaying each segment from its checkpoint. With ckpt_every = 1 the
+ * forward steps store every step's state and forward intermediates and the
+ * sweep replays nothing: faster, for ~24 planes of scratch per step. J
+ * (host) receives the value.
  * Walls or the outflow top in y, no ghost layer, thermal runs only.
  * Synchronises. */
 int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes,

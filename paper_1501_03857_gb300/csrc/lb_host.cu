@@ -1482,8 +1482,10 @@ AdjLayout adj_layout(const lb_handle* h, const StepParams& P, int nsteps, int C)
     L.ckpt = L.lam + 2 * align256(sizeof(float) * 11 * (size_t)P.plane);  // lambda: lf, theta, lr
     L.seg = L.ckpt + (size_t)L.nck * state;
     L.rec = L.seg + 2 * (size_t)C * state;  // two segment buffers of states
-    // and of the forward intermediates of each of their steps
-    L.total = L.rec + 2 * (size_t)C * align256(sizeof(float) * kRecomputePlanes * (size_t)P.plane);
+    // and of the forward intermediates of each of their steps; with a
+    // checkpoint every step, the intermediates of every step instead
+    const size_t nrec = C == 1 ? (size_t)nsteps : 2 * (size_t)C;
+    L.total = L.rec + nrec * align256(sizeof(float) * kRecomputePlanes * (size_t)P.plane);
     (void)h;
     return L;
 }
@@ -1538,7 +1540,37 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         return LB_OK;
     };
     if ((rc = save(sf(L.ckpt, 0), h->f[h->cur], h->t[h->cur]))) return rc;
-    {
+    const size_t rec_stride = align256(sizeof(float) * kRecomputePlanes * pl);
+    auto rec_at = [&](size_t k) {  // the k-th set of forward intermediates
+        float* r = (float*)(s + L.rec + k * rec_stride);
+        return RecomputeOut{r,           r + pl,      r + 2 * pl,  r + 3 * pl,  r + 4 * pl,
+                            r + 5 * pl,  r + 6 * pl,  r + 7 * pl,  r + 8 * pl,  r + 9 * pl,
+                            r + 10 * pl, r + 11 * pl, r + 12 * pl, r + 13 * pl};
+    };
+    if (C == 1) {
+        // every step stored: the forward pass runs the fused step in its
+        // recompute mode with the step's output and q(t), writing state n+1
+        // into checkpoint n+1 and the step's intermediates into set n, so the
+        // reverse sweep replays nothing
+        for (int n = 0; n < nsteps; ++n) {
+            StepParams P = base;
+            P.acc = acc;
+            P.f_in = sf(L.ckpt, n);
+            P.th_in = sf(L.ckpt, n) + 9 * pl;
+            P.f_out = sf(L.ckpt, n + 1);
+            P.th_out = sf(L.ckpt, n + 1) + 9 * pl;
+            LB_CUDA(dual_recompute(P, rec_at(n), true, true, h->launch, st), "adjoint forward step");
+            if (h->probe.n > 0) {
+                ProbeArgs A = h->probe;
+                A.f = P.f_out;
+                A.th = P.th_in;
+                LB_CUDA(launch_probe(A, st), "probe launch");
+            }
+        }
+        // the simulation advances as with the plain steps
+        if ((rc = save(h->f[h->cur], sf(L.ckpt, nsteps), sf(L.ckpt, nsteps) + 9 * pl))) return rc;
+        h->steps += nsteps;
+    } else {
         StepParams P = base;
         P.acc = acc;
         for (int n0 = 0; n0 < nsteps; n0 += C) {
@@ -1577,13 +1609,7 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
     LB_CUDA(cudaStreamWaitEvent(rs, h->adj_in, 0), "cudaStreamWaitEvent");
     LB_CUDA(cudaStreamWaitEvent(cs, h->adj_in, 0), "cudaStreamWaitEvent");
     auto seg_state = [&](int buf, int j) { return sf(L.seg, buf * C + j); };
-    const size_t rec_stride = align256(sizeof(float) * kRecomputePlanes * pl);
-    auto seg_rec = [&](int buf, int j) {  // the intermediates of step j of segment buffer buf
-        float* r = (float*)(s + L.rec + (size_t)(buf * C + j) * rec_stride);
-        return RecomputeOut{r,           r + pl,      r + 2 * pl,  r + 3 * pl,  r + 4 * pl,
-                            r + 5 * pl,  r + 6 * pl,  r + 7 * pl,  r + 8 * pl,  r + 9 * pl,
-                            r + 10 * pl, r + 11 * pl, r + 12 * pl, r + 13 * pl};
-    };
+    auto seg_rec = [&](int buf, int j) { return rec_at((size_t)(buf * C + j)); };  // step j of buffer buf
     // A segment is replayed from its checkpoint by the fused step in its
     // recompute mode: each step writes the next state and its own forward
     // intermediates (the last writes only the intermediates), so the reverse
@@ -1597,7 +1623,7 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
             const bool out = j + 1 < len;
             P.f_out = out ? seg_state(buf, j + 1) : nullptr;
             P.th_out = out ? seg_state(buf, j + 1) + 9 * pl : nullptr;
-            LB_CUDA(dual_recompute(P, seg_rec(buf, j), out, h->launch, q), "adjoint recompute step");
+            LB_CUDA(dual_recompute(P, seg_rec(buf, j), out, false, h->launch, q), "adjoint recompute step");
         }
         return LB_OK;
     };
@@ -1613,6 +1639,21 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         }
         return LB_OK;
     };
+    // every step stored (C = 1): one sweep over all of them, each reading its
+    // state and intermediates where the forward pass left them
+    auto sweep_all = [&](cudaStream_t q) -> int {
+        int c = 0;
+        for (int j = nsteps - 1; j >= 0; --j) {
+            const float* fs = sf(L.ckpt, j);
+            LB_CUDA(adjoint_reverse_step(RB, rec_at((size_t)j), work, fs, fs + 9 * pl, lam[c], lam[c] + 9 * pl,
+                                         lam[c] + 10 * pl, lam[1 - c], lam[1 - c] + 9 * pl, lam[1 - c] + 10 * pl, lq, q),
+                    "adjoint reverse step");
+            c ^= 1;
+        }
+        return LB_OK;
+    };
+    // kind 0: replay of a segment, 1: reverse sweep over a segment, 2: the
+    // sweep over every stored step
     auto graph_of = [&](int kind, int len, int buf, int c0, cudaStream_t q, cudaGraphExec_t* out) -> int {
         for (auto& g : h->adj_graphs)
             if (g.kind == kind && g.len == len && g.buf == buf && g.cur == c0 && g.C == C && g.nsteps == nsteps &&
@@ -1623,7 +1664,7 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
             }
         cudaGraph_t graph = nullptr;
         LB_CUDA(cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal), "begin capture");
-        int r = kind == 0 ? recompute(len, buf, q) : sweep(len, buf, c0, q);
+        int r = kind == 0 ? recompute(len, buf, q) : kind == 1 ? sweep(len, buf, c0, q) : sweep_all(q);
         cudaError_t e = cudaStreamEndCapture(q, &graph);
         if (r) {
             if (graph) cudaGraphDestroy(graph);
@@ -1659,9 +1700,16 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
         LB_CUDA(cudaEventRecord(h->adj_ready[buf], cs), "cudaEventRecord");
         return LB_OK;
     };
-    if ((rc = fill(kmax))) return rc;
     int cur = 0;
-    for (int k = kmax; k >= 0; --k) {
+    if (C == 1) {
+        cudaGraphExec_t g = nullptr;
+        if ((rc = graph_of(2, nsteps, 0, 0, rs, &g))) return rc;
+        LB_CUDA(cudaGraphLaunch(g, rs), "cudaGraphLaunch");
+        cur = nsteps & 1;
+    } else if ((rc = fill(kmax))) {
+        return rc;
+    }
+    for (int k = C == 1 ? -1 : kmax; k >= 0; --k) {
         const int buf = k & 1, len = std::min(C, nsteps - k * C);
         if (k > 0 && (rc = fill(k - 1))) return rc;  // overlaps the sweep below
         LB_CUDA(cudaStreamWaitEvent(rs, h->adj_ready[buf], 0), "cudaStreamWaitEvent");

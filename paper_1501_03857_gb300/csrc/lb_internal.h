@@ -28,13 +28,15 @@ cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
 // div v carry the stencil weights; ax, ay, cA, cB are the coefficients of
 // K(T), Eq. 18 (0 on the wall rows); u2-u4 the RK stage inputs (theta on the
 // wall rows). With out the step itself is written too (f*, theta of the
-// next level to P.f_out, P.th_out); the heat flux never is in this mode.
+// next level to P.f_out, P.th_out), and with heat (only with out) q(t) is
+// added to P.acc's heat-flux sums as the plain step does.
 struct RecomputeOut {
     float *rho, *psi, *Fmx, *Fmy;
     float *drx, *dry, *divv, *ax, *ay, *cA, *cB, *u2, *u3, *u4;
 };
 constexpr int kRecomputePlanes = 14;  // the planes of RecomputeOut, in its order
-cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, const Launch& L, cudaStream_t st);
+cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, bool heat, const Launch& L,
+                           cudaStream_t st);
 
 // The same step over a table of independent instances in one launch
 // (paired FP32, block_x 64 or 128); instance i owns blocks

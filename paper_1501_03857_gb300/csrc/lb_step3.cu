@@ -258,10 +258,11 @@ __device__ __forceinline__ void collide2(const T (&f)[9], T rho, T vx, T vy, T F
 // batch's shared constants in the parameter bank while P is an instance's
 // copy in shared memory. With REC (the adjoint's recompute mode) the block
 // writes the forward intermediates of its own cells to R (RecomputeOut,
-// lb_internal.h) and no heat flux; with OUT it writes the collided
-// populations and theta^{t+1} (the plain step: OUT without REC; the
-// adjoint's replay of a checkpoint segment: both).
-template <int BD, class T, bool REC = false, bool CG = false, bool OUT = !REC>
+// lb_internal.h); with OUT it writes the collided populations and
+// theta^{t+1}; with QF it adds q(t) to the heat-flux sums. The plain step is
+// OUT and QF; the adjoint's replay of a checkpoint segment REC and OUT; its
+// forward pass when it stores every step REC, OUT and QF.
+template <int BD, class T, bool REC = false, bool CG = false, bool OUT = !REC, bool QF = !REC>
 __device__ __forceinline__ void step_body(const StepParams& P, const StepParams& K, const int block,
                                           const RecomputeOut* R = nullptr) {
     constexpr int W = BD + 2;
@@ -395,7 +396,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
         __syncthreads();
 
         // ---- bottom-wall heat flux of level t (Sec. 3.2), one sample per step
-        if (!REC && !S && !periodic && ys == 0 && L == 2) {
+        if (QF && !S && !periodic && ys == 0 && L == 2) {
             double qv = 0.0;
             const float2 r0 = *LB_SMP(sRHO + 0 * W + s), t0 = *LB_SMP(sTH + 0 * W + s), t1 = *LB_SMP(sTH + 1 * W + s), t2 = *LB_SMP(sTH + 2 * W + s);
             if (outa) qv += -(double)K.cvchi * r0.x * (-3.0 * t0.x + 4.0 * t1.x - t2.x) * 0.5;
@@ -632,7 +633,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
     // the blocks finish (folding here, when the block has no work left,
     // costs nothing; folding right after the partial sums delayed that block
     // and lengthened the step by 4 %)
-    if (!REC && !periodic && ys == 0) {
+    if (QF && !periodic && ys == 0) {
         __shared__ bool s_last;
         if (lc == 0) {
             __threadfence();
@@ -687,10 +688,10 @@ constexpr auto dual_kernel() {
 }
 
 // The forward intermediates of one step for the adjoint (paired FP32); with
-// OUT also the step itself (f_out, th_out).
-template <int BD, int MINB, bool OUT>
+// OUT also the step itself (f_out, th_out), with QF also q(t).
+template <int BD, int MINB, bool OUT, bool QF>
 __global__ void __launch_bounds__(BD, MINB) lb_step_recompute(const StepParams P, const __grid_constant__ RecomputeOut R) {
-    step_body<BD, P2, true, false, OUT>(P, P, blockIdx.x, &R);
+    step_body<BD, P2, true, false, OUT, QF>(P, P, blockIdx.x, &R);
 }
 
 // Many independent simulations in one launch (the boiling-curve batch): the
@@ -989,27 +990,35 @@ namespace {
 
 template <int BD, int MINB>
 cudaError_t recompute_prepare_t() {
-    cudaError_t e = cudaFuncSetAttribute(lb_step_recompute<BD, MINB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)DualKernel<BD, MINB, P2>::smem());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(lb_step_recompute<BD, MINB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)DualKernel<BD, MINB, P2>::smem());
+    const int sm = (int)DualKernel<BD, MINB, P2>::smem();
+    cudaError_t e = cudaFuncSetAttribute(lb_step_recompute<BD, MINB, false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lb_step_recompute<BD, MINB, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(lb_step_recompute<BD, MINB, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
 }
 
 template <int BD, int MINB>
-cudaError_t recompute_t(const StepParams& P, const RecomputeOut& R, bool out, int nblocks, cudaStream_t st) {
-    if (out) lb_step_recompute<BD, MINB, true><<<nblocks, BD, DualKernel<BD, MINB, P2>::smem(), st>>>(P, R);
-    else lb_step_recompute<BD, MINB, false><<<nblocks, BD, DualKernel<BD, MINB, P2>::smem(), st>>>(P, R);
+cudaError_t recompute_t(const StepParams& P, const RecomputeOut& R, bool out, bool heat, int nblocks,
+                        cudaStream_t st) {
+    const size_t sm = DualKernel<BD, MINB, P2>::smem();
+    if (out && heat) lb_step_recompute<BD, MINB, true, true><<<nblocks, BD, sm, st>>>(P, R);
+    else if (out) lb_step_recompute<BD, MINB, true, false><<<nblocks, BD, sm, st>>>(P, R);
+    else lb_step_recompute<BD, MINB, false, false><<<nblocks, BD, sm, st>>>(P, R);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, const Launch& L, cudaStream_t st) {
+cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, bool heat, const Launch& L,
+                           cudaStream_t st) {
+    if (heat && !out) return cudaErrorInvalidValue;
     const int nb = L.nstrips * L.nseg;
-    if (L.block_x == 64) return recompute_t<64, 6>(P, R, out, nb, st);
-    if (L.block_x == 128) return recompute_t<128, 3>(P, R, out, nb, st);
-    if (L.block_x == 256) return recompute_t<256, 2>(P, R, out, nb, st);
+    if (L.block_x == 64) return recompute_t<64, 6>(P, R, out, heat, nb, st);
+    if (L.block_x == 128) return recompute_t<128, 3>(P, R, out, heat, nb, st);
+    if (L.block_x == 256) return recompute_t<256, 2>(P, R, out, heat, nb, st);
     return cudaErrorInvalidValue;
 }
 

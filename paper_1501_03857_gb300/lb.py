@@ -349,13 +349,20 @@ class Simulation:
     def sync(self):
         check(lib.lb_sync(self.h))
 
+    def adjoint_scratch_bytes(self, nsteps: int, ckpt_every: int = 100) -> int:
+        """Device scratch adjoint(nsteps, ckpt_every) allocates (lb_adjoint_scratch_bytes)."""
+        n = C.c_size_t()
+        check(lib.lb_adjoint_scratch_bytes(self.h, int(nsteps), int(ckpt_every), C.byref(n)))
+        return n.value
+
     def adjoint(self, nsteps: int, ckpt_every: int = 100):
         """J = mean wall heat flux over the next nsteps steps and its gradients
         dJ/d(T_b(x) - T_s) [Lx] and dJ/dG_w by the discrete adjoint
-        (lb_adjoint). Advances the simulation by nsteps."""
+        (lb_adjoint), with a checkpoint every ckpt_every steps; ckpt_every = 1
+        stores every step and replays none (faster, about 24 planes of
+        scratch per step). Advances the simulation by nsteps."""
         torch = self.torch
-        n = C.c_size_t()
-        check(lib.lb_adjoint_scratch_bytes(self.h, int(nsteps), int(ckpt_every), C.byref(n)))
+        n = C.c_size_t(self.adjoint_scratch_bytes(nsteps, ckpt_every))
         scratch = torch.empty(n.value + 256, dtype=torch.uint8, device="cuda")
         base = scratch.data_ptr()
         J, dGw = C.c_double(), C.c_double()
