@@ -56,21 +56,23 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+@pytest.mark.parametrize("ckpt", [5, 1])
 @pytest.mark.parametrize("Lx,Ly,outflow", [(24, 16, False), (24, 16, True), (24, 17, False), (24, 17, True),
                                            (130, 17, True)])
-def test_adjoint_matches_oracle_autograd(lb, Lx, Ly, outflow):
+def test_adjoint_matches_oracle_autograd(lb, Lx, Ly, outflow, ckpt):
     """Walls, and the outflow top (whose top row pulls populations 4, 7, 8
     from itself, so their f* has two consumers). The reverse kernels march
     segments of 4 rows here: with Ly = 17 the top row would be a segment of
     its own and is joined to the one below; Lx = 130 takes two column strips
-    of each reverse kernel."""
+    of each reverse kernel. Checkpoints every 5 steps (segments replayed) and
+    every step (every step stored by the forward pass)."""
     n = 12
     cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=Lx, Ly=Ly, bc=lb.BC_TOP_OUTFLOW if outflow else None)
     tb = torch.tensor(prof, dtype=F64, requires_grad=True)
     gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
     Jo = oracle_J(P, f0, th0, tb, gw, n)
     gtb, ggw = torch.autograd.grad(Jo, (tb, gw))
-    J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=5)
+    J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=ckpt)
     print(f"J rel {abs(J / float(Jo) - 1):.2e} dTb rel {rel(dTb, gtb.numpy()):.2e} "
           f"dGw rel {abs(dGw / float(ggw) - 1):.2e}")
     assert abs(J / float(Jo) - 1) < 1e-5
