@@ -133,9 +133,8 @@ def test_gradient_direction_at_bench_scale(lb, L):
     benchmark (500-step window after a 200-step transient, checkpoint every
     100): the FP32 forward's central difference along the normalised
     gradient g/|g| equals |g| within the 1e-3 bound, and along a direction
-    orthogonal to g it is small against |g|. At 512 x 512 the reverse steps
-    recompute the step's intermediates with the fused step kernel, at
-    256 x 256 (and in the tests above) with the field kernels."""
+    orthogonal to g it is small against |g|. Also at 512 x 512, where each
+    reverse kernel marches several column strips and many segments."""
     n = 500
     cfg = lb.Config(Lx=L, Ly=L, bc_y=lb.BC_WALLS, pool_height=0.4 * L, seed=5)
     sh, gw = 0.1 * lb.critical_temperature(cfg), 0.065
