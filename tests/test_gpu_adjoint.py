@@ -80,6 +80,26 @@ def test_adjoint_matches_oracle_autograd(lb, Lx, Ly, outflow, ckpt):
     assert abs(dGw / float(ggw) - 1) < 1e-3, (dGw, float(ggw))
 
 
+@pytest.mark.parametrize("Lx,Ly,outflow,ckpt", [(1, 3, False, 1), (1, 3, True, 3), (2, 4, True, 1), (2, 5, False, 2),
+                                                (5, 5, True, 4), (3, 9, False, 1)])
+def test_adjoint_small_grids_match_oracle_autograd(lb, Lx, Ly, outflow, ckpt):
+    """The smallest grids: one or two columns (every lane of a reverse
+    kernel's strip wraps onto them), three rows (both walls next to the one
+    fluid row), walls and outflow top, both adjoint modes."""
+    n = 6
+    cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=Lx, Ly=Ly, bc=lb.BC_TOP_OUTFLOW if outflow else None)
+    tb = torch.tensor(prof, dtype=F64, requires_grad=True)
+    gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
+    Jo = oracle_J(P, f0, th0, tb, gw, n)
+    gtb, ggw = torch.autograd.grad(Jo, (tb, gw))
+    J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=ckpt)
+    print(f"{Lx}x{Ly}: J rel {abs(J / float(Jo) - 1):.2e} dTb rel {rel(dTb, gtb.numpy()):.2e} "
+          f"dGw {dGw:.3e} oracle {float(ggw):.3e}")
+    assert abs(J / float(Jo) - 1) < 1e-5
+    assert rel(dTb, gtb.numpy()) < 1e-3, rel(dTb, gtb.numpy())
+    assert abs(dGw - float(ggw)) <= 1e-3 * abs(float(ggw)) + 1e-12, (dGw, float(ggw))
+
+
 def test_adjoint_matches_central_differences(lb):
     """Central differences (h = 1e-4) of the FP64 oracle on single cells of
     T_b, the uniform T_b mode and G_w."""
