@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     // this thread's slot of row L - j in the rings, j = 0..5, set at the
     // start of iteration L; a ring field is a fixed offset from it, so every
     // shared access is a register plus an immediate
-    float* p4[6];  // mu and u rings (RT_R slots)
-    float* p8[6];  // ax, ay rings (RT_RA slots)
-    float* q4[6];  // own-column values (RT_R slots)
+    float* p4[6] = {};  // mu and u rings (RT_R slots)
+    float* p8[6] = {};  // ax, ay rings (RT_RA slots)
+    float* q4[6] = {};  // own-column values (RT_R slots)
     auto own = [&](int f, int j) -> float& { return q4[j][f * RT_R * RT_BD]; };  // 0 cA, 1 cB, 2 lambda-bar
     auto mu = [&](int k, int j) { return p4[j] + k * RT_R * RT_W; };
     auto uu = [&](int k, int j) { return p4[j] + (4 + k) * RT_R * RT_W; };
@@ -824,21 +824,30 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const RecomputeOut& R, voi
     // the four RK stages transposed, then the collision, forces, psi and the
     // pull: two column-marching launches, segments sized so that the blocks
     // fill the GPU once
-    static int nsm = 0, occ_t = 0, occ_f = 0;
-    if (!nsm) {
-        int dev = 0, n = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(rev_thermal_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rt_smem_bytes());
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, rev_thermal_fused, RT_BD, rt_smem_bytes());
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, rev_flow_fused, RF_BD, 0);
-        if (e != cudaSuccess) return e;
-        occ_t = std::max(occ_t, 1);
-        occ_f = std::max(occ_f, 1);
-        nsm = n;
-    }
+    // SM count and blocks per SM of the two reverse kernels: looked up once
+    // (a function-local static: initialised once, also under concurrent
+    // first calls)
+    struct RevShape {
+        cudaError_t e;
+        int nsm, occ_t, occ_f;
+    };
+    static const RevShape RS = [] {
+        RevShape r{cudaSuccess, 0, 0, 0};
+        int dev = 0;
+        r.e = cudaGetDevice(&dev);
+        if (r.e == cudaSuccess) r.e = cudaDeviceGetAttribute(&r.nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (r.e == cudaSuccess)
+            r.e = cudaFuncSetAttribute(rev_thermal_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)rt_smem_bytes());
+        if (r.e == cudaSuccess)
+            r.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ_t, rev_thermal_fused, RT_BD, rt_smem_bytes());
+        if (r.e == cudaSuccess) r.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r.occ_f, rev_flow_fused, RF_BD, 0);
+        r.occ_t = std::max(r.occ_t, 1);
+        r.occ_f = std::max(r.occ_f, 1);
+        return r;
+    }();
+    if (RS.e != cudaSuccess) return RS.e;
+    const int nsm = RS.nsm, occ_t = RS.occ_t, occ_f = RS.occ_f;
     // (a floor of 4 rows per segment: on small domains more, shorter marches
     // beat fewer long ones despite the halo rows; measured cost of the 256^2,
     // 2000-step adjoint against its forward steps: 2.78x at 4, 2.90x at 1,
