@@ -52,6 +52,33 @@ __device__ __forceinline__ float rsqrt_a(float a) {
 __device__ constexpr int EXd[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int EYd[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
+// Global accesses of the reverse kernels: element i of an array of n. In the
+// checked build (LB_CHECKED) an index outside [0, n) sets ERR_BOUNDS in the
+// launch's fault flags; a load then reads element 0 instead (an index
+// select, not a branch, so the arithmetic around it compiles as in the
+// normal build) and a store is skipped. The kernels name their parameter
+// struct P.
+#ifdef LB_CHECKED
+__device__ __forceinline__ bool adj_inside(const StepParams& P, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&P.acc->err, ERR_BOUNDS);
+    return false;
+}
+#define LB_LD(p, i, n) ((p)[adj_inside(P, (long long)(i), (long long)(n)) ? (long long)(i) : 0LL])
+#define LB_ST(p, i, n, v)                                             \
+    do {                                                              \
+        if (adj_inside(P, (long long)(i), (long long)(n))) (p)[i] = (v); \
+    } while (0)
+#define LB_ADD(p, i, n, v)                                             \
+    do {                                                               \
+        if (adj_inside(P, (long long)(i), (long long)(n))) (p)[i] += (v); \
+    } while (0)
+#else
+#define LB_LD(p, i, n) ((p)[i])
+#define LB_ST(p, i, n, v) ((p)[i] = (v))
+#define LB_ADD(p, i, n, v) ((p)[i] += (v))
+#endif
+
 // All the field planes one adjoint step works on.
 struct AdjFields {
     // forward intermediates of the step being reversed (RecomputeOut)
@@ -109,8 +136,12 @@ __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFiel
                                               float lay, float lcA, float lcB, float rho, float divv, float drx,
                                               float dry) {
     if (wall) {
-        A.ldrx[i] = A.ldry[i] = A.ldivv[i] = 0.f;
-        A.lrho[i] = A.lvx[i] = A.lvy[i] = 0.f;
+        LB_ST(A.ldrx, i, P.plane, 0.f);
+        LB_ST(A.ldry, i, P.plane, 0.f);
+        LB_ST(A.ldivv, i, P.plane, 0.f);
+        LB_ST(A.lrho, i, P.plane, 0.f);
+        LB_ST(A.lvx, i, P.plane, 0.f);
+        LB_ST(A.lvy, i, P.plane, 0.f);
         return;
     }
     const float irho = rcp_a(rho);
@@ -118,13 +149,14 @@ __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFiel
     const float i1 = rcp_a(1.f - br);
     const float D = 1.f + 2.f * br - br * br, iD = rcp_a(D);
     const float dD = 2.f * P.b - 2.f * P.b * br;
-    A.ldrx[i] = P.chi * lax * irho;
-    A.ldry[i] = P.chi * lay * irho;
-    A.ldivv[i] = lcA * P.R * P.inv_cv * i1 + lcB * P.a * rho * P.inv_cv * iD;
-    A.lrho[i] = -P.chi * (drx * lax + dry * lay) * irho * irho + lcA * divv * P.R * P.inv_cv * P.b * i1 * i1 +
-                lcB * divv * P.a * P.inv_cv * (D - rho * dD) * iD * iD;
-    A.lvx[i] = -lax;
-    A.lvy[i] = -lay;
+    LB_ST(A.ldrx, i, P.plane, P.chi * lax * irho);
+    LB_ST(A.ldry, i, P.plane, P.chi * lay * irho);
+    LB_ST(A.ldivv, i, P.plane, lcA * P.R * P.inv_cv * i1 + lcB * P.a * rho * P.inv_cv * iD);
+    LB_ST(A.lrho, i, P.plane,
+          -P.chi * (drx * lax + dry * lay) * irho * irho + lcA * divv * P.R * P.inv_cv * P.b * i1 * i1 +
+              lcB * divv * P.a * P.inv_cv * (D - rho * dD) * iD * iD);
+    LB_ST(A.lvx, i, P.plane, -lax);
+    LB_ST(A.lvy, i, P.plane, -lay);
 }
 
 // ---- the four RK stages transposed in one column-marching launch ------------
@@ -273,25 +305,25 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     auto prefetch = [&](int L) {
         if (L <= hi) {
             const int i = L * pitch + x;
-            n_lin = A.lt_in[i];
-            n_ax = A.ax[i];
-            n_ay = A.ay[i];
-            n_u4 = A.u4[i];
-            n_u3 = A.u3[i];
+            n_lin = LB_LD(A.lt_in, i, P.plane);
+            n_ax = LB_LD(A.ax, i, P.plane);
+            n_ay = LB_LD(A.ay, i, P.plane);
+            n_u4 = LB_LD(A.u4, i, P.plane);
+            n_u3 = LB_LD(A.u3, i, P.plane);
         }
         if (L - 1 >= lo && L - 1 <= hi) {
             const int i = (L - 1) * pitch + x;
-            n_cA = A.cA[i];
-            n_cB = A.cB[i];
+            n_cA = LB_LD(A.cA, i, P.plane);
+            n_cB = LB_LD(A.cB, i, P.plane);
         }
-        if (L - 2 >= lo && L - 2 <= hi) n_u2 = A.u2[(L - 2) * pitch + x];
-        if (L - 3 >= lo && L - 3 <= hi) n_th = A.theta[(L - 3) * pitch + x];
+        if (L - 2 >= lo && L - 2 <= hi) n_u2 = LB_LD(A.u2, (L - 2) * pitch + x, P.plane);
+        if (L - 3 >= lo && L - 3 <= hi) n_th = LB_LD(A.theta, (L - 3) * pitch + x, P.plane);
         if (L - 4 >= ys && L - 4 < ye && out) {
             const int i = (L - 4) * pitch + x;
-            n_rho = A.rho[i];
-            n_dv = A.divv[i];
-            n_drx = A.drx[i];
-            n_dry = A.dry[i];
+            n_rho = LB_LD(A.rho, i, P.plane);
+            n_dv = LB_LD(A.divv, i, P.plane);
+            n_drx = LB_LD(A.drx, i, P.plane);
+            n_dry = LB_LD(A.dry, i, P.plane);
         }
     };
     prefetch(lo);
@@ -332,10 +364,10 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             stage(3, r);
             if (out) {
                 const int i = r * pitch + x;
-                A.lth[i] = acc_th[3];
+                LB_ST(A.lth, i, P.plane, acc_th[3]);
                 rev_coef_vals(P, A, i, r == 0 || r == Ly - 1, acc_ax[3], acc_ay[3], acc_cA[3], acc_cB[3], o_rho, o_dv,
                               o_drx, o_dry);
-                if (r == 0) A.dTb[x] += (double)A.lt_in[i];
+                if (r == 0) LB_ADD(A.dTb, x, P.pitch, (double)LB_LD(A.lt_in, i, P.plane));
             }
         }
 #pragma unroll
@@ -419,10 +451,10 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
     auto load_ring = [&](int r) {
         if (r >= 0 && r < Ly) {
             const int i = r * pitch + x;
-            nr[0] = A.ldrx[i];
-            nr[1] = A.ldry[i];
-            nr[2] = A.ldivv[i];
-            nr[3] = A.lr_in[i];
+            nr[0] = LB_LD(A.ldrx, i, pl);
+            nr[1] = LB_LD(A.ldry, i, pl);
+            nr[2] = LB_LD(A.ldivv, i, pl);
+            nr[3] = LB_LD(A.lr_in, i, pl);
         } else {
             nr[0] = nr[1] = nr[2] = nr[3] = 0.f;
         }
@@ -443,19 +475,19 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             const int rr = rows[1 - EYd[a]];
-            nf[a] = rr < 0 ? 0.f : A.fstar[a * pl + rr + cols[1 - EXd[a]]];
+            nf[a] = rr < 0 ? 0.f : LB_LD(A.fstar, a * pl + rr + cols[1 - EXd[a]], 9 * (size_t)pl);
         }
         const int i = rc + x;
 #pragma unroll
-        for (int a = 0; a < 9; ++a) nl[a] = A.lf_in[a * pl + i];
-        nFmx = A.Fmx[i];
-        nFmy = A.Fmy[i];
-        npsi = A.psi[i];
-        nlvx = A.lvx[i];
-        nlvy = A.lvy[i];
-        nlrho = A.lrho[i];
-        nth = A.theta[i];
-        nlth = A.lth[i];
+        for (int a = 0; a < 9; ++a) nl[a] = LB_LD(A.lf_in, a * pl + i, 9 * (size_t)pl);
+        nFmx = LB_LD(A.Fmx, i, pl);
+        nFmy = LB_LD(A.Fmy, i, pl);
+        npsi = LB_LD(A.psi, i, pl);
+        nlvx = LB_LD(A.lvx, i, pl);
+        nlvy = LB_LD(A.lvy, i, pl);
+        nlrho = LB_LD(A.lrho, i, pl);
+        nth = LB_LD(A.theta, i, pl);
+        nlth = LB_LD(A.lth, i, pl);
     };
     // stage C's results for stage P, carried one iteration (row L - 1)
     float c_lrho = 0.f, c_lpsi = 0.f, c_psi = 0.f, c_rho = 0.f, c_th = 0.f, c_lth = 0.f;
@@ -596,7 +628,7 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
                 lrho += -P.g * lFy;  // F_b (Eq. 9)
                 if (y == 1) {        // F_ads (Eq. 22) on the first fluid row
                     lpsi += 2.f * P.gw6 * psi * lFy;
-                    if (mine) A.dGwx[x] += (double)(psi2 * (1.f / 6.f) * lFy);  // one cell per x on this row
+                    if (mine) LB_ADD(A.dGwx, x, P.pitch, (double)(psi2 * (1.f / 6.f) * lFy));  // one cell per x on this row
                 }
                 if (psi > 0.f) lpsi += (Fmx * lFmx + Fmy * lFmy) * rcp_a(psi);  // own factor of F_m
             } else {
@@ -606,12 +638,13 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
             *ring(5, y) = psi * lFmy;
             if (mine) {
                 if (wall) {  // the wall row's lambda, completed by stage P
-                    float* sb = A.sb + (y == 0 ? 0 : pitch) + x;
+                    const int o = (y == 0 ? 0 : pitch) + x;
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) sb[2 * a * pitch] = lf[a];
+                    for (int a = 0; a < 9; ++a) LB_ST(A.sb, o + 2 * a * pitch, 18 * (size_t)pitch, lf[a]);
                 } else {  // pull-streaming transposed: lambda of f*_a(y - e_a) (always inside)
 #pragma unroll
-                    for (int a = 0; a < 9; ++a) A.lf_out[a * pl + (y - EYd[a]) * pitch + cols[1 - EXd[a]]] = lf[a];
+                    for (int a = 0; a < 9; ++a)
+                        LB_ST(A.lf_out, a * pl + (y - EYd[a]) * pitch + cols[1 - EXd[a]], 9 * (size_t)pl, lf[a]);
                 }
             }
             n_lrho = lrho;
@@ -646,9 +679,9 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
             // q(t) = (1/Lx) sum_x -cvchi rho(x,0) (-3 th0 + 4 th1 - th2) / 2 (Sec. 3.2)
             if (lq != 0.f && r <= 2) {
                 const float c = lq / (float)Lx * (-P.cvchi);
-                const float rho0 = r == 0 ? c_rho : A.rho[x];
+                const float rho0 = r == 0 ? c_rho : LB_LD(A.rho, x, pl);
                 if (r == 0) {
-                    lrho += c * 0.5f * (-3.f * c_th + 4.f * A.theta[pitch + x] - A.theta[2 * pitch + x]);
+                    lrho += c * 0.5f * (-3.f * c_th + 4.f * LB_LD(A.theta, pitch + x, pl) - LB_LD(A.theta, 2 * pitch + x, pl));
                     lth += c * rho0 * (-1.5f);
                 } else if (r == 1) {
                     lth += c * rho0 * 2.f;
@@ -656,15 +689,15 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
                     lth += c * rho0 * (-0.5f);
                 }
             }
-            A.lt_out[i] = lth;
+            LB_ST(A.lt_out, i, pl, lth);
             if (!wall) {
-                A.lr_out[i] = lrho;
+                LB_ST(A.lr_out, i, pl, lrho);
             } else {
-                A.lr_out[i] = 0.f;
+                LB_ST(A.lr_out, i, pl, 0.f);
                 float lf[9];
-                const float* sb = A.sb + (r == 0 ? 0 : pitch) + x;
+                const int o = (r == 0 ? 0 : pitch) + x;
 #pragma unroll
-                for (int a = 0; a < 9; ++a) lf[a] = sb[2 * a * pitch] + lrho;
+                for (int a = 0; a < 9; ++a) lf[a] = LB_LD(A.sb, o + 2 * a * pitch, 18 * (size_t)pitch) + lrho;
                 // Zou-He fill transposed: the filled populations pass their
                 // adjoint to the known ones they were built from
                 if (r == 0) {
@@ -687,9 +720,9 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
 #pragma unroll
                 for (int a = 0; a < 9; ++a) {
                     const int t = r - EYd[a];
-                    if (t >= 0 && t < Ly) A.lf_out[a * pl + t * pitch + cols[1 - EXd[a]]] = lf[a];
+                    if (t >= 0 && t < Ly) LB_ST(A.lf_out, a * pl + t * pitch + cols[1 - EXd[a]], 9 * (size_t)pl, lf[a]);
                     const int u = r + EYd[a];
-                    if (u < 0 || u >= Ly) A.lf_out[a * pl + i] = 0.f;
+                    if (u < 0 || u >= Ly) LB_ST(A.lf_out, a * pl + i, 9 * (size_t)pl, 0.f);
                 }
                 // the outflow top pulled populations 4, 7, 8 from its own row:
                 // f*_a(x - e_a, Ly - 1) has this second consumer besides the
@@ -697,9 +730,9 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
                 // stored its share in stage C two rows ago
                 if (P.bc == BC_TOP_OUTFLOW && r == Ly - 1) {
                     const int row = r * pitch;
-                    A.lf_out[4 * pl + row + x] += lf[4];
-                    A.lf_out[7 * pl + row + cols[2]] += lf[7];
-                    A.lf_out[8 * pl + row + cols[0]] += lf[8];
+                    LB_ADD(A.lf_out, 4 * pl + row + x, 9 * (size_t)pl, lf[4]);
+                    LB_ADD(A.lf_out, 7 * pl + row + cols[2], 9 * (size_t)pl, lf[7]);
+                    LB_ADD(A.lf_out, 8 * pl + row + cols[0], 9 * (size_t)pl, lf[8]);
                 }
             }
         }

@@ -1,7 +1,8 @@
 """Helper of test_gpu_checked.py (not a test module): steps the cases given
-on the command line with whichever library LBBOIL_LIB selects and saves the
-resulting states to an .npz file. Every run ends with a synchronising call,
-which raises if the checked build flagged an address outside its buffer."""
+on the command line, the batches and the adjoints below with whichever
+library LBBOIL_LIB selects and saves the resulting states and gradients to
+an .npz file. Every run ends with a synchronising call, which raises if the
+checked build flagged an address outside its buffer."""
 
 import json
 import sys
@@ -44,6 +45,24 @@ def run_batch(shapes, block_x=64, seg=0, vary=False, tpb=0):
     return out
 
 
+# adjoints (Lx, Ly, bc, nsteps, ckpt_every): odd sizes, one and two columns,
+# three rows, several strips and segments of both reverse kernels, walls and
+# outflow top, segments replayed and every step stored
+ADJOINTS = [(1, 3, 0, 6, 1), (2, 4, 1, 6, 3), (17, 9, 0, 8, 1), (33, 17, 1, 8, 5), (130, 17, 0, 6, 4),
+            (257, 40, 1, 5, 1), (300, 70, 0, 5, 2)]
+
+
+def run_adjoint(case):
+    Lx, Ly, bc, n, ck = case
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.45 * Ly)
+    rv, rl = lb.coexistence(cfg)
+    rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.45 * Ly, noise_amp=1e-2, seed=Lx + 7 * Ly)
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)
+    J, dTb, dGw = sim.adjoint(n, ck)
+    sim.close()
+    return np.concatenate([[J, dGw], dTb])
+
+
 def random_batch(seed=11, n=12):
     rng = np.random.default_rng(seed)
     return [(int(rng.integers(1, 200)), int(rng.integers(3, 90)), int(rng.integers(0, 3))) for _ in range(n)]
@@ -63,4 +82,6 @@ if __name__ == "__main__":
     for j, (shapes, bx, seg, vary, tpb) in enumerate(batches):
         for k, (f, t) in enumerate(run_batch(shapes, bx, seg, vary, tpb)):
             res[f"b{j}f{k}"], res[f"b{j}t{k}"] = f, t
+    for k, c in enumerate(ADJOINTS):
+        res[f"adj{k}"] = run_adjoint(c)
     np.savez(sys.argv[2], **res)

@@ -1,9 +1,11 @@
 """The checked build (liblbboil_checked.so, compiled with -DLB_CHECKED): its
-fused step checks every global and shared-memory address against its buffer
-and flags a miss as LB_E_BOUNDS instead of faulting. On grids with odd
-sizes, every boundary treatment, several launch shapes and batches of uneven
-instances (one launch per step and the persistent launch) it flags nothing
-and produces exactly the states of the normal build."""
+fused step checks every global and shared-memory address against its buffer,
+and the adjoint's reverse kernels every global address, and each flags a
+miss as LB_E_BOUNDS instead of faulting. On grids with odd sizes, every
+boundary treatment, several launch shapes, batches of uneven instances (one
+launch per step and the persistent launch) and adjoints of odd sizes (both
+modes) it flags nothing and produces exactly the states and gradients of the
+normal build."""
 
 import json
 import os
