@@ -476,7 +476,8 @@ def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
                          "frac": achieved / peak, "bytes_per_lu": ADJ_BYTES_PER_LU,
                          "what": "reverse sweep incl. forward recomputation, per step"},
             "store_every_step": {"ckpt_every": 1, "ms_reverse_per_step": rev_all,
-                                 "cost_ratio": 1 + rev_all / (t_fwd / nsteps), "scratch_gb": scratch_all / 1e9}}
+                                 "cost_ratio": 1 + rev_all / (t_fwd / nsteps), "scratch_gb": scratch_all / 1e9,
+                                 "roofline_frac": ADJ_BYTES_PER_LU * cells / (rev_all * 1e-3) / 1e9 / peak}}
 
 
 def summary(line):
