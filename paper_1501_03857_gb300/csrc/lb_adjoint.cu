@@ -188,7 +188,10 @@ __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFiel
 // (the adjoint's supported case). (Measured: this scalar form with 4 warps
 // per block runs 1.5 x faster than a paired-FP32 form over two strips,
 // whose shared rings allowed only 10 warps per SM; rings of the products
-// ax mu, ay mu per stage took 43.5 KB per block, 5 blocks per SM.)
+// ax mu, ay mu per stage took 43.5 KB per block, 5 blocks per SM. Steady
+// iterations without range and wall tests: 95 registers, 5 blocks per SM,
+// and the 2048^2 reverse step 0.374 ms instead of 0.414; held to 7 blocks
+// per SM, 72 registers with a small spill, 0.414.)
 // ring rows: RT_R for mu and u (3 rows read, one written per iteration),
 // RT_RA for ax, ay (read by all four stages: rows L-5..L)
 constexpr int RT_BD = 128, RT_HALO = 4, RT_W = RT_BD + 2, RT_R = 4, RT_RA = 8;
@@ -230,11 +233,13 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     __syncthreads();
 
     // stage k (0: stage 4 .. 3: stage 1) at row r = L - 1 - k (slot k + 1;
-    // its rows r - 1 and r + 1 are slots k + 2 and k)
-    auto stage = [&](const int k, const int r) {
-        const bool wall = r == 0 || r == Ly - 1;
+    // its rows r - 1 and r + 1 are slots k + 2 and k); in a steady iteration
+    // (S) no row of any stage is a wall row or next to one
+    auto stage = [&](const int k, const int r, auto steady) {
+        constexpr bool S = decltype(steady)::value;
+        const bool wall = !S && (r == 0 || r == Ly - 1);
         // rows beyond the walls hold no cell: their products are 0
-        const bool hm = r - 1 >= 0, hp = r + 1 < Ly;
+        const bool hm = S || r - 1 >= 0, hp = S || r + 1 < Ly;
         const int jm = k + 2, jc = k + 1, jp = k;
         const float* xm = aring(0, jm);
         const float* xc = aring(0, jc);
@@ -302,8 +307,9 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     // grad rho of row L - 4 (the output row)
     float n_lin = 0.f, n_ax = 0.f, n_ay = 0.f, n_u4 = 0.f, n_u3 = 0.f, n_cA = 0.f, n_cB = 0.f, n_u2 = 0.f, n_th = 0.f;
     float n_rho = 0.f, n_dv = 0.f, n_drx = 0.f, n_dry = 0.f;
-    auto prefetch = [&](int L) {
-        if (L <= hi) {
+    auto prefetch = [&](int L, auto steady) {
+        constexpr bool S = decltype(steady)::value;
+        if (S || L <= hi) {
             const int i = L * pitch + x;
             n_lin = LB_LD(A.lt_in, i, P.plane);
             n_ax = LB_LD(A.ax, i, P.plane);
@@ -311,14 +317,14 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             n_u4 = LB_LD(A.u4, i, P.plane);
             n_u3 = LB_LD(A.u3, i, P.plane);
         }
-        if (L - 1 >= lo && L - 1 <= hi) {
+        if (S || (L - 1 >= lo && L - 1 <= hi)) {
             const int i = (L - 1) * pitch + x;
             n_cA = LB_LD(A.cA, i, P.plane);
             n_cB = LB_LD(A.cB, i, P.plane);
         }
-        if (L - 2 >= lo && L - 2 <= hi) n_u2 = LB_LD(A.u2, (L - 2) * pitch + x, P.plane);
-        if (L - 3 >= lo && L - 3 <= hi) n_th = LB_LD(A.theta, (L - 3) * pitch + x, P.plane);
-        if (L - 4 >= ys && L - 4 < ye && out) {
+        if (S || (L - 2 >= lo && L - 2 <= hi)) n_u2 = LB_LD(A.u2, (L - 2) * pitch + x, P.plane);
+        if (S || (L - 3 >= lo && L - 3 <= hi)) n_th = LB_LD(A.theta, (L - 3) * pitch + x, P.plane);
+        if ((S || (L - 4 >= ys && L - 4 < ye)) && out) {
             const int i = (L - 4) * pitch + x;
             n_rho = LB_LD(A.rho, i, P.plane);
             n_dv = LB_LD(A.divv, i, P.plane);
@@ -326,8 +332,12 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             n_dry = LB_LD(A.dry, i, P.plane);
         }
     };
-    prefetch(lo);
-    for (int L = lo; L <= hi + RT_HALO; ++L) {
+    prefetch(lo, std::false_type{});
+    // one row iteration L; in a steady one (S) every row it touches (L - 5 ..
+    // L + 1) is loaded, off the walls and not next to them, and the output
+    // row is the block's own, so the range and wall tests are compiled out
+    auto iter = [&](const int L, auto steady) {
+        constexpr bool S = decltype(steady)::value;
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             p4[j] = rt_sm + ((L - j) & (RT_R - 1)) * RT_W + s;
@@ -335,8 +345,8 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             q4[j] = sOWN + ((L - j) & (RT_R - 1)) * RT_BD + lc;
         }
         // ---- S: the prefetched row into the rings, then the next one's loads
-        if (L <= hi) {
-            const bool wall = L == 0 || L == Ly - 1;
+        if (S || L <= hi) {
+            const bool wall = !S && (L == 0 || L == Ly - 1);
             *mu(0, 0) = wall ? 0.f : n_lin * (1.f / 6.f);
             *aring(0, 0) = n_ax;
             *aring(1, 0) = n_ay;
@@ -344,30 +354,30 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             *uu(0, 0) = n_u4;
             *uu(1, 0) = n_u3;
         }
-        if (L - 1 >= lo && L - 1 <= hi) {  // cA, cB of row L - 1 (stage 4 there next)
+        if (S || (L - 1 >= lo && L - 1 <= hi)) {  // cA, cB of row L - 1 (stage 4 there next)
             own(0, 1) = n_cA;
             own(1, 1) = n_cB;
         }
-        if (L - 2 >= lo && L - 2 <= hi) *uu(2, 2) = n_u2;
-        if (L - 3 >= lo && L - 3 <= hi) *uu(3, 3) = n_th;
+        if (S || (L - 2 >= lo && L - 2 <= hi)) *uu(2, 2) = n_u2;
+        if (S || (L - 3 >= lo && L - 3 <= hi)) *uu(3, 3) = n_th;
         const float o_rho = n_rho, o_dv = n_dv, o_drx = n_drx, o_dry = n_dry;  // row L - 4
-        prefetch(L + 1);
+        prefetch(L + 1, steady);
         __syncthreads();
-        if (L - 1 >= lo && L - 1 <= hi) stage(0, L - 1);
+        if (S || (L - 1 >= lo && L - 1 <= hi)) stage(0, L - 1, steady);
         __syncthreads();
-        if (L - 2 >= lo && L - 2 <= hi) stage(1, L - 2);
+        if (S || (L - 2 >= lo && L - 2 <= hi)) stage(1, L - 2, steady);
         __syncthreads();
-        if (L - 3 >= lo && L - 3 <= hi) stage(2, L - 3);
+        if (S || (L - 3 >= lo && L - 3 <= hi)) stage(2, L - 3, steady);
         __syncthreads();
         const int r = L - 4;
-        if (r >= ys && r < ye) {
-            stage(3, r);
+        if (S || (r >= ys && r < ye)) {
+            stage(3, r, steady);
             if (out) {
                 const int i = r * pitch + x;
                 LB_ST(A.lth, i, P.plane, acc_th[3]);
-                rev_coef_vals(P, A, i, r == 0 || r == Ly - 1, acc_ax[3], acc_ay[3], acc_cA[3], acc_cB[3], o_rho, o_dv,
-                              o_drx, o_dry);
-                if (r == 0) LB_ADD(A.dTb, x, P.pitch, (double)LB_LD(A.lt_in, i, P.plane));
+                rev_coef_vals(P, A, i, !S && (r == 0 || r == Ly - 1), acc_ax[3], acc_ay[3], acc_cA[3], acc_cB[3],
+                              o_rho, o_dv, o_drx, o_dry);
+                if (!S && r == 0) LB_ADD(A.dTb, x, P.pitch, (double)LB_LD(A.lt_in, i, P.plane));
             }
         }
 #pragma unroll
@@ -379,7 +389,15 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             acc_th[k] = acc_th[k - 1];
         }
         __syncthreads();
-    }
+    };
+    // steady iterations: the rows L - 5 .. L + 1 lie in [1, Ly - 2] and in
+    // the loaded rows, the output rows of L and L + 1 in [ys, ye)
+    const int Ls = max(max(ys + 4, 6), lo + 1);
+    const int Le = min(min(hi - 1, Ly - 2), ye + 2) + 1;
+    int L = lo;
+    for (; L < Ls; ++L) iter(L, std::false_type{});
+    for (; L < Le; ++L) iter(L, std::true_type{});
+    for (; L <= hi + RT_HALO; ++L) iter(L, std::false_type{});
 }
 
 constexpr size_t rt_smem_bytes() { return sizeof(float) * (size_t)RT_SMN; }
