@@ -433,7 +433,9 @@ constexpr size_t rt_smem_bytes() { return sizeof(float) * (size_t)RT_SMN; }
 // than its own and P one more: 2 halo columns per side. The owner's own
 // share of F_m(x) = -G psi(x) sum_a w_a psi(x + e_a) e_a is (F_m . lambda_F_m)
 // / psi; where psi = 0 (outside the EOS domain, which the forward step flags)
-// it is taken as 0.
+// it is taken as 0. Steady iterations are compiled without the range and
+// wall tests; held to 4 blocks per SM (128 registers) that measured 1 %
+// faster than before the split, 3 blocks per SM (145 registers) 2 % slower.
 constexpr int RF_BD = 128, RF_HALO = 2, RF_W = RF_BD + 2, RF_R = 4;
 
 // 12 Dx[v], 12 Dy[v] of a shared ring around lane pointer c (rows m, c, p)
@@ -442,7 +444,7 @@ __device__ __forceinline__ void grad12(const float* m, const float* c, const flo
     dy = 4.f * (p[0] - m[0]) + (p[1] - m[1]) + (p[-1] - m[-1]);
 }
 
-__global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjFields A, float lq, int seg_h) {
+__global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, AdjFields A, float lq, int seg_h) {
     // rings: 0 ldrx, 1 ldry, 2 ldivv, 3 lr_in (rows of stage C), 4 Qx, 5 Qy (stage P)
     __shared__ float sm[6 * RF_R * RF_W];
     for (int k = threadIdx.x; k < 6 * RF_R * RF_W; k += RF_BD) sm[k] = 0.f;
@@ -466,8 +468,8 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
     const float G = P.G;
 
     float nr[4];  // ring inputs of one row (0 beyond the walls)
-    auto load_ring = [&](int r) {
-        if (r >= 0 && r < Ly) {
+    auto load_ring = [&](int r, auto steady) {
+        if (decltype(steady)::value || (r >= 0 && r < Ly)) {
             const int i = r * pitch + x;
             nr[0] = LB_LD(A.ldrx, i, pl);
             nr[1] = LB_LD(A.ldry, i, pl);
@@ -486,14 +488,15 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
     // the step's F_m, psi, theta, and the thermal pass's lambda_v, lambda_rho,
     // lambda_theta
     float nf[9], nl[9], nFmx, nFmy, npsi, nlvx, nlvy, nlrho, nth, nlth;
-    auto load_in = [&](int r) {
+    auto load_in = [&](int r, auto steady) {
+        constexpr bool S = decltype(steady)::value;
         const int rc = r * pitch;
-        const int rows[3] = {r > 0 ? rc - pitch : -1, rc,
-                             r + 1 < Ly ? rc + pitch : (P.bc == BC_TOP_OUTFLOW ? rc : -1)};
+        const int rows[3] = {S || r > 0 ? rc - pitch : -1, rc,
+                             S || r + 1 < Ly ? rc + pitch : (P.bc == BC_TOP_OUTFLOW ? rc : -1)};
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
             const int rr = rows[1 - EYd[a]];
-            nf[a] = rr < 0 ? 0.f : LB_LD(A.fstar, a * pl + rr + cols[1 - EXd[a]], 9 * (size_t)pl);
+            nf[a] = !S && rr < 0 ? 0.f : LB_LD(A.fstar, a * pl + rr + cols[1 - EXd[a]], 9 * (size_t)pl);
         }
         const int i = rc + x;
 #pragma unroll
@@ -510,13 +513,18 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
     // stage C's results for stage P, carried one iteration (row L - 1)
     float c_lrho = 0.f, c_lpsi = 0.f, c_psi = 0.f, c_rho = 0.f, c_th = 0.f, c_lth = 0.f;
 
-    load_ring(cl - 1);
+    load_ring(cl - 1, std::false_type{});
     store_ring(cl - 1);
-    load_ring(cl);
+    load_ring(cl, std::false_type{});
     store_ring(cl);
-    load_ring(cl + 1);
-    load_in(cl);
-    for (int L = cl; L <= ch + 1; ++L) {
+    load_ring(cl + 1, std::false_type{});
+    load_in(cl, std::false_type{});
+    // one row iteration L; in a steady one (S) stage C's row is neither a
+    // wall row nor the first fluid row and is the block's own, stage P's row
+    // is the block's own, off the walls and above the heat-flux rows, and the
+    // next rows' loads lie inside the grid, so those tests are compiled out
+    auto iter = [&](const int L, auto steady) {
+        constexpr bool S = decltype(steady)::value;
         // ---- ring row L + 1 and this row's inputs; then row L + 1's loads
         float f[9], lo[9];
         const float Fmx = nFmx, Fmy = nFmy, psi = npsi, lvx_t = nlvx, lvy_t = nlvy, lrho_t = nlrho, th = nth;
@@ -526,18 +534,18 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
             f[a] = nf[a];
             lo[a] = nl[a];
         }
-        if (L <= ch) store_ring(L + 1);
-        if (L + 1 <= ch) {
-            load_in(L + 1);
-            load_ring(L + 2);
+        if (S || L <= ch) store_ring(L + 1);
+        if (S || L + 1 <= ch) {
+            load_in(L + 1, steady);
+            load_ring(L + 2, steady);
         }
         __syncthreads();
 
         // ---- C: row L
         float n_lrho = 0.f, n_lpsi = 0.f, n_rho = 0.f;
-        if (L <= ch) {
+        if (S || L <= ch) {
             const int y = L;
-            const bool wall = y == 0 || y == Ly - 1;
+            const bool wall = !S && (y == 0 || y == Ly - 1);
             wall_fill(P, y, f);
             float gx, gy, hx, hy, dvx, dvy;  // 12 D of ldrx, ldry, ldivv (gy, hx unused)
             grad12(ring(0, y - 1), ring(0, y), ring(0, y + 1), gx, gy);
@@ -555,7 +563,7 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
             const float Fx = Fmx;
             float Fy = Fmy;
             if (!wall) {
-                if (y == 1) Fy += P.gw6 * psi * psi;
+                if (!S && y == 1) Fy += P.gw6 * psi * psi;
                 Fy -= P.g * (rho - P.rho_ave);
             }
             const float irho = rcp_a(rho);
@@ -639,12 +647,12 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
 #pragma unroll
             for (int a = 0; a < 9; ++a) lf[a] += EXd[a] * ljx + EYd[a] * ljy;
             // forces: F = F_m + F_ads + F_b on fluid rows, 0 on wall rows
-            const bool mine = own && y >= ys && y < ye;
+            const bool mine = own && (S || (y >= ys && y < ye));
             if (!wall) {
                 lFmx += lFx;
                 lFmy += lFy;
                 lrho += -P.g * lFy;  // F_b (Eq. 9)
-                if (y == 1) {        // F_ads (Eq. 22) on the first fluid row
+                if (!S && y == 1) {  // F_ads (Eq. 22) on the first fluid row
                     lpsi += 2.f * P.gw6 * psi * lFy;
                     if (mine) LB_ADD(A.dGwx, x, P.pitch, (double)(psi2 * (1.f / 6.f) * lFy));  // one cell per x on this row
                 }
@@ -673,8 +681,8 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
 
         // ---- P: row L - 1
         const int r = L - 1;
-        if (r >= ys && r < ye && own) {
-            const bool wall = r == 0 || r == Ly - 1;
+        if ((S || (r >= ys && r < ye)) && own) {
+            const bool wall = !S && (r == 0 || r == Ly - 1);
             const int i = r * pitch + x;
             // F_m's neighbour sums transposed: lambda_psi += G (Dx[Qx] + Dy[Qy]);
             // rows beyond the walls hold no cell
@@ -684,8 +692,8 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
             const float* ym = ring(5, r - 1);
             const float* yp = ring(5, r + 1);
             float dq = 4.f * (xc[1] - xc[-1]);
-            if (r > 0) dq += (xm[1] - xm[-1]) - (4.f * ym[0] + ym[1] + ym[-1]);
-            if (r + 1 < Ly) dq += (xp[1] - xp[-1]) + (4.f * yp[0] + yp[1] + yp[-1]);
+            if (S || r > 0) dq += (xm[1] - xm[-1]) - (4.f * ym[0] + ym[1] + ym[-1]);
+            if (S || r + 1 < Ly) dq += (xp[1] - xp[-1]) + (4.f * yp[0] + yp[1] + yp[-1]);
             const float lpsi = c_lpsi + G * (1.f / 12.f) * dq;
             float lrho = c_lrho, lth = c_lth;
             if (c_psi > 0.f) {  // psi^2 = 2 (p_EOS - rho/3) / G (Eq. 21)
@@ -695,7 +703,7 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
                 lth += k * e.p_T;
             }
             // q(t) = (1/Lx) sum_x -cvchi rho(x,0) (-3 th0 + 4 th1 - th2) / 2 (Sec. 3.2)
-            if (lq != 0.f && r <= 2) {
+            if (!S && lq != 0.f && r <= 2) {
                 const float c = lq / (float)Lx * (-P.cvchi);
                 const float rho0 = r == 0 ? c_rho : LB_LD(A.rho, x, pl);
                 if (r == 0) {
@@ -760,7 +768,16 @@ __global__ void __launch_bounds__(RF_BD) rev_flow_fused(const StepParams P, AdjF
         c_psi = psi;
         c_th = th;
         c_lth = lth_t;
-    }
+    };
+    // steady iterations: stage C's row L in [max(ys, 2), min(ye, Ly - 2)),
+    // stage P's row L - 1 in [max(ys, 3), ye), the next rows' loads
+    // (L + 1 <= ch, L + 2 <= Ly - 1) inside
+    const int Ls = max(ys + 1, 4);
+    const int Le = min(min(ch - 1, Ly - 3), ye - 1) + 1;
+    int L = cl;
+    for (; L < Ls; ++L) iter(L, std::false_type{});
+    for (; L < Le; ++L) iter(L, std::true_type{});
+    for (; L <= ch + 1; ++L) iter(L, std::false_type{});
 }
 
 // Work-buffer layout: 7 field planes, the wall rows' lambda of the pulled
