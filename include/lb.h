@@ -209,7 +209,8 @@ int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* b
  * forward steps store every step's state and forward intermediates and the
  * sweep replays nothing: faster, for ~24 planes of scratch per step. J
  * (host) receives the value.
- * Walls or the outflow top in y, no ghost layer, thermal runs only.
+ * Walls or the outflow top in y, with or without the ghost layer, thermal runs
+ * only.
  * Synchronises. */
 int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes,
                double* J, double* dJ_dTb, double* dJ_dGw);

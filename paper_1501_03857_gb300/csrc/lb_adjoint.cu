@@ -26,7 +26,7 @@
 // A stencil applied forward as out(x) = sum_d c_d in(x + d) is transposed as
 // a gather lambda_in(y) += sum_d c_d lambda_out(y - d). Fields are pitched
 // [Ly][pitch] FP32; gradients are accumulated in FP64. Supported: walls in
-// y or the outflow top, no ghost layer (the host checks).
+// y or the outflow top, with or without the ghost layer (the host checks).
 #include <algorithm>
 
 #include "lb_internal.h"
@@ -646,7 +646,8 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
             lrho += -(lvx * vx + lvy * vy) * irho;
 #pragma unroll
             for (int a = 0; a < 9; ++a) lf[a] += EXd[a] * ljx + EYd[a] * ljy;
-            // forces: F = F_m + F_ads + F_b on fluid rows, 0 on wall rows
+            // forces: F = F_m + F_ads + F_b on fluid rows; on wall rows F_m
+            // with the ghost layer, else 0
             const bool mine = own && (S || (y >= ys && y < ye));
             if (!wall) {
                 lFmx += lFx;
@@ -657,6 +658,10 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
                     if (mine) LB_ADD(A.dGwx, x, P.pitch, (double)(psi2 * (1.f / 6.f) * lFy));  // one cell per x on this row
                 }
                 if (psi > 0.f) lpsi += (Fmx * lFmx + Fmy * lFmy) * rcp_a(psi);  // own factor of F_m
+            } else if (P.ghost) {
+                lFmx += lFx;
+                lFmy += lFy;
+                if (psi > 0.f) lpsi += (Fmx * lFmx + Fmy * lFmy) * rcp_a(psi);
             } else {
                 lFmx = lFmy = 0.f;  // no force is applied on wall rows
             }
@@ -694,6 +699,14 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
             float dq = 4.f * (xc[1] - xc[-1]);
             if (S || r > 0) dq += (xm[1] - xm[-1]) - (4.f * ym[0] + ym[1] + ym[-1]);
             if (S || r + 1 < Ly) dq += (xp[1] - xp[-1]) + (4.f * yp[0] + yp[1] + yp[-1]);
+            if (!S && P.ghost && wall) {
+                // the ghost row beyond this wall row is a copy of it: the
+                // row's cells that reached across the wall read psi here
+                // too (bottom: through e_y = -1, top: e_y = +1)
+                const float* yc = ring(5, r);
+                const float g = 4.f * yc[0] + yc[1] + yc[-1];
+                dq += (xc[1] - xc[-1]) + (r == 0 ? g : -g);
+            }
             const float lpsi = c_lpsi + G * (1.f / 12.f) * dq;
             float lrho = c_lrho, lth = c_lth;
             if (c_psi > 0.f) {  // psi^2 = 2 (p_EOS - rho/3) / G (Eq. 21)

@@ -1493,8 +1493,8 @@ AdjLayout adj_layout(const lb_handle* h, const StepParams& P, int nsteps, int C)
 int adjoint_check(lb_handle* h, int nsteps, int C) {
     if (!h) return fail(LB_E_INVAL, "null handle");
     if (nsteps < 1 || C < 1) return fail(LB_E_INVAL, "need nsteps >= 1 and ckpt_every >= 1");
-    if (h->grid.bc_y == LB_BC_PERIODIC || h->grid.ghost_layer || h->grid.isothermal)
-        return fail(LB_E_INVAL, "the adjoint supports wall-bounded or outflow-top, non-ghost, thermal runs only");
+    if (h->grid.bc_y == LB_BC_PERIODIC || h->grid.isothermal)
+        return fail(LB_E_INVAL, "the adjoint supports wall-bounded or outflow-top thermal runs only");
     return LB_OK;
 }
 

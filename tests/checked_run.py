@@ -49,12 +49,13 @@ def run_batch(shapes, block_x=64, seg=0, vary=False, tpb=0):
 # three rows, several strips and segments of both reverse kernels, walls and
 # outflow top, segments replayed and every step stored
 ADJOINTS = [(1, 3, 0, 6, 1), (2, 4, 1, 6, 3), (17, 9, 0, 8, 1), (33, 17, 1, 8, 5), (130, 17, 0, 6, 4),
-            (257, 40, 1, 5, 1), (300, 70, 0, 5, 2)]
+            (257, 40, 1, 5, 1), (300, 70, 0, 5, 2), (45, 13, 0, 6, 1, 1), (131, 21, 1, 6, 3, 1)]  # ..., ghost layer
 
 
 def run_adjoint(case):
-    Lx, Ly, bc, n, ck = case
-    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.45 * Ly)
+    Lx, Ly, bc, n, ck = case[:5]
+    ghost = bool(case[5]) if len(case) > 5 else False
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=bc, pool_height=0.45 * Ly, ghost_layer=ghost)
     rv, rl = lb.coexistence(cfg)
     rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.45 * Ly, noise_amp=1e-2, seed=Lx + 7 * Ly)
     sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)

@@ -22,8 +22,8 @@ def lb():
     return lbmod
 
 
-def setup(lb, Lx=24, Ly=16, superheat=0.012, Gw=0.05, seed=3, bc=None):
-    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_WALLS if bc is None else bc, pool_height=0.45 * Ly)
+def setup(lb, Lx=24, Ly=16, superheat=0.012, Gw=0.05, seed=3, bc=None, ghost=False):
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_WALLS if bc is None else bc, pool_height=0.45 * Ly, ghost_layer=ghost)
     rv, rl = lb.coexistence(cfg)
     rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.45 * Ly, noise_amp=1e-2, seed=seed)
     prof = superheat + 0.003 * np.sin(2 * np.pi * np.arange(Lx) / Lx)
@@ -74,6 +74,26 @@ def test_adjoint_matches_oracle_autograd(lb, Lx, Ly, outflow, ckpt):
     gtb, ggw = torch.autograd.grad(Jo, (tb, gw))
     J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=ckpt)
     print(f"J rel {abs(J / float(Jo) - 1):.2e} dTb rel {rel(dTb, gtb.numpy()):.2e} "
+          f"dGw rel {abs(dGw / float(ggw) - 1):.2e}")
+    assert abs(J / float(Jo) - 1) < 1e-5
+    assert rel(dTb, gtb.numpy()) < 1e-3, rel(dTb, gtb.numpy())
+    assert abs(dGw / float(ggw) - 1) < 1e-3, (dGw, float(ggw))
+
+
+@pytest.mark.parametrize("Lx,Ly,outflow,ckpt", [(24, 16, False, 5), (24, 17, True, 1), (130, 16, False, 1),
+                                                (130, 17, True, 4), (3, 5, False, 2)])
+def test_adjoint_ghost_layer_matches_oracle_autograd(lb, Lx, Ly, outflow, ckpt):
+    """The ghost-layer option (F_m also on the wall rows, from a ghost row
+    that copies the wall row's psi): walls and outflow top, both modes."""
+    n = 10
+    cfg, rho0, prof, P, f0, th0 = setup(lb, Lx=Lx, Ly=Ly, bc=lb.BC_TOP_OUTFLOW if outflow else None, ghost=True)
+    assert P.ghost
+    tb = torch.tensor(prof, dtype=F64, requires_grad=True)
+    gw = torch.tensor(0.05, dtype=F64, requires_grad=True)
+    Jo = oracle_J(P, f0, th0, tb, gw, n)
+    gtb, ggw = torch.autograd.grad(Jo, (tb, gw))
+    J, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, n, ckpt=ckpt)
+    print(f"ghost {Lx}x{Ly}: J rel {abs(J / float(Jo) - 1):.2e} dTb rel {rel(dTb, gtb.numpy()):.2e} "
           f"dGw rel {abs(dGw / float(ggw) - 1):.2e}")
     assert abs(J / float(Jo) - 1) < 1e-5
     assert rel(dTb, gtb.numpy()) < 1e-3, rel(dTb, gtb.numpy())
