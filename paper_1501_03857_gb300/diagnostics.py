@@ -92,6 +92,26 @@ def bubbles(rho: np.ndarray, rho_l: float, rho_v: float, periodic_y: bool = Fals
     return out
 
 
+def bubble_count(rho: np.ndarray, rho_l: float, rho_v: float, periodic_y: bool = False, exclude_walls: bool = True,
+                 min_cells: int = 12) -> int:
+    """len(bubbles(rho, rho_l, rho_v, ...)) with the same arguments, from one
+    labelling and the labels' cell counts, without the per-bubble records
+    (about 1 ms instead of 9 on the 600 x 150 pool: the boiling-curve runs
+    sample it thousands of times)."""
+    rho = np.asarray(rho)
+    vap = rho < 0.5 * (rho_l + rho_v)
+    lab, _ = ndimage.label(vap)
+    lab = _merge_seam(lab, axis=1)
+    if periodic_y:
+        lab = _merge_seam(lab, axis=0)
+    keep = np.bincount(lab.ravel()) >= min_cells
+    keep[0] = False
+    if exclude_walls and not periodic_y:
+        keep[lab[0]] = False
+        keep[lab[-1]] = False
+    return int(keep.sum())
+
+
 def _distance(shape, xc: float, yc: float, periodic_y: bool) -> np.ndarray:
     Ly, Lx = shape
     y, x = np.mgrid[0:Ly, 0:Lx].astype(np.float64)

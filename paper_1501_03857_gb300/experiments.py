@@ -162,15 +162,24 @@ def run_cases(runs, cfg: lb.Config, rho_v: float, rho_l: float, base_superheat: 
                 batch.set_wall_temperature(i, dT)
         batch.step(t_settle)
         batch.heat_flux(reset=True)
-        done = 0
+
+        def sample(fields):
+            for i, rho in enumerate(fields):
+                cov[i].append(wall_coverage(rho, rho_l, rho_v))
+                nbub[i].append(diagnostics.bubble_count(rho, rho_l, rho_v))
+
+        # every sample_every steps the density fields come back to the host;
+        # they are measured while the GPU runs the next steps
+        done, pending = 0, None
         while done < t_avg:
             n = min(sample_every, t_avg - done)
             batch.step(n)
             done += n
-            for i in range(len(runs)):
-                rho = batch.fields(i, ("rho",))["rho"]
-                cov[i].append(wall_coverage(rho, rho_l, rho_v))
-                nbub[i].append(len(diagnostics.bubbles(rho, rho_l, rho_v)))
+            if pending is not None:
+                sample(pending)
+            pending = [batch.fields(i, ("rho",))["rho"] for i in range(len(runs))]
+        if pending is not None:
+            sample(pending)
         hf = batch.heat_flux()
     finally:
         batch.close()

@@ -81,3 +81,19 @@ def test_laplace_fit_exact_and_noisy():
     assert fit["r2"] > 1 - 1e-12
     noisy = 0.3 / r * (1 + 0.2 * np.array([1, -1, 1, -1, 1]))
     assert D.laplace_fit(r, noisy)["r2"] < 0.99
+
+
+def test_bubble_count_equals_bubbles():
+    """bubble_count gives len(bubbles(...)) for the same arguments on random
+    two-phase fields: periodic and wall-bounded y, walls excluded or not,
+    several size thresholds."""
+    rng = np.random.default_rng(5)
+    rl, rv = 6.5, 0.38
+    for _ in range(60):
+        Ly, Lx = int(rng.integers(5, 60)), int(rng.integers(5, 90))
+        rho = np.where(rng.random((Ly, Lx)) < rng.uniform(0.2, 0.7), rv, rl)
+        for per in (False, True):
+            for ex in (False, True):
+                for mc in (1, 4, 12):
+                    assert D.bubble_count(rho, rl, rv, periodic_y=per, exclude_walls=ex, min_cells=mc) == len(
+                        D.bubbles(rho, rl, rv, periodic_y=per, exclude_walls=ex, min_cells=mc))
