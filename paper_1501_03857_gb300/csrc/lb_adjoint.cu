@@ -84,8 +84,8 @@ struct AdjFields {
     // forward intermediates of the step being reversed (RecomputeOut)
     const float* fstar;  // f*^n, 9 planes
     const float* theta;  // theta^n
-    const float *rho, *psi, *Fmx, *Fmy;
-    const float *drx, *dry, *divv, *ax, *ay, *cA, *cB;
+    const float *rho, *psi;
+    const float *drx, *dry, *divv, *ax, *ay;
     const float *u2, *u3, *u4;
     // adjoints; lambda of f* is carried as lf[a](t) + lr(t + e_a) (see
     // adjoint_reverse_step in lb_internal.h)
@@ -302,10 +302,10 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
     };
 
     // the inputs of iteration L, loaded one iteration ahead (their latency is
-    // hidden behind the stages): lambda_theta', ax, ay, u4, u3 of row L, cA,
-    // cB of row L - 1, u2 of row L - 2, theta of row L - 3, and rho, div v,
-    // grad rho of row L - 4 (the output row)
-    float n_lin = 0.f, n_ax = 0.f, n_ay = 0.f, n_u4 = 0.f, n_u3 = 0.f, n_cA = 0.f, n_cB = 0.f, n_u2 = 0.f, n_th = 0.f;
+    // hidden behind the stages): lambda_theta', ax, ay, u4, u3 of row L, rho
+    // and div v of row L - 1 (for cA, cB), u2 of row L - 2, theta of row
+    // L - 3, and rho, div v, grad rho of row L - 4 (the output row)
+    float n_lin = 0.f, n_ax = 0.f, n_ay = 0.f, n_u4 = 0.f, n_u3 = 0.f, n_r1 = 0.f, n_d1 = 0.f, n_u2 = 0.f, n_th = 0.f;
     float n_rho = 0.f, n_dv = 0.f, n_drx = 0.f, n_dry = 0.f;
     auto prefetch = [&](int L, auto steady) {
         constexpr bool S = decltype(steady)::value;
@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
         }
         if (S || (L - 1 >= lo && L - 1 <= hi)) {
             const int i = (L - 1) * pitch + x;
-            n_cA = LB_LD(A.cA, i, P.plane);
-            n_cB = LB_LD(A.cB, i, P.plane);
+            n_r1 = LB_LD(A.rho, i, P.plane);
+            n_d1 = LB_LD(A.divv, i, P.plane);
         }
         if (S || (L - 2 >= lo && L - 2 <= hi)) n_u2 = LB_LD(A.u2, (L - 2) * pitch + x, P.plane);
         if (S || (L - 3 >= lo && L - 3 <= hi)) n_th = LB_LD(A.theta, (L - 3) * pitch + x, P.plane);
@@ -355,8 +355,11 @@ __global__ void __launch_bounds__(RT_BD) rev_thermal_fused(const StepParams P, A
             *uu(1, 0) = n_u3;
         }
         if (S || (L - 1 >= lo && L - 1 <= hi)) {  // cA, cB of row L - 1 (stage 4 there next)
-            own(0, 1) = n_cA;
-            own(1, 1) = n_cB;
+            // the coefficients of the source term as the step forms them (Eq. 18):
+            // cA = div v R / (c_v (1 - b rho)), cB = div v a rho / (c_v (1 + 2 b rho - b^2 rho^2))
+            const float br = P.b * n_r1;
+            own(0, 1) = n_d1 * P.R * P.inv_cv * rcp_a(1.f - br);
+            own(1, 1) = n_d1 * P.a * n_r1 * P.inv_cv * rcp_a(fmaf(br, 2.f - br, 1.f));
         }
         if (S || (L - 2 >= lo && L - 2 <= hi)) *uu(2, 2) = n_u2;
         if (S || (L - 3 >= lo && L - 3 <= hi)) *uu(3, 3) = n_th;
@@ -445,9 +448,10 @@ __device__ __forceinline__ void grad12(const float* m, const float* c, const flo
 }
 
 __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, AdjFields A, float lq, int seg_h) {
-    // rings: 0 ldrx, 1 ldry, 2 ldivv, 3 lr_in (rows of stage C), 4 Qx, 5 Qy (stage P)
-    __shared__ float sm[6 * RF_R * RF_W];
-    for (int k = threadIdx.x; k < 6 * RF_R * RF_W; k += RF_BD) sm[k] = 0.f;
+    // rings: 0 ldrx, 1 ldry, 2 ldivv, 3 lr_in, 6 psi (rows of stage C), 4 Qx,
+    // 5 Qy (stage P)
+    __shared__ float sm[7 * RF_R * RF_W];
+    for (int k = threadIdx.x; k < 7 * RF_R * RF_W; k += RF_BD) sm[k] = 0.f;
     const int Lx = P.Lx, Ly = P.Ly, pitch = P.pitch, pl = P.plane;
     const int nout = RF_BD - 2 * RF_HALO;
     const int nstrips = (Lx + nout - 1) / nout;
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
     auto ring = [&](int f, int r) { return sm + (f * RF_R + (r & (RF_R - 1))) * RF_W + s; };
     const float G = P.G;
 
-    float nr[4];  // ring inputs of one row (0 beyond the walls)
+    float nr[5];  // ring inputs of one row (0 beyond the walls)
     auto load_ring = [&](int r, auto steady) {
         if (decltype(steady)::value || (r >= 0 && r < Ly)) {
             const int i = r * pitch + x;
@@ -475,19 +479,21 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
             nr[1] = LB_LD(A.ldry, i, pl);
             nr[2] = LB_LD(A.ldivv, i, pl);
             nr[3] = LB_LD(A.lr_in, i, pl);
+            nr[4] = LB_LD(A.psi, i, pl);
         } else {
-            nr[0] = nr[1] = nr[2] = nr[3] = 0.f;
+            nr[0] = nr[1] = nr[2] = nr[3] = nr[4] = 0.f;
         }
     };
     auto store_ring = [&](int r) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) *ring(k, r) = nr[k];
+        *ring(6, r) = nr[4];
     };
     // stage C's per-cell inputs of one row: pulled populations (Eq. 3; the
     // outflow top pulls 4, 7, 8 from its own row), lf part of lambda_f*^{n+1},
-    // the step's F_m, psi, theta, and the thermal pass's lambda_v, lambda_rho,
-    // lambda_theta
-    float nf[9], nl[9], nFmx, nFmy, npsi, nlvx, nlvy, nlrho, nth, nlth;
+    // theta, and the thermal pass's lambda_v, lambda_rho, lambda_theta (psi
+    // comes through its ring)
+    float nf[9], nl[9], nlvx, nlvy, nlrho, nth, nlth;
     auto load_in = [&](int r, auto steady) {
         constexpr bool S = decltype(steady)::value;
         const int rc = r * pitch;
@@ -501,9 +507,6 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
         const int i = rc + x;
 #pragma unroll
         for (int a = 0; a < 9; ++a) nl[a] = LB_LD(A.lf_in, a * pl + i, 9 * (size_t)pl);
-        nFmx = LB_LD(A.Fmx, i, pl);
-        nFmy = LB_LD(A.Fmy, i, pl);
-        npsi = LB_LD(A.psi, i, pl);
         nlvx = LB_LD(A.lvx, i, pl);
         nlvy = LB_LD(A.lvy, i, pl);
         nlrho = LB_LD(A.lrho, i, pl);
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
         constexpr bool S = decltype(steady)::value;
         // ---- ring row L + 1 and this row's inputs; then row L + 1's loads
         float f[9], lo[9];
-        const float Fmx = nFmx, Fmy = nFmy, psi = npsi, lvx_t = nlvx, lvy_t = nlvy, lrho_t = nlrho, th = nth;
+        const float lvx_t = nlvx, lvy_t = nlvy, lrho_t = nlrho, th = nth;
         const float lth_t = nlth;
 #pragma unroll
         for (int a = 0; a < 9; ++a) {
@@ -542,11 +545,26 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
         __syncthreads();
 
         // ---- C: row L
-        float n_lrho = 0.f, n_lpsi = 0.f, n_rho = 0.f;
+        float n_lrho = 0.f, n_lpsi = 0.f, n_rho = 0.f, n_psi = 0.f;
         if (S || L <= ch) {
             const int y = L;
             const bool wall = !S && (y == 0 || y == Ly - 1);
             wall_fill(P, y, f);
+            // psi and F_m (Eq. 7) from the psi ring, as the step forms them; on
+            // wall rows only with the ghost layer, whose row beyond the wall
+            // is a copy of the wall row
+            const float psi = ring(6, y)[0];
+            float Fmx = 0.f, Fmy = 0.f;
+            if (!wall || P.ghost) {
+                const float* pc = ring(6, y);
+                const float* pm = (wall && y == 0) ? pc : ring(6, y - 1);
+                const float* pp = (wall && y == Ly - 1) ? pc : ring(6, y + 1);
+                float sx, sy;  // 12 sum_a w_a psi(x + e_a) e_a
+                grad12(pm, pc, pp, sx, sy);
+                const float mG = -G * (1.f / 12.f) * psi;
+                Fmx = mG * sx;
+                Fmy = mG * sy;
+            }
             float gx, gy, hx, hy, dvx, dvy;  // 12 D of ldrx, ldry, ldivv (gy, hx unused)
             grad12(ring(0, y - 1), ring(0, y), ring(0, y + 1), gx, gy);
             grad12(ring(1, y - 1), ring(1, y), ring(1, y + 1), hx, hy);
@@ -681,6 +699,7 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
             n_lrho = lrho;
             n_lpsi = lpsi;
             n_rho = rho;
+            n_psi = psi;
         }
         __syncthreads();
 
@@ -778,7 +797,7 @@ __global__ void __launch_bounds__(RF_BD, 4) rev_flow_fused(const StepParams P, A
         c_lrho = n_lrho;
         c_lpsi = n_lpsi;
         c_rho = n_rho;
-        c_psi = psi;
+        c_psi = n_psi;
         c_th = th;
         c_lth = lth_t;
     };
@@ -813,8 +832,8 @@ AdjFields fields_at(const StepParams& P, void* work) {
     A.theta = nullptr;
     A.lf_in = A.lt_in = A.lr_in = nullptr;
     A.lf_out = A.lt_out = A.lr_out = nullptr;
-    A.rho = A.psi = A.Fmx = A.Fmy = nullptr;
-    A.drx = A.dry = A.divv = A.ax = A.ay = A.cA = A.cB = A.u2 = A.u3 = A.u4 = nullptr;
+    A.rho = A.psi = nullptr;
+    A.drx = A.dry = A.divv = A.ax = A.ay = A.u2 = A.u3 = A.u4 = nullptr;
     A.lrho = next(1);
     A.lvx = next(1);
     A.lvy = next(1);
@@ -890,15 +909,11 @@ cudaError_t adjoint_reverse_step(const StepParams& P, const RecomputeOut& R, voi
     A.lr_out = lr_out;
     A.rho = R.rho;
     A.psi = R.psi;
-    A.Fmx = R.Fmx;
-    A.Fmy = R.Fmy;
     A.drx = R.drx;
     A.dry = R.dry;
     A.divv = R.divv;
     A.ax = R.ax;
     A.ay = R.ay;
-    A.cA = R.cA;
-    A.cB = R.cB;
     A.u2 = R.u2;
     A.u3 = R.u3;
     A.u4 = R.u4;

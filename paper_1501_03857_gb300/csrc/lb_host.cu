@@ -1543,9 +1543,8 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
     const size_t rec_stride = align256(sizeof(float) * kRecomputePlanes * pl);
     auto rec_at = [&](size_t k) {  // the k-th set of forward intermediates
         float* r = (float*)(s + L.rec + k * rec_stride);
-        return RecomputeOut{r,           r + pl,      r + 2 * pl,  r + 3 * pl,  r + 4 * pl,
-                            r + 5 * pl,  r + 6 * pl,  r + 7 * pl,  r + 8 * pl,  r + 9 * pl,
-                            r + 10 * pl, r + 11 * pl, r + 12 * pl, r + 13 * pl};
+        return RecomputeOut{r,          r + pl,     r + 2 * pl, r + 3 * pl, r + 4 * pl,
+                            r + 5 * pl, r + 6 * pl, r + 7 * pl, r + 8 * pl, r + 9 * pl};
     };
     if (C == 1) {
         // every step stored: the forward pass runs the fused step in its

@@ -25,16 +25,16 @@ cudaError_t launch_step(const StepParams& P, const Launch& L, cudaStream_t st);
 // The forward intermediates of one step that the adjoint's reverse kernels
 // read (lb_adjoint.cu), written by the dual-strip step in its recompute mode
 // (lb_step3.cu) into pitched [Ly][pitch] planes. The gradients drx, dry and
-// div v carry the stencil weights; ax, ay, cA, cB are the coefficients of
-// K(T), Eq. 18 (0 on the wall rows); u2-u4 the RK stage inputs (theta on the
-// wall rows). With out the step itself is written too (f*, theta of the
+// div v carry the stencil weights; ax, ay are coefficients of K(T), Eq. 18
+// (0 on the wall rows; cA, cB and F_m follow from div v, rho and psi); u2-u4
+// the RK stage inputs (theta on the wall rows). With out the step itself is written too (f*, theta of the
 // next level to P.f_out, P.th_out), and with heat (only with out) q(t) is
 // added to P.acc's heat-flux sums as the plain step does.
 struct RecomputeOut {
-    float *rho, *psi, *Fmx, *Fmy;
-    float *drx, *dry, *divv, *ax, *ay, *cA, *cB, *u2, *u3, *u4;
+    float *rho, *psi;
+    float *drx, *dry, *divv, *ax, *ay, *u2, *u3, *u4;
 };
-constexpr int kRecomputePlanes = 14;  // the planes of RecomputeOut, in its order
+constexpr int kRecomputePlanes = 10;  // the planes of RecomputeOut, in its order
 cudaError_t dual_recompute(const StepParams& P, const RecomputeOut& R, bool out, bool heat, const Launch& L,
                            cudaStream_t st);
 

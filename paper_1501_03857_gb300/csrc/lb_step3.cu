@@ -447,12 +447,6 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
                 *LB_SMP(sVX + (r & 3) * W + s) = vx.f2();
                 *LB_SMP(sVY + (r & 3) * W + s) = vy.f2();
                 const bool st = S || (r >= ys && r < ye);
-                if constexpr (REC) {
-                    if (st) {
-                        put(R->Fmx, y, Fmx);  // F and v follow from these, psi, rho and f
-                        put(R->Fmy, y, Fmy);
-                    }
-                }
                 if (OUT && st && (outa || outb)) {
                     T o[9];
                     collide2(fP, rhoP, vx, vy, Fx, Fy, g2, K, o);
@@ -514,8 +508,6 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
                                 put(R->divv, y, w12 * divv);
                                 put(R->ax, y, t12 * kC.ax);
                                 put(R->ay, y, t12 * kC.ay);
-                                put(R->cA, y, kC.cA);
-                                put(R->cB, y, kC.cB);
                             }
                         }
                     } else if constexpr (REC) {
@@ -526,8 +518,6 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
                             put(R->divv, y, zero);
                             put(R->ax, y, zero);
                             put(R->ay, y, zero);
-                            put(R->cA, y, zero);
-                            put(R->cB, y, zero);
                         }
                     }
                     *LB_SMP(sU2 + (r & 3) * W + s) = u2.f2();

@@ -4,8 +4,8 @@ and the adjoint's reverse kernels every global address, and each flags a
 miss as LB_E_BOUNDS instead of faulting. On grids with odd sizes, every
 boundary treatment, several launch shapes, batches of uneven instances (one
 launch per step and the persistent launch) and adjoints of odd sizes (both
-modes) it flags nothing and produces exactly the states and gradients of the
-normal build."""
+modes) it flags nothing and produces exactly the states of the normal build,
+and its gradients within rounding (1e-6 relative)."""
 
 import json
 import os
@@ -66,5 +66,16 @@ def test_checked_build_flags_nothing_and_matches(tmp_path):
     checked = states(str(tmp_path), os.path.join(lib_dir, "liblbboil_checked.so"))
     normal = states(str(tmp_path), os.path.join(lib_dir, "liblbboil.so"))
     assert sorted(checked.files) == sorted(normal.files)
+    worst = 0.0
     for k in normal.files:
-        assert np.array_equal(checked[k], normal[k]), k
+        if k.startswith("adj"):
+            # J, dJ/dG_w, dJ/dT_b: the checked build's guarded stores can move
+            # where the compiler fuses a multiply-add in the reverse kernels,
+            # so the gradients agree to rounding, not bit for bit
+            a, b = checked[k], normal[k]
+            err = float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-30)))
+            worst = max(worst, err)
+            assert err < 1e-6, (k, err)
+        else:
+            assert np.array_equal(checked[k], normal[k]), k
+    print(f"largest relative difference of the adjoints: {worst:.1e}")
