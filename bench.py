@@ -351,7 +351,7 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     J, dTb, dGw = sim.adjoint(nsteps, ckpt)
     t_adj = (time.perf_counter() - t0) * 1e3
     # the same window with every step stored (checkpoint every step: no
-    # replay, about 24 planes of scratch per step), timed the same way
+    # replay, about 20 planes of scratch per step), timed the same way
     sim.load(blob)
     sim.adjoint(nsteps, 1)
     sim.load(blob)

@@ -192,9 +192,9 @@ int lb_destroy(lb_handle* h);
 
 /* Device scratch lb_adjoint needs for nsteps steps with a checkpoint every
  * ckpt_every steps (work fields, checkpoints, two replayed segments with the
- * forward intermediates of their steps: about 10 nsteps / ckpt_every + 48
+ * forward intermediates of their steps: about 10 nsteps / ckpt_every + 40
  * ckpt_every planes of Lx * Ly floats; with ckpt_every = 1, every step's
- * state and intermediates: about 24 nsteps planes). */
+ * state and intermediates: about 20 nsteps planes). */
 int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* bytes);
 
 /* Gradient of the window-averaged bottom-wall heat flux
@@ -207,7 +207,7 @@ int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* b
  * touched) storing a checkpoint every ckpt_every steps, then sweeps back,
  * replaying each segment from its checkpoint. With ckpt_every = 1 the
  * forward steps store every step's state and forward intermediates and the
- * sweep replays nothing: faster, for ~24 planes of scratch per step. J
+ * sweep replays nothing: faster, for ~20 planes of scratch per step. J
  * (host) receives the value.
  * Walls or the outflow top in y, with or without the ghost layer, thermal runs
  * only.

@@ -359,7 +359,7 @@ class Simulation:
         """J = mean wall heat flux over the next nsteps steps and its gradients
         dJ/d(T_b(x) - T_s) [Lx] and dJ/dG_w by the discrete adjoint
         (lb_adjoint), with a checkpoint every ckpt_every steps; ckpt_every = 1
-        stores every step and replays none (faster, about 24 planes of
+        stores every step and replays none (faster, about 20 planes of
         scratch per step). Advances the simulation by nsteps."""
         torch = self.torch
         n = C.c_size_t(self.adjoint_scratch_bytes(nsteps, ckpt_every))
