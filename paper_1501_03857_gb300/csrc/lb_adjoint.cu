@@ -191,7 +191,14 @@ __device__ __forceinline__ void rev_coef_vals(const StepParams& P, const AdjFiel
 // ax mu, ay mu per stage took 43.5 KB per block, 5 blocks per SM. Steady
 // iterations without range and wall tests: 95 registers, 5 blocks per SM,
 // and the 2048^2 reverse step 0.374 ms instead of 0.414; held to 7 blocks
-// per SM, 72 registers with a small spill, 0.414.)
+// per SM, 72 registers with a small spill, 0.414. Packing each stage's u,
+// mu, ax mu and ay mu into one float4 ring, products formed by the thread
+// that forms mu, so that a neighbour is one 16-byte load (9 loads and 2
+// products per stage instead of 33 and 12): 0.404 ms at 4 blocks per SM
+// (128 registers), 0.446 at 5 (96 registers with a spill), against 0.363
+// for this form: a 16-byte load of a warp takes 4 shared-memory wavefronts
+// and the partial float4 stores at a 16-byte stride as many, more than the
+// 33 conflict-free 4-byte loads they replace.)
 // ring rows: RT_R for mu and u (3 rows read, one written per iteration),
 // RT_RA for ax, ay (read by all four stages: rows L-5..L)
 constexpr int RT_BD = 128, RT_HALO = 4, RT_W = RT_BD + 2, RT_R = 4, RT_RA = 8;
