@@ -362,6 +362,7 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
     store_all = {"ckpt_every": 1, "ms_adjoint_total": t_all, "cost_ratio": t_all / t_fwd,
                  "scratch_gb": sim.adjoint_scratch_bytes(nsteps, 1) / 1e9,
                  "same_gradients": bool(J1 == J and np.array_equal(dTb1, dTb) and dGw1 == dGw)}
+    default_ckpt = sim.adjoint_ckpt(nsteps)  # the interval sim.adjoint(nsteps) picks here
     h = 1e-4
     fd_tb = (forward_J(dtb=h) - forward_J(dtb=-h)) / (2 * h)
     fd_gw = (forward_J(dgw=h) - forward_J(dgw=-h)) / (2 * h)
@@ -381,7 +382,8 @@ def adjoint_window(torch, lb, L=256, nsteps=2000, ckpt=100):
                 "rel_err_J": abs(J / ref["J"] - 1), "rel_err_Gw": abs(dGw / ref["dGw"] - 1),
                 "rel_err_uniform": abs(float(dTb.sum()) / ref["dTb_uniform"] - 1),
                 "what": "FP64 oracle central differences, h = 2e-4 and 1e-4, Richardson-extrapolated"}
-    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "J": J, "vs_fp64_reference": fp64,
+    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "default_ckpt_every": default_ckpt,
+            "J": J, "vs_fp64_reference": fp64,
             "ms_forward": t_fwd, "ms_adjoint_total": t_adj, "cost_ratio": t_adj / t_fwd,
             "store_every_step": store_all,
             "mlups_adjoint": L * L * nsteps / (t_adj * 1e-3) / 1e6,
@@ -463,13 +465,15 @@ def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
     sim.adjoint(nsteps, 1)
     t_all = (time.perf_counter() - t0) * 1e3
     scratch_all = sim.adjoint_scratch_bytes(nsteps, 1)
+    default_ckpt = sim.adjoint_ckpt(nsteps)  # the interval sim.adjoint(nsteps) picks here
     sim.close()
     cells = L * L
     rev_ms = (t_adj - t_fwd) / nsteps
     rev_all = (t_all - t_fwd) / nsteps
     peak, _ = measured_peaks()
     achieved = ADJ_BYTES_PER_LU * cells / (rev_ms * 1e-3) / 1e9
-    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "ms_forward_per_step": t_fwd / nsteps,
+    return {"grid": f"{L}x{L}", "steps": nsteps, "ckpt_every": ckpt, "default_ckpt_every": default_ckpt,
+            "ms_forward_per_step": t_fwd / nsteps,
             "ms_reverse_per_step": rev_ms, "mlups_reverse": cells / (rev_ms * 1e-3) / 1e6,
             "mlups_adjoint": cells * nsteps / (t_adj * 1e-3) / 1e6,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -502,8 +506,10 @@ def summary(line):
                                 cost_vs_forward_2048=round(1 + g["ms_reverse_per_step"] / g["ms_forward_per_step"], 2))
             if g.get("store_every_step"):
                 r["adjoint"]["cost_vs_forward_2048_every_step_stored"] = round(g["store_every_step"]["cost_ratio"], 2)
+            r["adjoint"]["default_ckpt_2048"] = g.get("default_ckpt_every")
         if a.get("store_every_step"):
             r["adjoint"]["cost_vs_forward_256_every_step_stored"] = round(a["store_every_step"]["cost_ratio"], 2)
+        r["adjoint"]["default_ckpt_256"] = a.get("default_ckpt_every")
     e = line.get("experiments")
     if e:
         r["experiments"] = {"sims_per_hour": round(e["sims_per_hour"]),

@@ -197,6 +197,18 @@ int lb_destroy(lb_handle* h);
  * state and intermediates: about 20 nsteps planes). */
 int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* bytes);
 
+/* Checkpoint interval for lb_adjoint over nsteps steps whose scratch fits in
+ * budget_bytes of device memory. 1 (every step's state and intermediates
+ * stored, no replay: the fastest) when its scratch fits; otherwise the
+ * interval with the smallest scratch (checkpoints take ~10 nsteps / C
+ * planes and the replay buffers ~40 C, so about C = sqrt(nsteps / 4)), whose
+ * run time is about the same for every C >= 2 (each step is replayed once).
+ * Writes the interval to *ckpt_every and, if bytes is not NULL, its scratch
+ * to *bytes (as lb_adjoint_scratch_bytes). LB_E_INVAL when no interval fits
+ * (nothing written), for a null output, or when lb_adjoint would reject the
+ * run. Host arithmetic only; nothing is issued on the stream. */
+int lb_adjoint_pick_ckpt(lb_handle* h, int nsteps, size_t budget_bytes, int* ckpt_every, size_t* bytes);
+
 /* Gradient of the window-averaged bottom-wall heat flux
  * J = (1/nsteps) sum_{n} q(t_n) over the next nsteps steps (Sec. 3.2) with
  * respect to the bottom-wall temperature profile T_b(x) (dJ_dTb, host [Lx])

@@ -1510,6 +1510,33 @@ int lb_adjoint_scratch_bytes(lb_handle* h, int nsteps, int ckpt_every, size_t* b
     return LB_OK;
 }
 
+int lb_adjoint_pick_ckpt(lb_handle* h, int nsteps, size_t budget_bytes, int* ckpt_every, size_t* bytes) {
+    int rc = adjoint_check(h, nsteps, 1);
+    if (rc) return rc;
+    if (!ckpt_every) return fail(LB_E_INVAL, "null output");
+    const size_t all = adj_layout(h, h->base, nsteps, 1).total;
+    int pick = 1;
+    size_t need = all;
+    if (all > budget_bytes) {
+        // checkpoints fall as 1/C and the replay buffers grow as C: the
+        // smallest scratch lies near C = sqrt(nsteps / 4), well inside C*C <= nsteps + 16
+        pick = 0;
+        for (long long c = 2; c <= nsteps && c * c <= (long long)nsteps + 16; ++c) {
+            const size_t t = adj_layout(h, h->base, nsteps, (int)c).total;
+            if (pick == 0 || t < need) {
+                pick = (int)c;
+                need = t;
+            }
+        }
+        if (pick == 0 || need > budget_bytes)
+            return fail(LB_E_INVAL, "no checkpoint interval fits the adjoint of %d steps in %zu bytes (smallest: %zu)",
+                        nsteps, budget_bytes, pick ? need : all);
+    }
+    *ckpt_every = pick;
+    if (bytes) *bytes = need;
+    return LB_OK;
+}
+
 int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes, double* J,
                double* dJ_dTb, double* dJ_dGw) {
     int rc = adjoint_check(h, nsteps, ckpt_every);

@@ -91,6 +91,7 @@ def _load():
         "lb_batch_sync": [P],
         "lb_batch_destroy": [P],
         "lb_adjoint_scratch_bytes": [P, I, I, C.POINTER(C.c_size_t)],
+        "lb_adjoint_pick_ckpt": [P, I, SZ, C.POINTER(I), C.POINTER(C.c_size_t)],
         "lb_adjoint": [P, I, I, P, SZ, DP, P, DP],
         "lb_fields_noalloc": [C.POINTER(lb_grid), C.POINTER(lb_eos), C.POINTER(lb_thermal), D, D, P, P, P, P, P,
                               P, P],
@@ -355,13 +356,28 @@ class Simulation:
         check(lib.lb_adjoint_scratch_bytes(self.h, int(nsteps), int(ckpt_every), C.byref(n)))
         return n.value
 
-    def adjoint(self, nsteps: int, ckpt_every: int = 100):
+    def adjoint_ckpt(self, nsteps: int, budget_bytes=None) -> int:
+        """Checkpoint interval for adjoint(nsteps) within budget_bytes of
+        scratch (lb_adjoint_pick_ckpt): 1, every step stored, when that fits,
+        else the interval with the smallest scratch. The default budget is
+        half the device memory free now."""
+        if budget_bytes is None:
+            budget_bytes = self.torch.cuda.mem_get_info()[0] // 2
+        c, n = C.c_int(), C.c_size_t()
+        check(lib.lb_adjoint_pick_ckpt(self.h, int(nsteps), int(budget_bytes), C.byref(c), C.byref(n)))
+        return c.value
+
+    def adjoint(self, nsteps: int, ckpt_every=None):
         """J = mean wall heat flux over the next nsteps steps and its gradients
         dJ/d(T_b(x) - T_s) [Lx] and dJ/dG_w by the discrete adjoint
         (lb_adjoint), with a checkpoint every ckpt_every steps; ckpt_every = 1
         stores every step and replays none (faster, about 20 planes of
-        scratch per step). Advances the simulation by nsteps."""
+        scratch per step); None picks it with adjoint_ckpt (every step stored
+        whenever that takes at most half the free device memory). Advances
+        the simulation by nsteps."""
         torch = self.torch
+        if ckpt_every is None:
+            ckpt_every = self.adjoint_ckpt(nsteps)
         n = C.c_size_t(self.adjoint_scratch_bytes(nsteps, ckpt_every))
         scratch = torch.empty(n.value + 256, dtype=torch.uint8, device="cuda")
         base = scratch.data_ptr()
@@ -510,7 +526,7 @@ def _autograd_fn():
             sim.load(blob)
             sim.set_wall_temperature(0.0, Tb.detach().double().cpu().numpy())
             sim.set_wettability(float(Gw))
-            J, dTb, dGw = sim.adjoint(int(nsteps), int(ckpt_every))
+            J, dTb, dGw = sim.adjoint(int(nsteps), None if ckpt_every is None else int(ckpt_every))
             ctx.save_for_backward(torch.as_tensor(dTb, dtype=Tb.dtype, device=Tb.device),
                                   torch.as_tensor(dGw, dtype=Gw.dtype, device=Gw.device))
             return torch.as_tensor(J, dtype=torch.float64, device=Tb.device)
@@ -523,6 +539,6 @@ def _autograd_fn():
     return HeatFluxWindow
 
 
-def heat_flux_window(Tb, Gw, sim, blob, nsteps, ckpt_every=100):
+def heat_flux_window(Tb, Gw, sim, blob, nsteps, ckpt_every=None):
     """Differentiable J(Tb, Gw); see HeatFluxWindow."""
     return _autograd_fn().apply(Tb, Gw, sim, blob, nsteps, ckpt_every)

@@ -236,3 +236,29 @@ def test_adjoint_256_window_against_fp64_reference(lb):
           f"{abs(ref['dTb_uniform'] / ref['dTb_uniform_h1e-4'] - 1):.1e})")
     assert eJ < 1e-5
     assert eG < 1e-3 and eT < 1e-3
+
+
+def test_checkpoint_interval_for_a_memory_budget(lb):
+    """lb_adjoint_pick_ckpt: every step stored when its scratch fits the
+    budget; else the interval of smallest scratch, which fits and equals
+    lb_adjoint_scratch_bytes for it; an error when nothing fits. The picked
+    interval's adjoint is the one run with that interval given explicitly."""
+    cfg, rho0, prof, P, f0, th0 = setup(lb)
+    sim = lb.Simulation(cfg, superheat=0.0, profile=prof, Gw=0.05, rho0=rho0)
+    n = 40
+    all_steps = sim.adjoint_scratch_bytes(n, 1)
+    assert sim.adjoint_ckpt(n, all_steps) == 1
+    c = sim.adjoint_ckpt(n, all_steps - 1)
+    sizes = {k: sim.adjoint_scratch_bytes(n, k) for k in range(2, n + 1)}
+    assert c >= 2 and sizes[c] == min(sizes.values()) and sizes[c] < all_steps
+    assert sim.adjoint_ckpt(n, sizes[c]) == c
+    with pytest.raises(RuntimeError):
+        sim.adjoint_ckpt(n, sizes[c] - 1)
+    with pytest.raises(RuntimeError):
+        sim.adjoint_ckpt(1, sim.adjoint_scratch_bytes(1, 1) - 1)
+    sim.set_state(f0, th0)
+    J, dTb, dGw = sim.adjoint(12)  # default budget: half the free memory, every step stored
+    sim.set_state(f0, th0)
+    J1, dTb1, dGw1 = sim.adjoint(12, 1)
+    assert J == J1 and dGw == dGw1 and np.array_equal(dTb, dTb1)
+    sim.close()
