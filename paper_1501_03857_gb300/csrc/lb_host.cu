@@ -1593,8 +1593,15 @@ int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size
                 LB_CUDA(launch_probe(A, st), "probe launch");
             }
         }
-        // the simulation advances as with the plain steps
-        if ((rc = save(h->f[h->cur], sf(L.ckpt, nsteps), sf(L.ckpt, nsteps) + 9 * pl))) return rc;
+        // the simulation advances as with the plain steps: the last state
+        // into the current population and theta buffers (separate arrays of
+        // the workspace, not one 10-plane block like a checkpoint)
+        LB_CUDA(cudaMemcpyAsync(h->f[h->cur], sf(L.ckpt, nsteps), sizeof(float) * 9 * pl, cudaMemcpyDeviceToDevice,
+                                st),
+                "state copy");
+        LB_CUDA(cudaMemcpyAsync(h->t[h->cur], sf(L.ckpt, nsteps) + 9 * pl, sizeof(float) * pl,
+                                cudaMemcpyDeviceToDevice, st),
+                "state copy");
         h->steps += nsteps;
     } else {
         StepParams P = base;

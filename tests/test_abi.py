@@ -181,3 +181,17 @@ def test_largest_grid_accepted_one_row_more_rejected(lb):
     assert ok >= 2 * 10 * 16384 * 14563 * 4
     with pytest.raises(lb.LBError, match="too large"):
         lb.workspace_bytes(lb.Config(Lx=16384, Ly=14564))
+
+
+def test_empty_batch_rejected_before_any_device_call(lb):
+    """A batch of no instances (n = 0) or a null descriptor array is rejected
+    by the host before anything touches the device."""
+    import ctypes as C
+    desc = lb.lb_batch_desc()
+    n = C.c_size_t()
+    assert lb.lib.lb_batch_workspace_bytes(C.byref(desc), 0, C.byref(n)) == -1
+    assert "n >= 1" in lb.lib.lb_last_error().decode()
+    assert lb.lib.lb_batch_workspace_bytes(None, 1, C.byref(n)) == -1
+    b = C.c_void_p()
+    assert lb.lib.lb_batch_init(C.byref(b), C.byref(desc), 0, None, 0, None) == -1
+    assert not b.value

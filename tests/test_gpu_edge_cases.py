@@ -1,0 +1,91 @@
+"""Degenerate calls of the boundary on the GPU: zero steps, the heat-flux
+record before any step, and adjoint windows of one step or shorter than the
+checkpoint interval. Each either leaves the state exactly as it was or gives
+exactly what the general path gives."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1501_03857_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1501_03857_gb300 import lb as lbmod
+    return lbmod
+
+
+def pool(lb, Lx=40, Ly=24, bc=None, seed=2):
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_WALLS if bc is None else bc, pool_height=0.45 * Ly)
+    rv, rl = lb.coexistence(cfg)
+    rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.45 * Ly, noise_amp=1e-3, seed=seed)
+    return cfg, rho0
+
+
+def test_zero_steps_change_nothing(lb):
+    cfg, rho0 = pool(lb)
+    sim = lb.Simulation(cfg, superheat=0.01, Gw=0.05, rho0=rho0)
+    q0 = sim.heat_flux()
+    assert q0["n"] == 0 and q0["q_mean"] == 0.0 and q0["q_std"] == 0.0  # no sample yet
+    sim.step(5)
+    f0, t0 = sim.get_state()
+    q5 = sim.heat_flux()
+    sim.step(0)
+    f1, t1 = sim.get_state()
+    q = sim.heat_flux()
+    assert np.array_equal(f0, f1) and np.array_equal(t0, t1)
+    assert q == q5 and q["n"] == 5
+    with pytest.raises(RuntimeError):
+        sim.step(-1)
+    sim.close()
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_zero_batch_steps_change_nothing(lb, persistent):
+    insts = []
+    for i, (Lx, Ly) in enumerate([(40, 24), (70, 30)]):
+        cfg, rho0 = pool(lb, Lx, Ly, seed=5 + i)
+        insts.append({"cfg": cfg, "superheat": 0.01, "Gw": 0.02 * i, "rho0": rho0})
+    batch = lb.Batch(insts)
+    if persistent:
+        batch.set_persistent(1)
+    batch.step(3)
+    batch.sync()
+    before = [batch.get_state(i) for i in range(2)]
+    q3 = batch.heat_flux()
+    batch.step(0)
+    batch.sync()
+    q = batch.heat_flux()
+    for i in range(2):
+        f, t = batch.get_state(i)
+        assert np.array_equal(f, before[i][0]) and np.array_equal(t, before[i][1])
+    assert all(np.array_equal(q[k], q3[k]) for k in q) and list(q["n"]) == [3, 3]
+
+
+@pytest.mark.parametrize("n,ckpt", [(1, 1), (1, 4), (3, 5), (3, 3)])
+def test_short_adjoint_windows_equal_every_step_stored(lb, n, ckpt):
+    """One step, and windows no longer than the interval (one segment, one
+    checkpoint): the same J and gradients as storing every step, bit for bit,
+    and the simulation advances by the window either way."""
+    cfg, rho0 = pool(lb, bc=lb.BC_TOP_OUTFLOW)
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)
+    sim.step(4)
+    blob = sim.save()
+    J, dTb, dGw = sim.adjoint(n, ckpt)
+    fa, ta = sim.get_state()
+    sim.load(blob)
+    J1, dTb1, dGw1 = sim.adjoint(n, 1)
+    fb, tb = sim.get_state()
+    sim.load(blob)
+    sim.step(n)
+    fc, tc = sim.get_state()
+    assert J == J1 and dGw == dGw1 and np.array_equal(dTb, dTb1)
+    assert np.isfinite(J) and J != 0.0 and np.any(dTb != 0.0)
+    assert np.array_equal(fa, fb) and np.array_equal(fa, fc) and np.array_equal(ta, tc)
+    with pytest.raises(RuntimeError):
+        sim.adjoint(0, 1)
+    sim.close()
