@@ -1,7 +1,10 @@
 """Degenerate calls of the boundary on the GPU: zero steps, the heat-flux
 record before any step, and adjoint windows of one step or shorter than the
 checkpoint interval. Each either leaves the state exactly as it was or gives
-exactly what the general path gives."""
+exactly what the general path gives. With every step stored, the adjoint's
+forward pass runs in its own buffers and copies the window's last state
+(populations and theta) back into the simulation; the state comparison
+checks that copy."""
 
 import numpy as np
 import pytest
@@ -75,7 +78,9 @@ def test_short_adjoint_windows_equal_every_step_stored(lb, n, ckpt):
     sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)
     sim.step(4)
     blob = sim.save()
+    q4 = sim.heat_flux()
     J, dTb, dGw = sim.adjoint(n, ckpt)
+    assert sim.heat_flux() == q4 and sim.info()["steps"] == 4 + n  # accumulators untouched, steps advanced
     fa, ta = sim.get_state()
     sim.load(blob)
     J1, dTb1, dGw1 = sim.adjoint(n, 1)
