@@ -85,9 +85,12 @@ def test_batch_with_different_model_constants(lb):
     batch.close()
 
 
-def test_batch_parameter_changes_follow_instances(lb):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_parameter_changes_follow_instances(lb, persistent):
     insts = make_instances(lb)[:3]
     batch = lb.Batch(insts)
+    if persistent:
+        batch.set_persistent(1)  # 33 steps after the change: one 32-step launch and one of 1
     batch.step(7)
     batch.set_wall_temperature(1, 0.03)
     batch.set_wettability(2, 0.1)
