@@ -94,3 +94,26 @@ def test_short_adjoint_windows_equal_every_step_stored(lb, n, ckpt):
     with pytest.raises(RuntimeError):
         sim.adjoint(0, 1)
     sim.close()
+
+
+@pytest.mark.parametrize("ckpt", [1, 3])
+def test_adjoint_window_records_probes_once(lb, ckpt):
+    """Probes record each step of the adjoint's forward pass once, with the
+    values plain steps record; the segment replays of the reverse sweep add
+    no records."""
+    cfg, rho0 = pool(lb)
+    pts = [(3, 2), (20, 10), (39, 22)]
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)
+    sim.step(2)
+    blob = sim.save()
+    sim.set_probes(pts, capacity=32)
+    sim.adjoint(7, ckpt)
+    ra = sim.probe_read()
+    sim.load(blob)
+    sim.set_probes(pts, capacity=32)
+    sim.step(7)
+    rb = sim.probe_read()
+    assert ra["count"] == rb["count"] == 7
+    for k in ("rho", "T", "p"):
+        assert ra[k].shape == (3, 7) and np.array_equal(ra[k], rb[k]), k
+    sim.close()
