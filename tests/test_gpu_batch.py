@@ -230,3 +230,38 @@ def test_batch_instance_matches_oracle(lb, tpb):
     assert rel_err(fb, fr.numpy()) < 1e-5
     assert theta_err(tb, tr.numpy(), d["superheat"]) < 1e-5
     assert abs(q["q_mean"][1] / np.mean(qs) - 1) < 1e-5
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_of_every_grid_option_equals_single_instances(lb, persistent):
+    """Instances with the ghost layer (walls and outflow top), periodic y and
+    the thermal step off, mixed in one batch, give the single-instance
+    results bit for bit, heat-flux statistics included."""
+    opts = [dict(bc_y=lb.BC_WALLS, ghost_layer=True), dict(bc_y=lb.BC_TOP_OUTFLOW, ghost_layer=True),
+            dict(bc_y=lb.BC_PERIODIC), dict(bc_y=lb.BC_WALLS, isothermal=True),
+            dict(bc_y=lb.BC_TOP_OUTFLOW, isothermal=True, ghost_layer=True)]
+    sizes = [(56, 30), (90, 41), (48, 36), (120, 25), (33, 50)]
+    insts = []
+    for i, (o, (Lx, Ly)) in enumerate(zip(opts, sizes)):
+        cfg = lb.Config(Lx=Lx, Ly=Ly, pool_height=0.4 * Ly, **o)
+        rv, rl = lb.coexistence(cfg)
+        rho0 = inputs.pool_density(Lx, Ly, rl, rv, 0.4 * Ly, noise_amp=1e-3, seed=30 + i)
+        insts.append({"cfg": cfg, "superheat": 0.004 * (i + 2), "Gw": 0.02 * i, "rho0": rho0})
+    batch = lb.Batch(insts)
+    batch.set_launch(64, 0)  # the single instances' block size: the same strips, the same heat-flux fold
+    if persistent:
+        batch.set_persistent(2)
+    batch.step(37)  # one 32-step run and a remainder of 5
+    batch.sync()
+    q = batch.heat_flux()
+    for i, d in enumerate(insts):
+        sim = lb.Simulation(d["cfg"], superheat=d["superheat"], Gw=d["Gw"], rho0=d["rho0"])
+        sim.set_launch(64, 0)
+        sim.step(37)
+        fs, ts = sim.get_state()
+        fb, tb = batch.get_state(i)
+        assert np.array_equal(fs, fb) and np.array_equal(ts, tb), i
+        hs = sim.heat_flux()
+        assert q["n"][i] == hs["n"] and q["q_mean"][i] == hs["q_mean"] and q["q_std"][i] == hs["q_std"], i
+        sim.close()
+    batch.close()
