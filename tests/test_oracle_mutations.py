@@ -204,6 +204,24 @@ def forcing_zeta_sigma_tau_e(vx, vy, Fx, Fy, Fmx, Fmy, psi, P):
     return S
 
 
+_nb = L._neighbour
+
+
+def ghost_mirrored(field, a, P, ghost_rows):
+    """The ghost row beyond each wall mirrors the first fluid row
+    (psi(-1) = psi(1)) instead of copying the wall row."""
+    if P.bc_y == L.BC_PERIODIC or not ghost_rows:
+        return _nb(field, a, P, ghost_rows)
+    ext = torch.cat([field[1:2], field, field[-2:-1]], dim=0)
+    ext = torch.roll(ext, shifts=(-L.EY[a], -L.EX[a]), dims=(0, 1))
+    return ext[1:-1]
+
+
+def ghost_wrapped(field, a, P, ghost_rows):
+    """Rows beyond the walls taken periodically (the ghost layer ignored)."""
+    return _nb(field, a, P, False)
+
+
 FORCE_W_WRONG = (0.0,) + (1.0 / 3.0,) * 4 + (1.0 / 6.0,) * 4  # diagonal 1/6 instead of 1/12
 STENCIL_W_WRONG = (4.0 / 9.0,) + (1.0 / 9.0,) * 4 + (1.0 / 18.0,) * 4  # diagonal 1/18 instead of 1/36
 
@@ -230,6 +248,9 @@ MUTATIONS = {
     "sigma-term denominator": ("forcing_moments", forcing_sigma_tau, ["coexistence"], True),
     "zeta sigma term dropped": ("forcing_moments", forcing_zeta_sigma_dropped, ["sigma_rows"], True),
     "zeta sigma term sign": ("forcing_moments", forcing_zeta_sigma_sign, ["sigma_rows"], True),
+    # the ghost layer is an option the default step does not use
+    "ghost row mirrored": ("_neighbour", ghost_mirrored, ["ghost"], False),
+    "ghost row wrapped": ("_neighbour", ghost_wrapped, ["ghost"], False),
     # identical to the oracle at the default s_e = s_zeta, so not a change of
     # the default step; the pin runs it at unequal rates
     "zeta sigma term rate": ("forcing_moments", forcing_zeta_sigma_tau_e, ["sigma_rows"], False),
@@ -269,6 +290,7 @@ PINS = {
     "maxwell": _maxwell_pins,
     "coexistence": lambda c: pins.test_flat_interface_coexistence_matches_maxwell(c),
     "sigma_rows": _sigma_rows,
+    "ghost": lambda c: pins.test_ghost_layer_wall_rows_on_linear_psi(),
 }
 
 

@@ -295,6 +295,27 @@ def test_interaction_force_taylor_limit():
     assert 3.6 < errs[0] / errs[1] < 4.4
 
 
+def test_ghost_layer_wall_rows_on_linear_psi():
+    """The ghost-layer variant (Sec. 3.2; reading: the ghost row beyond each
+    wall copies the wall row's psi). On psi = c + b y, uniform in x, the
+    stencil of Eq. 7 gives the exact -G psi b in the interior (it is exact on
+    linear fields), and on each wall row, where the ghost row equals the wall
+    row, half of it: -G psi (1/3 + 2/12)(psi(1) - psi(0)) = -G psi b / 2.
+    F_x vanishes everywhere. A mirrored ghost row (psi(-1) = psi(1)) would
+    give 0 on the wall rows and a periodic wrap -G psi (1/2)(psi(1) -
+    psi(Ly - 1)); neither matches."""
+    for bc in (O.BC_WALLS, O.BC_TOP_OUTFLOW):
+        Ly, Lx, c, b = 9, 5, 0.7, 0.05
+        P = O.Params(Lx=Lx, Ly=Ly, bc_y=bc, ghost=True)
+        psi = (c + b * torch.arange(Ly, dtype=F64)).unsqueeze(1).expand(Ly, Lx).clone()
+        fx, fy = O.interaction_force(psi, P)
+        want = -P.G * psi * b
+        want[0] *= 0.5
+        want[-1] *= 0.5
+        assert torch.allclose(fy, want, rtol=1e-13, atol=1e-15)
+        assert float(fx.abs().max()) < 1e-15
+
+
 def test_interaction_force_sums_to_zero_periodic():
     g = torch.Generator().manual_seed(4)
     P = O.Params(Lx=7, Ly=9, bc_y=O.BC_PERIODIC)
