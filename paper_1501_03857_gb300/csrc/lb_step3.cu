@@ -654,7 +654,7 @@ __device__ __forceinline__ void step_body(const StepParams& P, const StepParams&
 #undef LB_SMC
 
 // The single-domain step at 64 and 128 threads gives the compiler only its
-// block size (154 registers: 12 warps per SM, 6 blocks of 64 or 3 of 128).
+// block size (151 registers: 12 warps per SM, 6 blocks of 64 or 3 of 128).
 // This measured 5 % faster on 4096^2 and 8 % on 8192^2 than the same
 // occupancy requested through __launch_bounds__' minimum blocks (148
 // registers, a different schedule), and faster than register caps of 144
@@ -932,7 +932,7 @@ struct DualKernel {
 
 // the instantiations a launch can pick: (block size, paired FP32 or scalar).
 // The single-domain step runs 12 warps per SM (6 blocks of 64 or 3 of 128
-// with ~154 registers a thread), not 16 (8 x 64 or 4 x 128 at 128
+// with ~151 registers a thread), not 16 (8 x 64 or 4 x 128 at 128
 // registers): within 128 registers the compiler spends ~50 more instructions
 // per cell on copies and recomputation, which costs more than the four warps
 // gain. For the single-domain kernels at 64 and 128 threads MINB names the
