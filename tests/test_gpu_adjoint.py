@@ -165,6 +165,16 @@ def test_autograd_function(lb):
     _, dTb, dGw = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, 10, 4)
     assert np.allclose(Tb.grad.numpy(), dTb, rtol=1e-12, atol=0)
     assert abs(float(Gw.grad) - dGw) <= 1e-12 * abs(dGw)
+    # without an interval the wrapper lets the library pick it (every step
+    # stored here): the same J and gradients as an explicit interval of 1
+    Tb2 = torch.tensor(prof, dtype=F64, requires_grad=True)
+    Gw2 = torch.tensor(0.05, dtype=F64, requires_grad=True)
+    J2 = lb.heat_flux_window(Tb2, Gw2, sim, blob, 10)
+    J2.backward()
+    J1, dTb1, dGw1 = gpu_adjoint(lb, cfg, rho0, prof, 0.05, f0, th0, 10, 1)
+    assert float(J2) == J1
+    assert np.allclose(Tb2.grad.numpy(), dTb1, rtol=1e-12, atol=0)
+    assert abs(float(Gw2.grad) - dGw1) <= 1e-12 * abs(dGw1)
 
 
 @pytest.mark.parametrize("L", [256, 512])
