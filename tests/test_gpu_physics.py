@@ -1,6 +1,7 @@
 """Physics checks of the oracle's pins repeated on the GPU at larger size:
 flat-interface coexistence against Maxwell's construction across the
-temperature range (the improved forcing of Eq. 8 with sigma = 1.2, Sec. 2).
+temperature range (the improved forcing of Eq. 8 with sigma = 1.2, Sec. 2),
+and the shear-wave decay at the liquid and vapour viscosities of Sec. 3.1.
 Young-Laplace and the contact angles are in test_gpu_diagnostics.py and
 test_gpu_wetting.py."""
 
@@ -44,3 +45,47 @@ def test_flat_interface_coexistence(lb, tr):
     assert abs(v1 / rv - 1) < 0.04, (v1, rv)
     if tr == 0.86:
         assert abs(v0 / rv - 1) > 0.3
+
+
+def _shear_wave_state(rho, u0, Lx, Ly):
+    """Post-collision populations of a resting uniform density with the
+    x-velocity u0 sin(2 pi y / Ly): the D2Q9 second-order equilibrium
+    w_a rho (1 + 3 e.u + 9/2 (e.u)^2 - 3/2 u^2)."""
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.float64)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    ux = u0 * np.sin(2 * np.pi * np.arange(Ly) / Ly)[:, None] * np.ones((1, Lx))
+    eu = ex[:, None, None] * ux[None]
+    f = w[:, None, None] * rho * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * ux[None] ** 2)
+    return f.astype(np.float32)
+
+
+def test_shear_wave_viscosity(lb):
+    """A shear wave in uniform liquid (rho_L) and uniform vapour (rho_V),
+    periodic 512 x 512, thermal step off, no gravity: F_m vanishes on the
+    uniform density, so u_x(y) = A(t) sin(k y) decays as exp(-nu k^2 t) with
+    the kinematic viscosities of Sec. 3.1, nu_L = 0.1 and nu_V = 0.5/3 (the
+    phase's end of the rho-linear relaxation time). The rate measured
+    between steps 500 and 4500 matches within 1 %."""
+    Lx = Ly = 512
+    cfg = lb.Config(Lx=Lx, Ly=Ly, bc_y=lb.BC_PERIODIC, isothermal=True, g=0.0, noise_amp=0.0)
+    rv, rl = lb.coexistence(cfg)
+    k = 2 * np.pi / Ly
+    s = np.sin(k * np.arange(Ly))
+    insts = []
+    for rho in (rl, rv):
+        insts.append({"cfg": cfg, "rho0": np.full((Ly, Lx), rho, dtype=np.float32)})
+    batch = lb.Batch(insts)
+    for i, rho in enumerate((rl, rv)):
+        batch.set_state(i, _shear_wave_state(rho, 1e-3, Lx, Ly), np.zeros((Ly, Lx), dtype=np.float32))
+
+    def amplitude():
+        return [2.0 / Ly * float(batch.fields(i)["ux"].astype(np.float64).mean(axis=1) @ s) for i in range(2)]
+
+    batch.step(500)
+    a1 = amplitude()
+    batch.step(4000)
+    a2 = amplitude()
+    batch.close()
+    for (nu_want, x1, x2) in zip((cfg.nu_l, cfg.nu_v), a1, a2):
+        nu = np.log(x1 / x2) / (k * k * 4000)
+        assert abs(nu / nu_want - 1) < 0.01, (nu, nu_want)
