@@ -45,6 +45,8 @@ CASES = [
     (21, 9, 0, False, 0.0, True),
     (300, 70, 0, False, 0.105, False),
     (517, 41, 1, False, 0.065, False),
+    (130, 23, 1, True, 0.05, False),   # outflow top with the ghost layer, two strips, ragged
+    (229, 31, 2, False, 0.0, True),    # periodic, thermal step off, three strips, ragged
 ]
 
 
