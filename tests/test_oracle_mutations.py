@@ -107,6 +107,15 @@ def wall_fill_sign(f, fpost, P):
     return out
 
 
+def wall_fill_top_sign(f, fpost, P):
+    """Zou-He at the top wall with f7 = f5 - (f1 - f3)/2 (sign slip)."""
+    out = _fill(f, fpost, P).clone()
+    _, top = L._row_masks(P)
+    d = 0.5 * (out[1] - out[3])
+    out[7] = torch.where(top, out[5] - d, out[7]) if P.bc_y == L.BC_WALLS else out[7]
+    return out
+
+
 def adhesion_sign(psi, P):
     """F_ads with the opposite sign (Eq. 22)."""
     fx, fy = _ads(psi, P)
@@ -235,6 +244,7 @@ MUTATIONS = {
     "forcing factor": ("collide", collide_forcing_factor, ["guo"], True),
     "RK4 stage": ("rk4_temperature", rk4_stage3, ["rk4"], True),
     "Zou-He sign": ("wall_fill", wall_fill_sign, ["zou_he"], True),
+    "Zou-He top sign": ("wall_fill", wall_fill_top_sign, ["zou_he"], True),
     "adhesion sign": ("adhesion_force", adhesion_sign, ["adhesion"], True),
     "force weight": ("FORCE_W", FORCE_W_WRONG, ["taylor"], True),
     "streaming direction": ("stream_pull", stream_push, ["stream"], True),
