@@ -116,6 +116,26 @@ def wall_fill_top_sign(f, fpost, P):
     return out
 
 
+_wflux = L.wall_heat_flux
+_rk4 = L.rk4_temperature
+
+
+def flux_sign(theta, rho, P):
+    """q_w = +lambda dT/dy instead of -lambda dT/dy (Sec. 3.2)."""
+    qw, q = _wflux(theta, rho, P)
+    return -qw, -q
+
+
+def top_wall_zero_gradient(theta, rho, vx, vy, P):
+    """The new top wall row copies the row below (zero gradient) instead of
+    the Dirichlet T_s."""
+    th = _rk4(theta, rho, vx, vy, P)
+    if P.bc_y != L.BC_PERIODIC and not P.isothermal:
+        th = th.clone()
+        th[-1] = th[-2]
+    return th
+
+
 def adhesion_sign(psi, P):
     """F_ads with the opposite sign (Eq. 22)."""
     fx, fy = _ads(psi, P)
@@ -252,6 +272,8 @@ MUTATIONS = {
     "psi factor": ("pseudopotential", psi_half, ["bulk_pressure"], True),
     "relaxation time": ("tau_nu", tau_nu_no_half, ["tau_nu"], True),
     "wall derivative order": ("wall_heat_flux", flux_first_order, ["wall_flux"], True),
+    "wall flux sign": ("wall_heat_flux", flux_sign, ["wall_flux", "conduction"], True),
+    "top wall temperature": ("rk4_temperature", top_wall_zero_gradient, ["conduction"], True),
     "d phi / dT sign": ("pr_dphi_dT", dphi_sign, ["dp_dT"], True),
     "buoyancy sign": ("buoyancy", buoyancy_sign, ["buoyancy"], True),
     "equal-area primitive": ("_pr_area", area_half_log, ["maxwell"], False),
@@ -301,6 +323,7 @@ PINS = {
     "coexistence": lambda c: pins.test_flat_interface_coexistence_matches_maxwell(c),
     "sigma_rows": _sigma_rows,
     "ghost": lambda c: pins.test_ghost_layer_wall_rows_on_linear_psi(),
+    "conduction": lambda c: pins.test_linear_conduction_profile_is_steady(c),
 }
 
 
