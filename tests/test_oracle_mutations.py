@@ -136,6 +136,20 @@ def top_wall_zero_gradient(theta, rho, vx, vy, P):
     return th
 
 
+_fmf = L.interaction_force
+
+
+def interaction_sign(psi, P):
+    """F_m = +G psi sum_a w_a psi(x + e_a) e_a (Eq. 7 with the sign lost)."""
+    fx, fy = _fmf(psi, P)
+    return -fx, -fy
+
+
+def kappa_sign(omega):
+    """The acentric-factor polynomial of Eq. 21 with + on the omega^2 term."""
+    return 0.37464 + 1.54226 * omega + 0.26992 * omega * omega
+
+
 def adhesion_sign(psi, P):
     """F_ads with the opposite sign (Eq. 22)."""
     fx, fy = _ads(psi, P)
@@ -267,6 +281,8 @@ MUTATIONS = {
     "Zou-He top sign": ("wall_fill", wall_fill_top_sign, ["zou_he"], True),
     "adhesion sign": ("adhesion_force", adhesion_sign, ["adhesion"], True),
     "force weight": ("FORCE_W", FORCE_W_WRONG, ["taylor"], True),
+    "interaction-force sign": ("interaction_force", interaction_sign, ["taylor"], True),
+    "kappa polynomial": ("pr_kappa", kappa_sign, ["maxwell"], True),
     "streaming direction": ("stream_pull", stream_push, ["stream"], True),
     "stencil weight": ("STENCIL_W", STENCIL_W_WRONG, ["quadratics", "symbol"], True),
     "psi factor": ("pseudopotential", psi_half, ["bulk_pressure"], True),
