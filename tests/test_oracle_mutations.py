@@ -150,6 +150,16 @@ def kappa_sign(omega):
     return 0.37464 + 1.54226 * omega + 0.26992 * omega * omega
 
 
+def solid_both_walls(P):
+    """s = 1 on the top wall row too (R7 gives the wettability to the
+    heating surface only)."""
+    s_ = torch.zeros(P.Ly, P.Lx, dtype=F64)
+    if P.bc_y != L.BC_PERIODIC:
+        s_[0] = 1.0
+        s_[-1] = 1.0
+    return s_
+
+
 def adhesion_sign(psi, P):
     """F_ads with the opposite sign (Eq. 22)."""
     fx, fy = _ads(psi, P)
@@ -280,6 +290,7 @@ MUTATIONS = {
     "Zou-He sign": ("wall_fill", wall_fill_sign, ["zou_he"], True),
     "Zou-He top sign": ("wall_fill", wall_fill_top_sign, ["zou_he"], True),
     "adhesion sign": ("adhesion_force", adhesion_sign, ["adhesion"], True),
+    "adhesion on both walls": ("solid_switch", solid_both_walls, ["adhesion"], True),
     "force weight": ("FORCE_W", FORCE_W_WRONG, ["taylor"], True),
     "interaction-force sign": ("interaction_force", interaction_sign, ["taylor"], True),
     "kappa polynomial": ("pr_kappa", kappa_sign, ["maxwell"], True),
