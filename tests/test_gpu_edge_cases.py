@@ -117,3 +117,42 @@ def test_adjoint_window_records_probes_once(lb, ckpt):
     for k in ("rho", "T", "p"):
         assert ra[k].shape == (3, 7) and np.array_equal(ra[k], rb[k]), k
     sim.close()
+
+
+def test_adjoint_does_not_depend_on_the_launch_shape(lb):
+    """The replayed forward steps are launch-shape independent, so J and the
+    gradients are the same under another block size and segment height."""
+    cfg, rho0 = pool(lb, Lx=150, Ly=40)
+    out = []
+    for shape in ((0, 0), (128, 7), (64, 3)):
+        sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)
+        sim.set_launch(*shape)
+        sim.step(3)
+        out.append(sim.adjoint(9, 4))
+        sim.close()
+    for J, dTb, dGw in out[1:]:
+        assert J == out[0][0] and np.array_equal(dTb, out[0][1])
+        assert abs(dGw - out[0][2]) <= 1e-12 * abs(out[0][2])
+
+
+def test_simulations_on_two_streams_are_independent(lb):
+    """Two simulations on their own CUDA streams, stepped in turns (runs of 32
+    steps replayed from graphs and single steps), each end where it ends when
+    run alone: handles share no device state."""
+    cases = [pool(lb, Lx=90, Ly=36, seed=1), pool(lb, Lx=64, Ly=48, bc=lb.BC_TOP_OUTFLOW, seed=2)]
+    solo = []
+    for cfg, rho0 in cases:
+        sim = lb.Simulation(cfg, superheat=0.01, Gw=0.03, rho0=rho0)
+        sim.step(70)
+        solo.append(sim.get_state() + (sim.heat_flux(),))
+        sim.close()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    sims = [lb.Simulation(cfg, superheat=0.01, Gw=0.03, rho0=rho0, stream=s) for (cfg, rho0), s in zip(cases, streams)]
+    for n in (33, 1, 36):
+        for sim in sims:
+            sim.step(n)
+    for sim, (f, t, q) in zip(sims, solo):
+        f2, t2 = sim.get_state()
+        assert np.array_equal(f, f2) and np.array_equal(t, t2)
+        assert sim.heat_flux() == q
+        sim.close()
