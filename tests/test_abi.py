@@ -195,3 +195,32 @@ def test_empty_batch_rejected_before_any_device_call(lb):
     b = C.c_void_p()
     assert lb.lib.lb_batch_init(C.byref(b), C.byref(desc), 0, None, 0, None) == -1
     assert not b.value
+
+
+HANDLE_CALLS = ["lb_step", "lb_set_wall_temperature", "lb_set_wettability", "lb_heat_flux", "lb_fields",
+                "lb_get_state", "lb_set_state", "lb_mass", "lb_sync", "lb_info", "lb_set_launch", "lb_save_bytes",
+                "lb_save", "lb_load", "lb_destroy", "lb_adjoint_scratch_bytes", "lb_adjoint_pick_ckpt", "lb_adjoint",
+                "lb_set_probes", "lb_probe_read", "lb_batch_step", "lb_batch_set_launch", "lb_batch_set_persistent",
+                "lb_batch_heat_flux", "lb_batch_get_state", "lb_batch_set_state", "lb_batch_fields",
+                "lb_batch_set_wall_temperature", "lb_batch_set_wettability", "lb_batch_info", "lb_batch_sync",
+                "lb_batch_destroy"]
+
+
+@pytest.mark.parametrize("name", HANDLE_CALLS)
+def test_null_handle_rejected_before_any_device_call(lb, name):
+    """Every entry point that takes a simulation or batch handle rejects a
+    null one with LB_E_INVAL and a message, whatever its other arguments
+    (zeros and null pointers here), before it touches the device."""
+    import ctypes as C
+    fn = getattr(lb.lib, name)
+    args = []
+    for t in fn.argtypes:
+        if t in (C.c_double, C.c_float):
+            args.append(0.0)
+        elif t in (C.c_int, C.c_int32, C.c_int64, C.c_longlong, C.c_size_t, C.c_uint64):
+            args.append(0)
+        else:
+            args.append(None)
+    assert fn(*args) == -1, name
+    msg = lb.lib.lb_last_error().decode()
+    assert "null" in msg or "bad batch" in msg, msg

@@ -156,3 +156,24 @@ def test_simulations_on_two_streams_are_independent(lb):
         assert np.array_equal(f, f2) and np.array_equal(t, t2)
         assert sim.heat_flux() == q
         sim.close()
+
+
+def test_calls_after_close_raise(lb):
+    """A closed simulation or batch has no handle: every call is rejected by
+    the library's null-handle check (an LBError), nothing reaches the device,
+    and closing twice is harmless."""
+    cfg, rho0 = pool(lb)
+    sim = lb.Simulation(cfg, superheat=0.01, rho0=rho0)
+    sim.step(2)
+    sim.close()
+    sim.close()
+    for call in (lambda: sim.step(1), sim.heat_flux, sim.get_state, sim.sync, lambda: sim.adjoint(2, 1)):
+        with pytest.raises(lb.LBError):
+            call()
+    batch = lb.Batch([{"cfg": cfg, "rho0": rho0}])
+    batch.step(2)
+    batch.close()
+    batch.close()
+    for call in (lambda: batch.step(1), batch.heat_flux, batch.sync):
+        with pytest.raises(lb.LBError):
+            call()
