@@ -177,3 +177,30 @@ def test_calls_after_close_raise(lb):
     for call in (lambda: batch.step(1), batch.heat_flux, batch.sync):
         with pytest.raises(lb.LBError):
             call()
+
+
+@pytest.mark.parametrize("ckpt", [1, 3])
+def test_adjoint_reports_faults_in_its_window(lb, ckpt):
+    """A density beyond the EOS limit (rho = 9.9 > the domain of psi, as in
+    the step's own flag test) and a NaN population, planted on the host in
+    the window-start state, make lb_adjoint return LB_E_EOS_DOMAIN and
+    LB_E_NONFINITE; the simulation's own flags stay clear, and after a good
+    state is set the same call succeeds."""
+    cfg, rho0 = pool(lb)
+    sim = lb.Simulation(cfg, superheat=0.012, Gw=0.05, rho0=rho0)
+    f, th = sim.get_state()
+    rl = lb.coexistence(cfg)[1]
+    bad = f.copy()
+    bad[:, 3:6, 10:14] *= np.float32(9.9 / rl)  # liquid cells pushed past the EOS domain
+    nan = f.copy()
+    nan[4, 8, 8] = np.nan
+    for state, code in ((bad, -3), (nan, -4)):
+        sim.set_state(state, th)
+        with pytest.raises(lb.LBError) as ei:
+            sim.adjoint(1, ckpt)  # one step: the planted fault, before it can turn into another
+        assert ei.value.code == code
+        sim.sync()  # the simulation's own accumulator saw nothing
+    sim.set_state(f, th)
+    J, dTb, dGw = sim.adjoint(4, ckpt)
+    assert np.isfinite(J) and np.all(np.isfinite(dTb)) and np.isfinite(dGw)
+    sim.close()
