@@ -222,7 +222,10 @@ int lb_adjoint_pick_ckpt(lb_handle* h, int nsteps, size_t budget_bytes, int* ckp
  * sweep replays nothing: faster, for ~20 planes of scratch per step. J
  * (host) receives the value.
  * Walls or the outflow top in y, with or without the ghost layer, thermal runs
- * only.
+ * only. A fault met by the window's forward steps is returned as
+ * LB_E_EOS_DOMAIN or LB_E_NONFINITE (LB_E_BOUNDS in the checked build), with
+ * the simulation's own fault flags left clear; the simulation has then been
+ * advanced through the window all the same.
  * Synchronises. */
 int lb_adjoint(lb_handle* h, int nsteps, int ckpt_every, void* dev_scratch, size_t scratch_bytes,
                double* J, double* dJ_dTb, double* dJ_dGw);
