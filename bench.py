@@ -484,6 +484,22 @@ def adjoint_roofline(torch, lb, L=2048, nsteps=16, ckpt=8):
                                  "roofline_frac": ADJ_BYTES_PER_LU * cells / (rev_all * 1e-3) / 1e9 / peak}}
 
 
+def paper_context(experiments=None):
+    """What the paper gives about its own runs, beside this run's figures on
+    the same grid: its grid and step counts (Sec. 3.1-3.3); it reports no
+    runtime, hardware, precision or throughput."""
+    ctx = {"grid": "600x150 (Sec. 3.1), periodic x, walls in y",
+           "steps": "superheat switched at 20 000 steps; runs of 10 000-50 000 steps, film boiling to 140 000 "
+                    "(Sec. 3.2-3.3)",
+           "timing": "not reported: the paper gives no runtime, hardware, precision or MLUPS"}
+    if experiments:
+        sims, steps, s = experiments["simulations"], experiments["steps_per_case"], experiments["s_curves"]
+        ctx["here_on_that_grid"] = {"simulations": sims, "steps_each": steps, "seconds": s,
+                                    "glups": sims * steps * 600 * 150 / s / 1e9,
+                                    "what": "the boiling-curve runs of the experiments block, batched on one GPU"}
+    return ctx
+
+
 def summary(line):
     """The key figures of the line's blocks, compact."""
     r = {"mlups": round(line["value"]), "hbm_frac": round(line["roofline"]["frac"], 4),
@@ -660,6 +676,7 @@ def run_ours(args):
             line["adjoint"]["large"] = adjoint_roofline(torch, lb)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        line["paper_context"] = paper_context(line.get("experiments"))
         line["summary"] = summary(line)  # last, so that the end of the line carries the key figures
         print(json.dumps(line), flush=True)
     sim.close()

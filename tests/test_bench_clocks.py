@@ -64,3 +64,12 @@ def test_stop_without_nvidia_smi():
     s = bench.ClockSampler.__new__(bench.ClockSampler)
     s.proc = None
     assert s.stop(0.0, 1.0)["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_paper_context_block():
+    """The bench line quotes what the paper gives about its runs (grid, step
+    counts; no timing) and this run's throughput on that grid."""
+    ctx = bench.paper_context(None)
+    assert "600x150" in ctx["grid"] and "not reported" in ctx["timing"] and "here_on_that_grid" not in ctx
+    ctx = bench.paper_context({"simulations": 108, "steps_per_case": 40000, "s_curves": 13.5})
+    assert abs(ctx["here_on_that_grid"]["glups"] - 108 * 40000 * 600 * 150 / 13.5 / 1e9) < 1e-9
